@@ -1,0 +1,357 @@
+"""Throughput of one design step of the diffractive-storage hot path on GB300.
+
+A step is one forward (every channel through all K layers and K+1 gaps), the
+MSE objective with per-channel PSNR and dL/dI, and the adjoint gradient
+dL/dh, over a design of 4096 wavelength channels, 5 layers of 200 x 200
+thickness pixels padded to 400 x 400 (the massive workload).  The metric is
+lambda-channel layer-propagations per second (N_w * (K+1) per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
+4096-channel shard of an N*4096-channel design (weak scaling) and the
+gradient shards are summed with one all-reduce.  ``--impl reference`` times
+the FP64 CPU oracle on the host cores on a bounded channel sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lambda-channel layer-propagations/s (fwd+adjoint, 4096 lambda)"
+UNIT = "propagations/s"
+WORKLOAD = "massive"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--path", default="auto")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _workload(name, rank, world):
+    from paper_2604_02624_gb300 import workloads as W
+    w = W.workload(name)
+    if world > 1:
+        # weak scaling: the design holds world * N_w channels, rank r owns shard r
+        nw = w.n_lambda
+        big = W.workload(name, n_lambda=nw * world) if name in ("batched", "massive", "precision") else w
+        w = big.subset(np.arange(rank * nw, (rank + 1) * nw))
+    return w
+
+
+def _config(w, world):
+    return {"workload": f"{w.name}: {w.n_lambda} lambda x {w.n_layers} layers, {w.n}x{w.n} "
+                        f"padded to {w.m}x{w.m}, FOV {w.fov}x{w.fov}",
+            "n_lambda_per_gpu": int(w.n_lambda), "n_layers": int(w.n_layers), "n": int(w.n),
+            "m": int(w.m), "fov": int(w.fov), "n_lambda_total": int(w.n_lambda * world),
+            "l2": "inputs larger than L2 (row spectra and checkpoints are several GB)",
+            "parallelism": f"lambda-shard x{world}" if world > 1 else "single GPU"}
+
+
+# ----------------------------------------------------------------- oracle timing
+def _oracle_sample(w, seconds, h, T):
+    """Time the FP64 oracle (as it stands) on whole channels of the workload
+    until ``seconds`` of CPU work; returns (propagations/s, channels, cores)."""
+    from oracle import dos_oracle as O
+    idx = []
+    t0 = time.perf_counter()
+    w_all = w
+    done = 0
+    while True:
+        i = (done * 997) % w_all.n_lambda
+        ws = w_all.subset([i])
+        model = dict(lambdas=ws.lambdas, gaps=ws.gaps, pitch=ws.pitch, m=ws.m, fov=ws.fov,
+                     aperture=ws.aperture, n_index=ws.n_index, kappa=ws.kappa)
+        O.loss_and_grad(h, T[i:i + 1], **model)
+        idx.append(i)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and done >= 2:
+            break
+    units = done * (w.n_layers + 1)
+    return units / el, done, el
+
+
+def _cores_used():
+    # numpy's pocketfft and the oracle's loops run on one thread
+    return 1
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    from paper_2604_02624_gb300 import workloads as W
+    w = _workload(a.workload, 0, 1)
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    per_step = max(1.0, a.cpu_seconds / max(1, a.steps + a.warmup))
+    for _ in range(a.warmup):
+        _oracle_sample(w, 0.0, h, T)
+    vals, chans, secs = [], 0, 0.0
+    for _ in range(a.steps):
+        v, c, s = _oracle_sample(w, per_step, h, T)
+        vals.append(v)
+        chans += c
+        secs += s
+    value = chans * (w.n_layers + 1) / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * secs / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(w, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cores_used(), "kind": "oracle",
+                             "sample": f"{chans} whole channels (fwd + MSE + adjoint) of the "
+                                       f"{w.n_lambda}-channel design, timed on the host"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(a):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2604_02624_gb300 import workloads as W
+    from paper_2604_02624_gb300 import _lib as L
+    from paper_2604_02624_gb300.api import DiffractiveStack
+
+    w = _workload(a.workload, rank, world)
+    h_np = W.thickness(w, 0)
+    T_np = W.targets(w, 1)
+    stack = DiffractiveStack.from_workload(w, device=dev, n_lambda_total=w.n_lambda * world,
+                                           path=a.path)
+    h = torch.tensor(h_np, dtype=torch.float32, device=dev)
+    T = torch.tensor(T_np, dtype=torch.float32, device=dev)
+    I = torch.empty((w.n_lambda, w.fov, w.fov), dtype=torch.float32, device=dev)
+    g = torch.empty_like(h)
+    stream = torch.cuda.current_stream(dev)
+    launches = [0]
+
+    def step():
+        stack.forward(h, out=I)
+        n1 = stack.last_launch_count
+        _, psnr, dLdI = stack.loss(T, read=False)
+        n2 = stack.last_launch_count
+        stack.backward(h, dLdI, out=g)
+        n3 = stack.last_launch_count
+        if dist is not None:
+            dist.all_reduce(g)
+        launches[0] += n1 + n2 + n3
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    L.dos_set_timing(stack.handle, True)
+    launches[0] = 0
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    kernel = {}
+    for kind, name in enumerate(L.KERNEL_KINDS):
+        n, t = L.dos_kernel_time(stack.handle, kind)
+        kernel[name] = (n, t)
+    L.dos_set_timing(stack.handle, False)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / a.steps
+    units_per_step = w.n_lambda * (w.n_layers + 1) * world
+    value = units_per_step / (ms_step * 1e-3)
+
+    # ---- roofline of the dominant kernel (live CUDA-event times above)
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dom = max(kernel, key=lambda k: kernel[k][1])
+    n_l, t_l = kernel[dom]
+    per_launch_ms = t_l / max(1, n_l)
+    nw, n, m, hs = w.n_lambda, w.n, w.m, w.m // 2 + 1
+    # algorithmic bytes per launch (every channel once): complex64 = 8 B
+    algo = {
+        "column_forward": nw * (16 * n * m + 8 * hs * hs),
+        "column_adjoint": nw * (16 * n * m + 8 * hs * hs),
+        "row_forward": nw * (16 * n * m + 8 * n * n),
+        "row_adjoint": nw * (16 * n * m + 8 * n * n),
+    }.get(dom)
+    roof = None
+    if algo:
+        ach = algo / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes_per_launch": algo, "ms_per_launch": per_launch_ms,
+                "launches": n_l}
+    kernel_share = {k: {"launches": v[0], "ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in kernel.values()))}
+                    for k, v in kernel.items() if v[0]}
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        h_host = torch.tensor(h_np, dtype=torch.float32).pin_memory()
+        T_host = torch.tensor(T_np, dtype=torch.float32).pin_memory()
+        g_host = torch.empty(h.shape, dtype=torch.float32).pin_memory()
+        loss_host = torch.empty(1, dtype=torch.float64).pin_memory()
+        h_dev = torch.empty_like(h)
+        T_dev = torch.empty_like(T)
+
+        def e2e_step():
+            h_dev.copy_(h_host, non_blocking=True)
+            T_dev.copy_(T_host, non_blocking=True)
+            stack.forward(h_dev, out=I)
+            _, _, dLdI = stack.loss(T_dev, read=False)
+            stack.backward(h_dev, dLdI, out=g)
+            if dist is not None:
+                dist.all_reduce(g)
+            g_host.copy_(g, non_blocking=True)
+            loss_host[0] = stack.read_loss()   # waits for the step
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(3, a.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": units_per_step * k2 / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_host.numel() * 4 + T_host.numel() * 4),
+               "d2h_bytes_per_step": int(g_host.numel() * 4 + 8)}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        v, c, s = _oracle_sample(w, a.cpu_seconds, h_np, T_np)
+        cpu = {"value": v, "unit": UNIT, "cores": _cores_used(), "kind": "oracle",
+               "sample": f"{c} whole channels (fwd + MSE + adjoint, FP64) of the {w.n_lambda}-channel "
+                         f"design in {s:.1f} s"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(w, world), "path": stack.path, "roofline": roof,
+            "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches[0], "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    stack.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

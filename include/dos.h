@@ -1,0 +1,234 @@
+/*
+ * dos.h - C ABI of the GB300 (sm_103a) engine for the forward model and the
+ * gradient of wavelength-multiplexed diffractive optical storage
+ * (Shen, Li, Isil et al., arxiv 2604.02624).
+ *
+ * The engine evaluates, for N_w independent wavelength channels at once, the
+ * cascade of Section 4 of the paper:
+ *
+ *   u_0      = 1 on the centred A x A input aperture, 0 elsewhere (N x N)
+ *   v_1      = P_{z_0}(u_0)
+ *   u_l      = t_l * v_l,   t_l = exp(-2 pi kappa h/lambda)
+ *                                  * exp(-j 2 pi (n - n_medium) h / lambda)   (Eq. 1)
+ *              with h = h_l + h_base                                            (Eq. 2)
+ *   v_{l+1}  = P_{z_l}(u_l),  l = 1..K                                          (Eq. 5)
+ *   o        = central F x F window of v_{K+1},   I = |o|^2                     (Section 2)
+ *
+ * where P_z is free-space propagation by the angular-spectrum transfer
+ * function of the Rayleigh-Sommerfeld impulse response of Eq. 4,
+ *   P_z(u) = crop_N( IDFT_M( H_z * DFT_M( zero_pad_M(u) ) ) ),
+ *   H_z(fx, fy) = exp(j 2 pi z sqrt((n_medium/lambda)^2 - fx^2 - fy^2)),
+ * fx, fy the DFT bin frequencies of an M-point grid of pitch Delta, and for
+ * evanescent bins exp(-2 pi z sqrt(fx^2 + fy^2 - (n_medium/lambda)^2)) (or 0).
+ * The objective is the MSE between I and per-channel targets (Section 2) and
+ * the gradient with respect to every thickness pixel is the adjoint of the
+ * cascade, summed over the channels that share the layers.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lengths are in metres (pitch, gaps, wavelengths, thickness).
+ *  - Arrays are C-contiguous, row-major; images are [row y][column x].
+ *  - "d_" pointers are CUDA device pointers on the context's device; they are
+ *    owned by the caller, must stay valid until the work queued on the
+ *    context's stream has finished, and are never freed by the library.
+ *  - "h_" pointers are host pointers, read during the call only.
+ *  - Complex arrays are interleaved (re, im) float pairs.
+ *  - All work is queued on the context's CUDA stream; calls return before the
+ *    GPU finishes unless stated otherwise.
+ *  - A context is not thread-safe; use one context per host thread / stream.
+ *  - Every int-returning call returns DOS_OK (0) or one of DOS_ERR_*; no C++
+ *    exception crosses the ABI. dos_last_error() describes the last failure
+ *    of the calling thread.
+ */
+#ifndef DOS_H_
+#define DOS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DOS_API __attribute__((visibility("default")))
+#else
+#define DOS_API
+#endif
+
+/* Status codes. */
+enum {
+  DOS_OK = 0,
+  DOS_ERR_ARG = 1,         /* invalid argument or unsupported size           */
+  DOS_ERR_OOM = 2,         /* device or host allocation failed               */
+  DOS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed    */
+  DOS_ERR_STATE = 4,       /* call out of order (e.g. backward w/o forward)  */
+  DOS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up             */
+  DOS_ERR_UNSUPPORTED = 6  /* valid request that this build cannot serve     */
+};
+
+/* Evanescent bins of the transfer function (q < 0). */
+enum { DOS_EVAN_DECAY = 0, DOS_EVAN_ZERO = 1 };
+
+/* Objective of dos_loss (Section 2: an MSE between I and the targets). */
+enum {
+  DOS_LOSS_MSE = 0,        /* mean over channels and FOV pixels of (I - T)^2            */
+  DOS_LOSS_MSE_SCALED = 1  /* same with sigma_w I, sigma_w = sum I T / sum I^2 per channel */
+};
+
+/* Implementation of the propagation passes. */
+enum {
+  DOS_PATH_AUTO = 0,       /* fastest available for the sizes                       */
+  DOS_PATH_MULTIPASS = 1,  /* row pass / column pass kernels, spectra staged in HBM */
+  DOS_PATH_FUSED = 2       /* one persistent launch per sweep, fields kept on chip   */
+};
+
+typedef struct dos_config {
+  int n;              /* N: thickness pixels per side of every layer (Section 4)     */
+  int m;              /* M: zero-padded DFT size, M >= N, see dos_supported_m()      */
+  int n_layers;       /* K >= 1 diffractive layers                                   */
+  int n_lambda;       /* N_w >= 1 wavelength channels handled by this context        */
+  int n_lambda_total; /* channels of the whole design (loss normalisation); 0 = N_w  */
+  int fov;            /* F: output field of view side, N - F even, 1 <= F <= N       */
+  int aperture;       /* A: input aperture side, N - A even; 0 means A = F            */
+  double pitch;       /* Delta: sampling period = feature size [m] (Section 4)       */
+  const double *gaps; /* K+1 distances [m]: input->L1, L1->L2, ..., LK->output (>= 0) */
+  const double *lambda;  /* N_w vacuum wavelengths [m] (> 0)                          */
+  const double *n_index; /* N_w real parts n(lambda) of the layer index (Eq. 1)       */
+  const double *kappa;   /* N_w extinction coefficients kappa(lambda); NULL = all 0   */
+  double n_medium;    /* index of the medium between layers (Eq. 1 n_air, Eq. 4 n); > 0 */
+  double h_base;      /* base thickness of Eq. 2 [m], added to every pixel            */
+  int evanescent;     /* DOS_EVAN_DECAY or DOS_EVAN_ZERO                               */
+  int loss;           /* DOS_LOSS_MSE or DOS_LOSS_MSE_SCALED                           */
+  int path;           /* DOS_PATH_*                                                    */
+} dos_config;
+
+typedef struct dos_ctx dos_ctx;
+
+/*
+ * Sizes M accepted by this build (the padded DFT length); writes up to `cap`
+ * of them to `out` and returns how many there are.  Host-only, no GPU needed.
+ */
+DOS_API int dos_supported_m(int *out, int cap);
+
+/*
+ * Creates a context on the current CUDA device for the design of `cfg`
+ * (Section 4 geometry), binding it to `cuda_stream` (a cudaStream_t, may be
+ * NULL for the legacy default stream).  Copies every array of `cfg`.
+ * Allocates the device workspace (spectra, per-layer field checkpoints, the
+ * transfer-function tables H_z for every distinct gap and wavelength, computed
+ * here with an FP64 phase, and the aperture spectrum) and synchronises the
+ * stream once.  On failure *out is NULL and nothing stays allocated.
+ * Errors: DOS_ERR_ARG (sizes / values), DOS_ERR_OOM, DOS_ERR_CUDA.
+ */
+DOS_API int dos_create(dos_ctx **out, const dos_config *cfg, void *cuda_stream);
+
+/* Rebinds the context to another stream (the caller orders the two streams). */
+DOS_API int dos_set_stream(dos_ctx *ctx, void *cuda_stream);
+
+/*
+ * Forward model, Section 4 Eq. 1-5: every channel through the K layers.
+ *   d_h  [K][N][N] float32 thickness h_l (learnable part of Eq. 2) [m].
+ *   d_I  [N_w][F][F] float32 output intensities |o|^2, or NULL to skip.
+ *   save_for_backward: nonzero keeps the incoming field of every layer
+ *        (K x N_w x N x N complex64 in the workspace) for dos_backward.
+ * The complex output fields o are always kept (dos_loss, dos_backward and
+ * dos_output_field read them).  Errors: DOS_ERR_ARG (NULL d_h), DOS_ERR_CUDA.
+ */
+DOS_API int dos_forward(dos_ctx *ctx, const float *d_h, float *d_I, int save_for_backward);
+
+/*
+ * Objective of the last forward (Section 2: MSE between O_w = |o_w|^2 and its
+ * target, over all channels), with the per-channel PSNR.
+ *   d_T     [N_w][F][F] float32 targets (required).
+ *   h_loss  host double receiving L; when non-NULL the call waits for the
+ *           stream.  When NULL, L stays on the device (dos_read_loss).
+ *   d_psnr  [N_w] float32: 10 log10(1 / mean_p (sigma_w I - T)^2), sigma_w the
+ *           least-squares scale sum I T / sum I^2; NULL to skip.
+ *   d_dLdI  [N_w][F][F] float32 gradient dL/dI of the configured loss; NULL to skip.
+ * L is normalised by n_lambda_total * F^2 so that shards of one design add up.
+ * Errors: DOS_ERR_STATE (no forward yet), DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_loss(dos_ctx *ctx, const float *d_T, double *h_loss, float *d_psnr,
+                     float *d_dLdI);
+
+/* Copies the loss of the last dos_loss to *h_loss (waits for the stream). */
+DOS_API int dos_read_loss(dos_ctx *ctx, double *h_loss);
+
+/*
+ * Gradient of a real objective with respect to the thickness, by the adjoint
+ * of Eq. 1-5 (error back-propagation, Section 2), summed over the channels.
+ *   d_dLdI [N_w][F][F] float32 dL/dI for the last forward's intensities.
+ *   d_dLdh [K][N][N] float32, overwritten with dL/dh_l [1/m].
+ * Needs the last dos_forward to have had save_for_backward != 0 and the same
+ * d_h contents (the layers' transmissions are recomputed from it).
+ * The sum over channels has a fixed order: results are bitwise reproducible.
+ * Errors: DOS_ERR_STATE, DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_backward(dos_ctx *ctx, const float *d_h, const float *d_dLdI, float *d_dLdh);
+
+/*
+ * Copies the complex output field o of the last forward, [N_w][F][F] complex64
+ * (interleaved floats), to d_o.  Errors: DOS_ERR_STATE, DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_output_field(dos_ctx *ctx, float *d_o);
+
+/*
+ * Copies the incoming field v_l of layer `layer` (1..K, before its
+ * modulation) saved by the last dos_forward(save_for_backward != 0),
+ * [N_w][N][N] complex64, to d_v.  Errors: DOS_ERR_STATE, DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_layer_field(dos_ctx *ctx, int layer, float *d_v);
+
+/*
+ * One free-space propagation P_z (Eq. 4-5, angular spectrum) of caller
+ * fields over gap `gap` (0..K) for every channel, or its adjoint (the same
+ * chain with conj(H)) when `adjoint` is nonzero.
+ *   d_in, d_out [N_w][N][N] complex64; may not alias.
+ * Errors: DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_propagate(dos_ctx *ctx, int gap, const float *d_in, float *d_out, int adjoint);
+
+/* Kernel kinds reported by dos_kernel_time. */
+enum {
+  DOS_KERNEL_COLUMN_FORWARD = 0,  /* column pass: DFT, H, IDFT              */
+  DOS_KERNEL_COLUMN_ADJOINT = 1,  /* column pass with conj(H)               */
+  DOS_KERNEL_ROW_FORWARD = 2,     /* row pass: IDFT, Eq. 1 modulation, DFT  */
+  DOS_KERNEL_ROW_ADJOINT = 3,     /* adjoint row pass with dL/dh partials   */
+  DOS_KERNEL_ROW_OUTPUT = 4,      /* output plane: o, I                     */
+  DOS_KERNEL_ROW_SEED = 5,        /* adjoint seed 2 dL/dI o                 */
+  DOS_KERNEL_LOSS = 6,            /* objective, PSNR, dL/dI                 */
+  DOS_KERNEL_GRAD_REDUCE = 7,     /* fixed-order sum of dL/dh partials      */
+  DOS_KERNEL_KINDS = 8
+};
+
+/*
+ * Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch (enable != 0 starts it and clears the totals; 0 stops it).
+ */
+DOS_API int dos_set_timing(dos_ctx *ctx, int enable);
+
+/*
+ * Launch count and total device time [ms] of kernel kind `kind` since timing
+ * was enabled.  Waits for the stream.  Errors: DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_kernel_time(dos_ctx *ctx, int kind, int *launches, double *ms);
+
+/* Bytes of device memory held by the context. */
+DOS_API size_t dos_workspace_bytes(const dos_ctx *ctx);
+
+/* Number of kernel launches queued by the last dos_forward / dos_loss / dos_backward. */
+DOS_API int dos_last_launch_count(const dos_ctx *ctx);
+
+/* Implementation chosen for the context (DOS_PATH_MULTIPASS or DOS_PATH_FUSED). */
+DOS_API int dos_path(const dos_ctx *ctx);
+
+/* Frees every resource of the context (waits for its stream).  NULL is a no-op. */
+DOS_API void dos_destroy(dos_ctx *ctx);
+
+/* Message for the last failing call of the calling thread ("" if none). */
+DOS_API const char *dos_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOS_H_ */

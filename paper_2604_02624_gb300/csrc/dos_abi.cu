@@ -1,0 +1,523 @@
+// dos_abi.cu - the C ABI of include/dos.h: validation, workspace, launch order.
+//
+// Launch order of one design step (K layers, all channels, one stream):
+//   forward : column pass of gap 0 on the aperture spectrum,
+//             K x (row pass [IDFT, crop, checkpoint, Eq. 1 modulation, pad, DFT]
+//                  + column pass [DFT, H, IDFT]),
+//             output row pass (IDFT of the FOV rows -> o, I = |o|^2)
+//   loss    : per-channel statistics, fixed-order total, optional dL/dI
+//   backward: seed row pass (2 dL/dI o), K x (adjoint column pass with conj H
+//             + adjoint row pass [grad_u, dL/dh partials, conj(t) grad_u]),
+//             fixed-order reduction of the partials over channel chunks.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dos.h"
+#include "dos_internal.h"
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace
+
+#define DOS_TIMED(ctx, kind, expr, what)    \
+  do {                                      \
+    (ctx)->timer.begin((kind), (ctx)->stream); \
+    cudaError_t t_ = (expr);                \
+    (ctx)->timer.end((ctx)->stream);        \
+    DOS_CUDA(t_, what);                     \
+  } while (0)
+
+#define DOS_CUDA(expr, what)                                                           \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) return fail(DOS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// CUDA-event timing of each launch, by kernel kind (opt-in).
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  int count[DOS_KERNEL_KINDS] = {0};
+  double ms[DOS_KERNEL_KINDS] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int kind, cudaStream_t s) {
+    if (!on) return;
+    Pending p{kind, get(), get()};
+    cudaEventRecord(p.a, s);
+    pending.push_back(p);
+  }
+  void end(cudaStream_t s) {
+    if (!on || pending.empty()) return;
+    cudaEventRecord(pending.back().b, s);
+  }
+  cudaError_t collect() {
+    for (const Pending& p : pending) {
+      cudaError_t e = cudaEventSynchronize(p.b);
+      if (e != cudaSuccess) return e;
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, p.a, p.b);
+      if (e != cudaSuccess) return e;
+      count[p.kind] += 1;
+      ms[p.kind] += t;
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+    return cudaSuccess;
+  }
+  void reset() {
+    pending.clear();
+    for (int k = 0; k < DOS_KERNEL_KINDS; ++k) count[k] = 0, ms[k] = 0;
+  }
+  void destroy() {
+    for (const Pending& p : pending) pool.push_back(p.a), pool.push_back(p.b);
+    pending.clear();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
+struct dos_ctx {
+  KernelTimer timer;
+  int n = 0, m = 0, K = 0, nw = 0, nw_total = 0, fov = 0, ap = 0, of = 0, oa = 0, hs = 0;
+  int evan = 0, loss = 0, path = DOS_PATH_MULTIPASS;
+  double pitch = 0, n_med = 1, h_base = 0;
+  std::vector<double> gaps, lam, nidx, kap;
+  std::vector<int> gap_slot;  // gap index -> transfer table slot
+  int n_slots = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  const dos::PassOps* ops = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  float2 *S = nullptr, *ckpt = nullptr, *o = nullptr, *Hq = nullptr, *arow = nullptr, *tw = nullptr;
+  dos::ChanConst* chan = nullptr;
+  float* partial = nullptr;
+  dos::LossStats* stats = nullptr;
+  double* d_loss = nullptr;
+  double* h_loss = nullptr;  // pinned
+  int chunk = 1, n_chunks = 1;
+  bool have_fwd = false, have_ckpt = false, have_loss = false;
+  int launches = 0;
+
+  template <typename T>
+  int alloc(T** p, size_t count, const char* what) {
+    void* q = nullptr;
+    const size_t b = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, b);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? DOS_ERR_OOM : DOS_ERR_CUDA,
+                  std::string("cudaMalloc(") + what + ", " + std::to_string(b) + " bytes): " +
+                      cudaGetErrorString(e));
+    }
+    allocs.push_back(q);
+    bytes += b;
+    *p = static_cast<T*>(q);
+    return DOS_OK;
+  }
+  void release() {
+    cudaStreamSynchronize(stream);
+    timer.destroy();
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    if (h_loss) cudaFreeHost(h_loss);
+    h_loss = nullptr;
+  }
+  float2* hq_slot(int gap) const { return Hq + (size_t)gap_slot[gap] * nw * hs * hs; }
+  dos::PassArgs base() const {
+    dos::PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.S = S;
+    a.arow = arow;
+    a.tw = tw;
+    a.chan = chan;
+    a.o = o;
+    a.n = n;
+    a.m = m;
+    a.nw = nw;
+    a.fov = fov;
+    a.of = of;
+    a.hs = hs;
+    a.chunk = chunk;
+    a.n_chunks = n_chunks;
+    return a;
+  }
+};
+
+namespace {
+
+bool finite(double x) { return std::isfinite(x); }
+
+int validate(const dos_config* c) {
+  if (!c) return fail(DOS_ERR_ARG, "config is NULL");
+  if (c->n < 1) return fail(DOS_ERR_ARG, "n must be >= 1");
+  if (c->m < c->n) return fail(DOS_ERR_ARG, "m must be >= n");
+  if (!dos::pass_ops_for_m(c->m)) {
+    int l[32];
+    const int k = dos::supported_m_list(l, 32);
+    std::string s = "m=" + std::to_string(c->m) + " is not a supported padded size (supported:";
+    for (int i = 0; i < k; ++i) s += " " + std::to_string(l[i]);
+    return fail(DOS_ERR_ARG, s + ")");
+  }
+  if (c->n_layers < 1) return fail(DOS_ERR_ARG, "n_layers must be >= 1");
+  if (c->n_lambda < 1 || c->n_lambda > 65535) return fail(DOS_ERR_ARG, "n_lambda must be in [1, 65535]");
+  if (c->n_lambda_total != 0 && c->n_lambda_total < c->n_lambda)
+    return fail(DOS_ERR_ARG, "n_lambda_total must be 0 or >= n_lambda");
+  if (c->fov < 1 || c->fov > c->n || (c->n - c->fov) % 2 != 0)
+    return fail(DOS_ERR_ARG, "fov must be in [1, n] with n - fov even");
+  const int ap = c->aperture == 0 ? c->fov : c->aperture;
+  if (ap < 1 || ap > c->n || (c->n - ap) % 2 != 0)
+    return fail(DOS_ERR_ARG, "aperture must be 0 or in [1, n] with n - aperture even");
+  if (!(c->pitch > 0) || !finite(c->pitch)) return fail(DOS_ERR_ARG, "pitch must be > 0");
+  if (!c->gaps || !c->lambda || !c->n_index) return fail(DOS_ERR_ARG, "gaps, lambda and n_index are required");
+  for (int i = 0; i <= c->n_layers; ++i)
+    if (!(c->gaps[i] >= 0) || !finite(c->gaps[i])) return fail(DOS_ERR_ARG, "gaps must be finite and >= 0");
+  for (int w = 0; w < c->n_lambda; ++w) {
+    if (!(c->lambda[w] > 0) || !finite(c->lambda[w])) return fail(DOS_ERR_ARG, "lambda must be > 0");
+    if (!finite(c->n_index[w])) return fail(DOS_ERR_ARG, "n_index must be finite");
+    if (c->kappa && !finite(c->kappa[w])) return fail(DOS_ERR_ARG, "kappa must be finite");
+  }
+  if (!(c->n_medium > 0) || !finite(c->n_medium)) return fail(DOS_ERR_ARG, "n_medium must be > 0");
+  if (!finite(c->h_base)) return fail(DOS_ERR_ARG, "h_base must be finite");
+  if (c->evanescent != DOS_EVAN_DECAY && c->evanescent != DOS_EVAN_ZERO)
+    return fail(DOS_ERR_ARG, "evanescent must be DOS_EVAN_DECAY or DOS_EVAN_ZERO");
+  if (c->loss != DOS_LOSS_MSE && c->loss != DOS_LOSS_MSE_SCALED)
+    return fail(DOS_ERR_ARG, "loss must be DOS_LOSS_MSE or DOS_LOSS_MSE_SCALED");
+  if (c->path != DOS_PATH_AUTO && c->path != DOS_PATH_MULTIPASS && c->path != DOS_PATH_FUSED)
+    return fail(DOS_ERR_ARG, "path must be a DOS_PATH_* value");
+  return DOS_OK;
+}
+
+int build(dos_ctx* x, const dos_config* c) {
+  x->n = c->n;
+  x->m = c->m;
+  x->K = c->n_layers;
+  x->nw = c->n_lambda;
+  x->nw_total = c->n_lambda_total ? c->n_lambda_total : c->n_lambda;
+  x->fov = c->fov;
+  x->ap = c->aperture ? c->aperture : c->fov;
+  x->of = (c->n - c->fov) / 2;
+  x->oa = (c->n - x->ap) / 2;
+  x->hs = c->m / 2 + 1;
+  x->pitch = c->pitch;
+  x->n_med = c->n_medium;
+  x->h_base = c->h_base;
+  x->evan = c->evanescent;
+  x->loss = c->loss;
+  if (c->path == DOS_PATH_FUSED)
+    return fail(DOS_ERR_UNSUPPORTED, "DOS_PATH_FUSED is not available in this build");
+  x->path = DOS_PATH_MULTIPASS;
+  x->gaps.assign(c->gaps, c->gaps + c->n_layers + 1);
+  x->lam.assign(c->lambda, c->lambda + c->n_lambda);
+  x->nidx.assign(c->n_index, c->n_index + c->n_lambda);
+  x->kap.assign(c->n_lambda, 0.0);
+  if (c->kappa) x->kap.assign(c->kappa, c->kappa + c->n_lambda);
+  x->ops = dos::pass_ops_for_m(c->m);
+  // one transfer table per distinct gap distance
+  std::vector<double> slots;
+  for (double g : x->gaps) {
+    int s = -1;
+    for (size_t i = 0; i < slots.size(); ++i)
+      if (slots[i] == g) s = (int)i;
+    if (s < 0) {
+      s = (int)slots.size();
+      slots.push_back(g);
+    }
+    x->gap_slot.push_back(s);
+  }
+  x->n_slots = (int)slots.size();
+  // channel chunks of the adjoint row pass: about 8 blocks per SM in flight
+  const int row_blocks = (x->n + x->ops->row_lines - 1) / x->ops->row_lines;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, x->device);
+  const int want_chunks = std::max(1, (8 * sms) / std::max(1, row_blocks));
+  x->chunk = std::max(1, (x->nw + want_chunks - 1) / want_chunks);
+  x->n_chunks = (x->nw + x->chunk - 1) / x->chunk;
+
+  const size_t n2 = (size_t)x->n * x->n;
+  int rc;
+  if ((rc = x->alloc(&x->S, (size_t)x->nw * x->n * x->m, "row spectra"))) return rc;
+  if ((rc = x->alloc(&x->ckpt, (size_t)x->K * x->nw * n2, "layer checkpoints"))) return rc;
+  if ((rc = x->alloc(&x->o, (size_t)x->nw * x->fov * x->fov, "output field"))) return rc;
+  if ((rc = x->alloc(&x->Hq, (size_t)x->n_slots * x->nw * x->hs * x->hs, "transfer tables"))) return rc;
+  if ((rc = x->alloc(&x->arow, (size_t)x->m, "aperture spectrum"))) return rc;
+  if ((rc = x->alloc(&x->tw, (size_t)x->ops->Q * (x->ops->P + 1), "twiddles"))) return rc;
+  if ((rc = x->alloc(&x->chan, (size_t)x->nw, "channel constants"))) return rc;
+  if ((rc = x->alloc(&x->partial, (size_t)x->K * x->n_chunks * n2, "gradient partials"))) return rc;
+  if ((rc = x->alloc(&x->stats, (size_t)x->nw, "loss statistics"))) return rc;
+  if ((rc = x->alloc(&x->d_loss, 1, "loss"))) return rc;
+  DOS_CUDA(cudaMallocHost(&x->h_loss, sizeof(double)), "cudaMallocHost(loss)");
+
+  double *d_lam = nullptr, *d_nidx = nullptr, *d_kap = nullptr;
+  if ((rc = x->alloc(&d_lam, (size_t)x->nw, "wavelengths"))) return rc;
+  if ((rc = x->alloc(&d_nidx, (size_t)x->nw, "indices"))) return rc;
+  if ((rc = x->alloc(&d_kap, (size_t)x->nw, "extinction"))) return rc;
+  const size_t db = sizeof(double) * x->nw;
+  DOS_CUDA(cudaMemcpyAsync(d_lam, x->lam.data(), db, cudaMemcpyHostToDevice, x->stream), "copy lambda");
+  DOS_CUDA(cudaMemcpyAsync(d_nidx, x->nidx.data(), db, cudaMemcpyHostToDevice, x->stream), "copy n_index");
+  DOS_CUDA(cudaMemcpyAsync(d_kap, x->kap.data(), db, cudaMemcpyHostToDevice, x->stream), "copy kappa");
+  DOS_CUDA(dos::launch_chan(x->chan, d_lam, d_nidx, d_kap, x->nw, x->n_med, x->h_base, x->stream),
+           "channel constants");
+  for (int s = 0; s < x->n_slots; ++s)
+    DOS_CUDA(dos::launch_htable(x->Hq + (size_t)s * x->nw * x->hs * x->hs, d_lam, x->nw, slots[s],
+                                x->n_med, x->pitch, x->m, x->hs, x->evan, x->stream),
+             "transfer tables");
+  DOS_CUDA(dos::launch_arow(x->arow, x->m, x->oa, x->ap, x->stream), "aperture spectrum");
+  const int RP = x->ops->P % 2 == 0 ? x->ops->P + 1 : x->ops->P;
+  DOS_CUDA(dos::launch_twiddles(x->tw, x->ops->P, x->ops->Q, RP, x->m, x->stream), "twiddles");
+  DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
+  return DOS_OK;
+}
+
+int check_ctx(dos_ctx* c) {
+  if (!c) return fail(DOS_ERR_ARG, "context is NULL");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return fail(DOS_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return DOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+DOS_API int dos_supported_m(int* out, int cap) {
+  int tmp[64];
+  const int k = dos::supported_m_list(tmp, 64);
+  for (int i = 0; out && i < k && i < cap; ++i) out[i] = tmp[i];
+  return k;
+}
+
+DOS_API int dos_create(dos_ctx** out, const dos_config* cfg, void* cuda_stream) {
+  if (!out) return fail(DOS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = validate(cfg);
+  if (rc) return rc;
+  dos_ctx* x = new (std::nothrow) dos_ctx();
+  if (!x) return fail(DOS_ERR_OOM, "host allocation of the context failed");
+  x->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&x->device);
+  if (e != cudaSuccess) {
+    delete x;
+    return fail(DOS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  rc = build(x, cfg);
+  if (rc) {
+    const std::string keep = g_err;
+    x->release();
+    delete x;
+    g_err = keep;
+    return rc;
+  }
+  *out = x;
+  return DOS_OK;
+}
+
+DOS_API int dos_set_stream(dos_ctx* c, void* cuda_stream) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return DOS_OK;
+}
+
+DOS_API int dos_forward(dos_ctx* c, const float* d_h, float* d_I, int save_for_backward) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!d_h) return fail(DOS_ERR_ARG, "d_h is NULL");
+  const dos::PassOps* op = c->ops;
+  const size_t n2 = (size_t)c->n * c->n;
+  c->have_fwd = c->have_ckpt = c->have_loss = false;
+  c->launches = 0;
+  dos::PassArgs a = c->base();
+  // gap 0: the aperture field has the separable spectrum Arow[ky] Arow[kx]
+  a.Hq = c->hq_slot(0);
+  a.out_r0 = 0;
+  a.out_r1 = c->n;
+  DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, true, c->stream), "forward column pass (aperture)");
+  ++c->launches;
+  for (int l = 1; l <= c->K; ++l) {
+    a.h = d_h + (size_t)(l - 1) * n2;
+    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
+    DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_fwd(a, save_for_backward != 0, c->stream), "forward row pass");
+    a.Hq = c->hq_slot(l);
+    a.in_r0 = 0;
+    a.in_r1 = c->n;
+    a.out_r0 = l == c->K ? c->of : 0;
+    a.out_r1 = l == c->K ? c->of + c->fov : c->n;
+    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, false, c->stream), "forward column pass");
+    c->launches += 2;
+  }
+  a.I = d_I;
+  DOS_TIMED(c, DOS_KERNEL_ROW_OUTPUT, op->row_out(a, c->stream), "output row pass");
+  ++c->launches;
+  c->have_fwd = true;
+  c->have_ckpt = save_for_backward != 0;
+  return DOS_OK;
+}
+
+DOS_API int dos_loss(dos_ctx* c, const float* d_T, double* h_loss, float* d_psnr, float* d_dLdI) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_fwd) return fail(DOS_ERR_STATE, "dos_loss needs a dos_forward first");
+  if (!d_T) return fail(DOS_ERR_ARG, "d_T is NULL");
+  const int fov2 = c->fov * c->fov;
+  const double norm = (double)c->nw_total * fov2;
+  c->launches = 0;
+  DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, fov2, c->stream), "loss statistics");
+  DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_final(c->stats, c->nw, fov2, norm, c->loss, c->d_loss, d_psnr, c->stream),
+            "loss total");
+  c->launches += 2;
+  if (d_dLdI) {
+    DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_dldi(c->o, d_T, c->stats, d_dLdI, c->nw, fov2, norm, c->loss, c->stream),
+              "dL/dI");
+    ++c->launches;
+  }
+  c->have_loss = true;
+  if (h_loss) return dos_read_loss(c, h_loss);
+  return DOS_OK;
+}
+
+DOS_API int dos_read_loss(dos_ctx* c, double* h_loss) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_loss) return fail(DOS_ERR_STATE, "no loss computed yet");
+  if (!h_loss) return fail(DOS_ERR_ARG, "h_loss is NULL");
+  DOS_CUDA(cudaMemcpyAsync(c->h_loss, c->d_loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+           "read loss");
+  DOS_CUDA(cudaStreamSynchronize(c->stream), "read loss");
+  *h_loss = *c->h_loss;
+  return DOS_OK;
+}
+
+DOS_API int dos_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_ckpt) return fail(DOS_ERR_STATE, "dos_backward needs dos_forward(save_for_backward=1) first");
+  if (!d_h || !d_dLdI || !d_dLdh) return fail(DOS_ERR_ARG, "d_h, d_dLdI and d_dLdh are required");
+  const dos::PassOps* op = c->ops;
+  const size_t n2 = (size_t)c->n * c->n;
+  c->launches = 0;
+  dos::PassArgs a = c->base();
+  a.dLdI = d_dLdI;
+  DOS_TIMED(c, DOS_KERNEL_ROW_SEED, op->row_seed(a, c->stream), "adjoint seed row pass");
+  ++c->launches;
+  for (int l = c->K; l >= 1; --l) {
+    a.Hq = c->hq_slot(l);
+    a.in_r0 = l == c->K ? c->of : 0;
+    a.in_r1 = l == c->K ? c->of + c->fov : c->n;
+    a.out_r0 = 0;
+    a.out_r1 = c->n;
+    DOS_TIMED(c, DOS_KERNEL_COLUMN_ADJOINT, op->col(a, true, false, c->stream), "adjoint column pass");
+    a.h = d_h + (size_t)(l - 1) * n2;
+    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
+    a.partial = c->partial + (size_t)(l - 1) * c->n_chunks * n2;
+    DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT, op->row_adj(a, l == 1, c->stream), "adjoint row pass");
+    c->launches += 2;
+  }
+  DOS_TIMED(c, DOS_KERNEL_GRAD_REDUCE, dos::launch_grad_reduce(c->partial, d_dLdh, c->n_chunks, (size_t)c->K * n2, n2, c->stream),
+            "gradient reduction");
+  ++c->launches;
+  return DOS_OK;
+}
+
+DOS_API int dos_output_field(dos_ctx* c, float* d_o) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_fwd) return fail(DOS_ERR_STATE, "no forward yet");
+  if (!d_o) return fail(DOS_ERR_ARG, "d_o is NULL");
+  DOS_CUDA(cudaMemcpyAsync(d_o, c->o, sizeof(float2) * c->nw * c->fov * c->fov, cudaMemcpyDeviceToDevice,
+                           c->stream),
+           "copy output field");
+  return DOS_OK;
+}
+
+DOS_API int dos_layer_field(dos_ctx* c, int layer, float* d_v) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_ckpt) return fail(DOS_ERR_STATE, "no forward with save_for_backward yet");
+  if (layer < 1 || layer > c->K) return fail(DOS_ERR_ARG, "layer must be in [1, n_layers]");
+  if (!d_v) return fail(DOS_ERR_ARG, "d_v is NULL");
+  const size_t n2 = (size_t)c->n * c->n;
+  DOS_CUDA(cudaMemcpyAsync(d_v, c->ckpt + (size_t)(layer - 1) * c->nw * n2, sizeof(float2) * c->nw * n2,
+                           cudaMemcpyDeviceToDevice, c->stream),
+           "copy layer field");
+  return DOS_OK;
+}
+
+DOS_API int dos_propagate(dos_ctx* c, int gap, const float* d_in, float* d_out, int adjoint) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (gap < 0 || gap > c->K) return fail(DOS_ERR_ARG, "gap must be in [0, n_layers]");
+  if (!d_in || !d_out || d_in == d_out) return fail(DOS_ERR_ARG, "d_in and d_out must be distinct non-NULL");
+  const dos::PassOps* op = c->ops;
+  c->launches = 0;
+  c->have_fwd = c->have_ckpt = c->have_loss = false;  // the spectra buffer is reused
+  dos::PassArgs a = c->base();
+  a.fin = reinterpret_cast<const float2*>(d_in);
+  a.fout = reinterpret_cast<float2*>(d_out);
+  a.Hq = c->hq_slot(gap);
+  a.in_r0 = 0;
+  a.in_r1 = c->n;
+  a.out_r0 = 0;
+  a.out_r1 = c->n;
+  DOS_CUDA(op->row_in(a, c->stream), "propagate row pass");
+  DOS_CUDA(op->col(a, adjoint != 0, false, c->stream), "propagate column pass");
+  DOS_CUDA(op->row_back(a, c->stream), "propagate back row pass");
+  c->launches = 3;
+  return DOS_OK;
+}
+
+DOS_API int dos_set_timing(dos_ctx* c, int enable) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  c->timer.reset();
+  c->timer.on = enable != 0;
+  return DOS_OK;
+}
+
+DOS_API int dos_kernel_time(dos_ctx* c, int kind, int* launches, double* ms) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (kind < 0 || kind >= DOS_KERNEL_KINDS) return fail(DOS_ERR_ARG, "unknown kernel kind");
+  DOS_CUDA(c->timer.collect(), "kernel timing");
+  if (launches) *launches = c->timer.count[kind];
+  if (ms) *ms = c->timer.ms[kind];
+  return DOS_OK;
+}
+
+DOS_API size_t dos_workspace_bytes(const dos_ctx* c) { return c ? c->bytes : 0; }
+
+DOS_API int dos_last_launch_count(const dos_ctx* c) { return c ? c->launches : 0; }
+
+DOS_API int dos_path(const dos_ctx* c) { return c ? c->path : 0; }
+
+DOS_API void dos_destroy(dos_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  c->release();
+  delete c;
+}
+
+DOS_API const char* dos_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

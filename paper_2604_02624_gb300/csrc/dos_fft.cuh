@@ -1,0 +1,307 @@
+// dos_fft.cuh - FP32 complex DFTs for the angular-spectrum passes (sm_103a).
+//
+// Two levels:
+//  * dft<N, INV, NZ, NO>(x): an N-point DFT held entirely in one thread's
+//    registers, natural order in and out, built at compile time from radix
+//    2/3/4/5 butterflies by Cooley-Tukey splitting. Twiddles are compile-time
+//    constants (cos/sin of rational turns evaluated by a constexpr series), so
+//    they become instruction immediates. NZ leading inputs may be non-zero,
+//    NO leading outputs are needed: zero-padding and cropping prune work.
+//  * Line<P, Q, T>::fft: an M = P*Q point DFT shared by T threads, one shared
+//    memory exchange. Thread t holds x[t + T*i] in r[i] on input *and* output,
+//    so an inverse followed by a forward transform (crop -> modulate -> pad of
+//    Eq. 1/5) needs no data movement between them.
+//
+// Sign convention: forward = exp(-2 pi j k n / M), inverse = exp(+2 pi j k n / M),
+// both unnormalised (the 1/M^2 of the inverse 2D DFT is folded into H).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#define DOS_HD __host__ __device__ __forceinline__
+
+namespace dos {
+
+// ---------------------------------------------------------------- complex ops
+DOS_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+DOS_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+DOS_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+DOS_HD float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+DOS_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+DOS_HD float2 czero() { return make_float2(0.f, 0.f); }
+
+// ------------------------------------------------- compile-time trigonometry
+namespace ct {
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double taylor_sin(double x) {
+  double term = x, sum = x;
+  for (int i = 1; i < 14; ++i) {
+    term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double taylor_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int i = 1; i < 14; ++i) {
+    term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    sum += term;
+  }
+  return sum;
+}
+// cos(2 pi k / n) for integers, by quarter-turn symmetry and a series on [0, pi/4].
+constexpr double cos_turn(long k, long n) {
+  k %= n;
+  if (k < 0) k += n;
+  const long q = (4 * k) / n;
+  const long r = 4 * k - q * n;                 // angle = (q + r/n) * pi/2
+  const double x = (double)r / (double)n * (kPi / 2);
+  const double sx = x > kPi / 4 ? taylor_cos(kPi / 2 - x) : taylor_sin(x);
+  const double cx = x > kPi / 4 ? taylor_sin(kPi / 2 - x) : taylor_cos(x);
+  return q == 0 ? cx : q == 1 ? -sx : q == 2 ? -cx : sx;
+}
+// sin(2 pi k / n) = cos(2 pi (4k - n) / (4n))
+constexpr double sin_turn(long k, long n) { return cos_turn(4 * k - n, 4 * n); }
+
+constexpr int cdiv_clamp(int num, int den, int hi) {
+  return num <= 0 ? 0 : ((num + den - 1) / den < hi ? (num + den - 1) / den : hi);
+}
+constexpr int first_factor(int n) {
+  return n % 4 == 0 && n != 4 ? 4 : n % 5 == 0 && n != 5 ? 5 : n % 3 == 0 && n != 3 ? 3 : 2;
+}
+constexpr bool is_base(int n) { return n == 2 || n == 3 || n == 4 || n == 5; }
+constexpr int butterfly_cost(int n) { return n == 2 ? 4 : n == 3 ? 16 : n == 4 ? 16 : 36; }
+// instruction estimate of a direct sum with NZ inputs and NO outputs
+constexpr int direct_cost(int n, int nz, int no) {
+  int c = 0;
+  for (int k = 0; k < no; ++k)
+    for (int j = 1; j < nz; ++j) {
+      const int e = (j * k) % n;
+      c += 2 + ((e == 0 || 2 * e == n || 4 * e == n || 4 * e == 3 * n) ? 0 : 4);
+    }
+  return c;
+}
+}  // namespace ct
+
+template <int B, int E, typename F>
+DOS_HD void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// x * w^E with w = exp(-2 pi j / N) (forward) or exp(+2 pi j / N) (inverse).
+template <int N, long E, bool INV>
+DOS_HD float2 twiddle(float2 x) {
+  constexpr long e = ((E % N) + N) % N;
+  if constexpr (e == 0) {
+    return x;
+  } else if constexpr (2 * e == N) {
+    return make_float2(-x.x, -x.y);
+  } else if constexpr (4 * e == N) {  // forward -j, inverse +j
+    if constexpr (INV) return make_float2(-x.y, x.x);
+    else return make_float2(x.y, -x.x);
+  } else if constexpr (4 * e == 3 * N) {  // forward +j, inverse -j
+    if constexpr (INV) return make_float2(x.y, -x.x);
+    else return make_float2(-x.y, x.x);
+  } else {
+    constexpr float c = (float)ct::cos_turn(e, N);
+    constexpr float s = INV ? (float)ct::sin_turn(e, N) : -(float)ct::sin_turn(e, N);
+    return make_float2(fmaf(x.x, c, -x.y * s), fmaf(x.x, s, x.y * c));
+  }
+}
+
+// ------------------------------------------------------------- butterflies
+template <bool INV>
+DOS_HD void bfly2(float2* x) {
+  const float2 a = x[0], b = x[1];
+  x[0] = cadd(a, b);
+  x[1] = csub(a, b);
+}
+template <bool INV>
+DOS_HD void bfly3(float2* x) {
+  constexpr float c = -0.5f;
+  constexpr float s = INV ? 0.86602540378443864676f : -0.86602540378443864676f;
+  const float2 t = cadd(x[1], x[2]);
+  const float2 d = csub(x[1], x[2]);
+  const float2 m = make_float2(fmaf(c, t.x, x[0].x), fmaf(c, t.y, x[0].y));
+  x[0] = cadd(x[0], t);
+  // j*s*d
+  const float2 jd = make_float2(-s * d.y, s * d.x);
+  x[1] = cadd(m, jd);
+  x[2] = csub(m, jd);
+}
+template <bool INV>
+DOS_HD void bfly4(float2* x) {
+  const float2 t0 = cadd(x[0], x[2]);
+  const float2 t1 = csub(x[0], x[2]);
+  const float2 t2 = cadd(x[1], x[3]);
+  const float2 d = csub(x[1], x[3]);
+  // forward: -j*d, inverse: +j*d
+  const float2 t3 = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+  x[0] = cadd(t0, t2);
+  x[2] = csub(t0, t2);
+  x[1] = cadd(t1, t3);
+  x[3] = csub(t1, t3);
+}
+template <bool INV>
+DOS_HD void bfly5(float2* x) {
+  constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+  constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+  constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+  constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+  const float2 x0 = x[0];
+  const float2 t1 = cadd(x[1], x[4]);
+  const float2 t2 = cadd(x[2], x[3]);
+  const float2 t3 = csub(x[1], x[4]);
+  const float2 t4 = csub(x[2], x[3]);
+  const float2 a1 = make_float2(fmaf(c2, t2.x, fmaf(c1, t1.x, x0.x)), fmaf(c2, t2.y, fmaf(c1, t1.y, x0.y)));
+  const float2 a2 = make_float2(fmaf(c1, t2.x, fmaf(c2, t1.x, x0.x)), fmaf(c1, t2.y, fmaf(c2, t1.y, x0.y)));
+  const float2 b1 = make_float2(fmaf(s2, t4.x, s1 * t3.x), fmaf(s2, t4.y, s1 * t3.y));
+  const float2 b2 = make_float2(fmaf(-s1, t4.x, s2 * t3.x), fmaf(-s1, t4.y, s2 * t3.y));
+  // forward: X1 = a1 - j b1, X4 = a1 + j b1, X2 = a2 - j b2, X3 = a2 + j b2
+  const float2 jb1 = INV ? make_float2(-b1.y, b1.x) : make_float2(b1.y, -b1.x);
+  const float2 jb2 = INV ? make_float2(-b2.y, b2.x) : make_float2(b2.y, -b2.x);
+  x[0] = make_float2(x0.x + t1.x + t2.x, x0.y + t1.y + t2.y);
+  x[1] = cadd(a1, jb1);
+  x[4] = csub(a1, jb1);
+  x[2] = cadd(a2, jb2);
+  x[3] = csub(a2, jb2);
+}
+
+// Direct sum X[k] = sum_{n < NZ} x[n] w^{nk} for k < NO (small pruned cases).
+template <int N, bool INV, int NZ, int NO>
+DOS_HD void dft_direct(float2* x) {
+  float2 out[NO];
+  static_for<0, NO>([&](auto kk) {
+    constexpr int k = kk;
+    float2 acc = x[0];
+    static_for<1, NZ>([&](auto jj) {
+      constexpr int j = jj;
+      acc = cadd(acc, twiddle<N, (long)j * k, INV>(x[j]));
+    });
+    out[k] = acc;
+  });
+  static_for<0, NO>([&](auto k) { x[k] = out[k]; });
+}
+
+// N-point DFT in registers; only x[0..NZ) are read, only X[0..NO) are produced.
+template <int N, bool INV, int NZ = N, int NO = N>
+DOS_HD void dft(float2* x) {
+  static_assert(NZ >= 0 && NZ <= N && NO >= 0 && NO <= N, "bad pruning");
+  if constexpr (N == 1 || NO == 0) {
+    return;
+  } else if constexpr (NZ == 0) {
+    static_for<0, NO>([&](auto k) { x[k] = czero(); });
+  } else if constexpr (NZ == 1) {
+    static_for<1, NO>([&](auto k) { x[k] = x[0]; });
+  } else if constexpr (ct::is_base(N)) {
+    if constexpr ((NZ < N || NO < N) && ct::direct_cost(N, NZ, NO) < ct::butterfly_cost(N)) {
+      dft_direct<N, INV, NZ, NO>(x);
+    } else {
+      if constexpr (NZ < N) static_for<NZ, N>([&](auto k) { x[k] = czero(); });
+      if constexpr (N == 2) bfly2<INV>(x);
+      else if constexpr (N == 3) bfly3<INV>(x);
+      else if constexpr (N == 4) bfly4<INV>(x);
+      else bfly5<INV>(x);
+    }
+  } else {
+    // N = A*B; input n = B*a + b, output k = k1 + A*k2.
+    constexpr int A = ct::first_factor(N);
+    constexpr int B = N / A;
+    constexpr int NOA = NO < A ? NO : A;
+    constexpr int NZB = NZ < B ? NZ : B;
+    float2 y[N];
+    static_for<0, B>([&](auto bb) {
+      constexpr int b = bb;
+      constexpr int nza = ct::cdiv_clamp(NZ - b, B, A);
+      if constexpr (nza > 0) {
+        float2 t[A];
+        static_for<0, nza>([&](auto aa) { t[aa] = x[B * aa + b]; });
+        dft<A, INV, nza, NOA>(t);
+        static_for<0, NOA>([&](auto kk) {
+          constexpr int k1 = kk;
+          y[b * A + k1] = twiddle<N, (long)b * k1, INV>(t[k1]);
+        });
+      }
+    });
+    static_for<0, NOA>([&](auto kk) {
+      constexpr int k1 = kk;
+      constexpr int nob = ct::cdiv_clamp(NO - k1, A, B);
+      if constexpr (nob > 0) {
+        float2 t[B];
+        static_for<0, NZB>([&](auto bb) { t[bb] = y[bb * A + k1]; });
+        dft<B, INV, NZB, nob>(t);
+        static_for<0, nob>([&](auto k2) { x[k1 + A * k2] = t[k2]; });
+      }
+    });
+  }
+}
+
+// --------------------------------------------------- line FFT over T threads
+// M = P*Q points shared by T threads (T | P, T | Q). Thread t holds element
+// t + T*i in r[i], i < M/T, both before and after the transform.
+// z: this line's exchange buffer (ZS float2 in shared memory).
+// tw: shared table tw[q*RP + k1] = exp(-2 pi j q k1 / M) (forward sign).
+// Every thread of the block must call fft() the same number of times (it
+// contains two block-wide barriers).
+template <int P_, int Q_, int T_>
+struct Line {
+  static constexpr int P = P_, Q = Q_, T = T_, M = P * Q, E = M / T;
+  static constexpr int QJ = Q / T, PJ = P / T;
+  static constexpr int RP = (P % 2 == 0) ? P + 1 : P;  // odd pitch: conflict-free columns
+  static constexpr int ZS = Q * RP;
+  static_assert(P % T == 0 && Q % T == 0, "T must divide P and Q");
+
+  // Step 1: the Q/T sub-DFTs of length P owned by thread t (q = t + T*j),
+  // twiddled and written to the exchange matrix z[q][k1].
+  // NZP: leading non-zero inputs of each sub-DFT (zero padding).
+  template <bool INV, int NZP = P>
+  DOS_HD static void step1(const float2 (&r)[E], int t, float2* z, const float2* tw) {
+    static_for<0, QJ>([&](auto jj) {
+      constexpr int j = jj;
+      float2 a[P];
+      static_for<0, NZP>([&](auto pp) { a[pp] = r[j + QJ * pp]; });
+      dft<P, INV, NZP, P>(a);
+      const int q = t + T * j;
+      const float2* twq = tw + q * RP;
+      float2* zq = z + q * RP;
+      zq[0] = a[0];
+      static_for<1, P>([&](auto kk) {
+        const float2 w = twq[kk];
+        zq[kk] = INV ? cmulc(a[kk], w) : cmul(a[kk], w);
+      });
+    });
+  }
+  // Step 2: the P/T sub-DFTs of length Q owned by thread t (k1 = t + T*j),
+  // read as columns of z; outputs k1 + P*k2 land in r[j + (P/T)*k2].
+  // NOQ: leading outputs of each sub-DFT that are needed (cropping).
+  template <bool INV, int NOQ = Q>
+  DOS_HD static void step2(float2 (&r)[E], int t, const float2* z) {
+    static_for<0, PJ>([&](auto jj) {
+      constexpr int j = jj;
+      const int k1 = t + T * j;
+      float2 b[Q];
+      static_for<0, Q>([&](auto qq) { b[qq] = z[qq * RP + k1]; });
+      dft<Q, INV, Q, NOQ>(b);
+      static_for<0, NOQ>([&](auto k2) { r[j + PJ * k2] = b[k2]; });
+    });
+  }
+  template <bool INV, int NZP = P, int NOQ = Q>
+  __device__ static __forceinline__ void fft(float2 (&r)[E], int t, float2* z, const float2* tw) {
+    step1<INV, NZP>(r, t, z, tw);
+    __syncthreads();
+    step2<INV, NOQ>(r, t, z);
+    __syncthreads();
+  }
+};
+
+}  // namespace dos

@@ -1,0 +1,83 @@
+// dos_internal.h - declarations shared by the CUDA translation units of libdos.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace dos {
+
+// Per-channel constants of Eq. 1 (one wavelength), built on the device at create.
+struct ChanConst {
+  float a_hi, a_lo;   // (n - n_medium) / lambda as a float pair [cycles per metre]
+  float pc_base;      // phase of the base thickness, frac((n - n_medium) h_base / lambda) [cycles]
+  float amp_k;        // -2 pi kappa / (lambda ln 2): amplitude = exp2(amp_k * h) * amp_base
+  float amp_base;     // exp(-2 pi kappa h_base / lambda)
+  float c_re, c_im;   // c = dt/dh / t = -2 pi (kappa + j (n - n_medium)) / lambda
+  float pad;
+};
+
+// Arguments of one propagation pass (all channels of the context).
+struct PassArgs {
+  float2* S;              // [nw][n][m] spectra of the rows (row pass output / column pass in-out)
+  const float2* Hq;       // [nw][hs][hs] transfer function of this gap, 1/M^2 folded in
+  const float2* arow;     // [m] DFT of one aperture row (lambda independent)
+  const float2* tw;       // [Q*RP] line twiddles exp(-2 pi j q k1 / M)
+  const ChanConst* chan;  // [nw]
+  const float* h;         // [n][n] thickness of this layer
+  float2* ckpt;           // [nw][n][n] incoming field of this layer (checkpoint)
+  float2* o;              // [nw][fov][fov] complex output field
+  float* I;               // [nw][fov][fov] intensity (may be null)
+  const float* dLdI;      // [nw][fov][fov]
+  float* partial;         // [n_chunks][n][n] gradient partials of this layer
+  const float2* fin;      // [nw][n][n] caller field (propagate entry)
+  float2* fout;           // [nw][n][n] caller field (propagate entry)
+  int n, m, nw, fov, of, hs;
+  int in_r0, in_r1;       // column pass: rows that may be non-zero on input
+  int out_r0, out_r1;     // column pass: rows stored on output
+  int chunk;              // channels per block of the adjoint row pass
+  int n_chunks;
+};
+
+// Kernel launchers of one padded size M (one translation unit per M).
+struct PassOps {
+  int m, P, Q, T;
+  int row_lines, col_lines;
+  cudaError_t (*col)(const PassArgs&, bool adjoint, bool aperture, cudaStream_t);
+  cudaError_t (*row_fwd)(const PassArgs&, bool save, cudaStream_t);
+  cudaError_t (*row_out)(const PassArgs&, cudaStream_t);
+  cudaError_t (*row_seed)(const PassArgs&, cudaStream_t);
+  cudaError_t (*row_adj)(const PassArgs&, bool first, cudaStream_t);
+  cudaError_t (*row_in)(const PassArgs&, cudaStream_t);    // caller field -> row spectra
+  cudaError_t (*row_back)(const PassArgs&, cudaStream_t);  // row spectra -> caller field
+};
+
+const PassOps* pass_ops_for_m(int m);
+int supported_m_list(int* out, int cap);
+
+// Setup kernels (dos_setup.cu).
+cudaError_t launch_htable(float2* Hq, const double* d_lambda, int nw, double z, double n_medium,
+                          double pitch, int m, int hs, int evanescent, cudaStream_t s);
+cudaError_t launch_arow(float2* arow, int m, int offset, int width, cudaStream_t s);
+cudaError_t launch_twiddles(float2* tw, int P, int Q, int RP, int m, cudaStream_t s);
+cudaError_t launch_chan(ChanConst* chan, const double* d_lambda, const double* d_nidx,
+                        const double* d_kappa, int nw, double n_medium, double h_base,
+                        cudaStream_t s);
+
+// Objective kernels (dos_loss.cu).
+struct LossStats {
+  double sse;      // sum_p (I - T)^2
+  double sigma;    // sum I T / sum I^2
+  double sse_sc;   // sum_p (sigma I - T)^2
+  double pad;
+};
+cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov2,
+                              cudaStream_t s);
+cudaError_t launch_loss_final(const LossStats* st, int nw, int fov2, double norm, int mode,
+                              double* d_loss, float* d_psnr, cudaStream_t s);
+cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, float* dLdI, int nw,
+                        int fov2, double norm, int mode, cudaStream_t s);
+cudaError_t launch_grad_reduce(const float* partial, float* grad, int n_chunks, size_t count,
+                               size_t chunk_stride, cudaStream_t s);
+
+}  // namespace dos

@@ -1,0 +1,134 @@
+// dos_loss.cu - objective, quality metric and the gradient reduction.
+//
+// Section 2: the design minimises an MSE between the output intensity O_w of
+// every channel and its target; reconstruction quality is a PSNR.  All sums
+// run in FP64 in a fixed order (per-thread strided partial sums, then a
+// shared-memory tree), so results are reproducible bit for bit.
+#include "dos_internal.h"
+
+#include "../../include/dos.h"
+
+namespace dos {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ float intensity(float2 o) { return fmaf(o.x, o.x, o.y * o.y); }
+
+// per channel: sum (I-T)^2, sigma = sum I T / sum I^2, sum (sigma I - T)^2
+__global__ void __launch_bounds__(kRedThreads) k_loss_stats(const float2* __restrict__ o,
+                                                            const float* __restrict__ T,
+                                                            LossStats* __restrict__ st, int fov2) {
+  __shared__ double sh[kRedThreads];
+  const int w = blockIdx.x;
+  const float2* ow = o + (size_t)w * fov2;
+  const float* tw = T + (size_t)w * fov2;
+  double sse = 0, sit = 0, sii = 0;
+  for (int p = threadIdx.x; p < fov2; p += kRedThreads) {
+    const double I = intensity(ow[p]);
+    const double t = tw[p];
+    sse += (I - t) * (I - t);
+    sit += I * t;
+    sii += I * I;
+  }
+  sse = block_sum(sse, sh);
+  sit = block_sum(sit, sh);
+  sii = block_sum(sii, sh);
+  const double sigma = sii > 0.0 ? sit / sii : 0.0;
+  double ssc = 0;
+  for (int p = threadIdx.x; p < fov2; p += kRedThreads) {
+    const double d = sigma * (double)intensity(ow[p]) - (double)tw[p];
+    ssc += d * d;
+  }
+  ssc = block_sum(ssc, sh);
+  if (threadIdx.x == 0) {
+    LossStats s;
+    s.sse = sse;
+    s.sigma = sigma;
+    s.sse_sc = ssc;
+    s.pad = 0;
+    st[w] = s;
+  }
+}
+
+cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov2,
+                              cudaStream_t s) {
+  k_loss_stats<<<nw, kRedThreads, 0, s>>>(o, T, st, fov2);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_loss_final(const LossStats* __restrict__ st, int nw,
+                                                            int fov2, double norm, int mode,
+                                                            double* __restrict__ d_loss,
+                                                            float* __restrict__ psnr) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0;
+  for (int w = threadIdx.x; w < nw; w += kRedThreads) {
+    const LossStats s = st[w];
+    acc += mode == DOS_LOSS_MSE_SCALED ? s.sse_sc : s.sse;
+    if (psnr) psnr[w] = (float)(10.0 * log10((double)fov2 / s.sse_sc));
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) *d_loss = acc / norm;
+}
+
+cudaError_t launch_loss_final(const LossStats* st, int nw, int fov2, double norm, int mode,
+                              double* d_loss, float* d_psnr, cudaStream_t s) {
+  k_loss_final<<<1, kRedThreads, 0, s>>>(st, nw, fov2, norm, mode, d_loss, d_psnr);
+  return cudaGetLastError();
+}
+
+// dL/dI: 2 (I - T) / norm, or 2 sigma (sigma I - T) / norm for the scaled loss
+__global__ void k_dldi(const float2* __restrict__ o, const float* __restrict__ T,
+                       const LossStats* __restrict__ st, float* __restrict__ dLdI, size_t total,
+                       int fov2, double norm, int mode) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const double I = intensity(o[i]);
+  double g;
+  if (mode == DOS_LOSS_MSE_SCALED) {
+    const double sg = st[i / fov2].sigma;
+    g = 2.0 * sg * (sg * I - (double)T[i]) / norm;
+  } else {
+    g = 2.0 * (I - (double)T[i]) / norm;
+  }
+  dLdI[i] = (float)g;
+}
+
+cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, float* dLdI, int nw,
+                        int fov2, double norm, int mode, cudaStream_t s) {
+  const size_t total = (size_t)nw * fov2;
+  k_dldi<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(o, T, st, dLdI, total, fov2, norm, mode);
+  return cudaGetLastError();
+}
+
+// grad[g] = sum over chunks c (in order) of partial[layer(g)][c][pixel(g)]
+__global__ void k_grad_reduce(const float* __restrict__ partial, float* __restrict__ grad,
+                              int n_chunks, size_t count, size_t n2) {
+  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  const size_t layer = g / n2, px = g % n2;
+  const float* p = partial + layer * n_chunks * n2 + px;
+  double acc = 0.0;
+  for (int c = 0; c < n_chunks; ++c) acc += (double)p[(size_t)c * n2];
+  grad[g] = (float)acc;
+}
+
+cudaError_t launch_grad_reduce(const float* partial, float* grad, int n_chunks, size_t count,
+                               size_t n2, cudaStream_t s) {
+  k_grad_reduce<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(partial, grad, n_chunks, count, n2);
+  return cudaGetLastError();
+}
+
+}  // namespace dos

@@ -1,0 +1,400 @@
+// dos_pass.cuh - row and column passes of the angular-spectrum cascade.
+//
+// One free-space gap (Eq. 4-5 realised as P_z(u) = crop(IDFT(H * DFT(pad u))))
+// is split into a row pass and a column pass over an [nw][n][m] buffer S of
+// row spectra.  The N x N layer occupies rows/columns [0, N) of the padded
+// M x M grid; by shift invariance of circular convolution this equals the
+// centred placement.
+//
+//   row pass    : per (channel, row): inverse row DFT of the previous column
+//                 pass (-> field, cropped to N), modulation by the layer's
+//                 transmission t (Eq. 1-2) or the adjoint chain, zero pad,
+//                 forward row DFT.  One read and one write of a row of M.
+//   column pass : per (channel, column tile): forward column DFT of the
+//                 N non-zero rows, multiply by H (conj H for the adjoint),
+//                 inverse column DFT, keep the rows that are needed.
+//
+// Each kernel keeps every element of a line in registers across both of its
+// transforms; the only shared-memory traffic is the one exchange inside each
+// line DFT.
+#pragma once
+
+#include "dos_fft.cuh"
+#include "dos_internal.h"
+
+namespace dos {
+
+// Transmission of Eq. 1 at thickness h (Eq. 2 base folded into the constants):
+// t = exp(-2 pi kappa h / lambda) exp(-j 2 pi (n - n_med) h / lambda).
+// The phase in cycles is formed as a float-pair product (exact product error
+// by fma) and reduced modulo 1 before sincospi, which keeps ~1e-7 cycle
+// accuracy for any thickness.
+__device__ __forceinline__ float2 transmission(float h, const ChanConst& cc) {
+  const float p = cc.a_hi * h;
+  float e = fmaf(cc.a_hi, h, -p);
+  e = fmaf(cc.a_lo, h, e);
+  float f = (p - rintf(p)) + (e + cc.pc_base);
+  f -= rintf(f);
+  float s, c;
+  sincospif(2.0f * f, &s, &c);
+  const float amp = exp2f(cc.amp_k * h) * cc.amp_base;
+  return make_float2(amp * c, -amp * s);
+}
+
+template <class LF>
+struct Pass {
+  static constexpr int T = LF::T, E = LF::E, M = LF::M;
+  static constexpr int ROWL = 16;  // rows per block in the row passes
+  static constexpr int COLL = 16;  // columns per block in the column pass
+  static constexpr int ZL = LF::ZS + 1;  // odd stride between the lines' exchange buffers
+  static constexpr size_t smem_bytes(int lines) { return sizeof(float2) * (LF::ZS + (size_t)lines * ZL); }
+
+  __device__ static __forceinline__ void load_tw(float2* tw, const float2* g) {
+    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = g[i];
+    __syncthreads();
+  }
+
+  // ------------------------------------------------------------ column pass
+  template <bool ADJ, bool APERTURE>
+  __device__ static void col(const PassArgs& a) {
+    extern __shared__ float2 smem[];
+    float2* tw = smem;
+    const int l = threadIdx.x % COLL;
+    const int t = threadIdx.x / COLL;
+    float2* z = smem + LF::ZS + l * ZL;
+    load_tw(tw, a.tw);
+    const int w = blockIdx.y;
+    const int c = blockIdx.x * COLL + l;
+    const bool ok = c < M;
+    const int cc = ok ? c : 0;
+    float2 r[E];
+    if constexpr (APERTURE) {
+      // spectrum of the square aperture: Arow[ky] * Arow[kx]
+      const float2 ac = a.arow[cc];
+#pragma unroll
+      for (int i = 0; i < E; ++i) r[i] = cmul(a.arow[t + T * i], ac);
+    } else {
+      const float2* src = a.S + (size_t)w * a.n * M + cc;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int row = t + T * i;
+        r[i] = (ok && row >= a.in_r0 && row < a.in_r1) ? src[(size_t)row * M] : czero();
+      }
+      LF::template fft<false>(r, t, z, tw);
+    }
+    const float2* Hw = a.Hq + (size_t)w * a.hs * a.hs;
+    const int bc = min(cc, M - cc);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int k = t + T * i;
+      const float2 hv = Hw[min(k, M - k) * a.hs + bc];
+      r[i] = ADJ ? cmulc(r[i], hv) : cmul(r[i], hv);
+    }
+    LF::template fft<true>(r, t, z, tw);
+    float2* dst = a.S + (size_t)w * a.n * M + cc;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int row = t + T * i;
+      if (ok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
+    }
+  }
+
+  // ------------------------------------------------------------- row passes
+  struct RowCtx {
+    int l, t;
+    float2* z;
+    float2* tw;
+  };
+  __device__ static __forceinline__ RowCtx row_ctx(const PassArgs& a) {
+    extern __shared__ float2 smem[];
+    RowCtx rc;
+    rc.l = threadIdx.x / T;
+    rc.t = threadIdx.x % T;
+    rc.tw = smem;
+    rc.z = smem + LF::ZS + rc.l * ZL;
+    load_tw(rc.tw, a.tw);
+    return rc;
+  }
+
+  // forward, layer l: IDFT -> v (crop) -> [checkpoint] -> t*v -> pad -> DFT
+  template <bool SAVE>
+  __device__ static void row_fwd(const PassArgs& a) {
+    const RowCtx rc = row_ctx(a);
+    const int t = rc.t;
+    const int w = blockIdx.y;
+    const int row = blockIdx.x * ROWL + rc.l;
+    const bool ok = row < a.n;
+    const int rr = ok ? row : 0;
+    float2* srow = a.S + ((size_t)w * a.n + rr) * M;
+    float2 r[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
+    LF::template fft<true>(r, t, rc.z, rc.tw);
+    const ChanConst cc = a.chan[w];
+    const float* hrow = a.h + (size_t)rr * a.n;
+    float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = t + T * i;
+      if (x < a.n) {
+        const float2 v = r[i];
+        if (SAVE && ok) ck[x] = v;
+        r[i] = cmul(transmission(hrow[x], cc), v);
+      } else {
+        r[i] = czero();
+      }
+    }
+    LF::template fft<false>(r, t, rc.z, rc.tw);
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+    }
+  }
+
+  // output plane: IDFT of the FOV rows -> o (complex) and I = |o|^2
+  __device__ static void row_out(const PassArgs& a) {
+    const RowCtx rc = row_ctx(a);
+    const int t = rc.t;
+    const int w = blockIdx.y;
+    const int fr = blockIdx.x * ROWL + rc.l;  // FOV row
+    const bool ok = fr < a.fov;
+    const int row = a.of + (ok ? fr : 0);
+    const float2* srow = a.S + ((size_t)w * a.n + row) * M;
+    float2 r[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
+    LF::template fft<true>(r, t, rc.z, rc.tw);
+    if (ok) {
+      float2* orow = a.o + ((size_t)w * a.fov + fr) * a.fov;
+      float* irow = a.I ? a.I + ((size_t)w * a.fov + fr) * a.fov : nullptr;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i - a.of;
+        if (x >= 0 && x < a.fov) {
+          orow[x] = r[i];
+          if (irow) irow[x] = fmaf(r[i].x, r[i].x, r[i].y * r[i].y);
+        }
+      }
+    }
+  }
+
+  // adjoint seed: grad_o = 2 dL/dI o on the FOV, zero elsewhere -> DFT of the FOV rows
+  __device__ static void row_seed(const PassArgs& a) {
+    const RowCtx rc = row_ctx(a);
+    const int t = rc.t;
+    const int w = blockIdx.y;
+    const int fr = blockIdx.x * ROWL + rc.l;
+    const bool ok = fr < a.fov;
+    const int frr = ok ? fr : 0;
+    const float2* orow = a.o + ((size_t)w * a.fov + frr) * a.fov;
+    const float* grow = a.dLdI + ((size_t)w * a.fov + frr) * a.fov;
+    float2 r[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = t + T * i - a.of;
+      r[i] = (ok && x >= 0 && x < a.fov) ? cscale(orow[x], 2.0f * grow[x]) : czero();
+    }
+    LF::template fft<false>(r, t, rc.z, rc.tw);
+    if (ok) {
+      float2* srow = a.S + ((size_t)w * a.n + a.of + fr) * M;
+#pragma unroll
+      for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+    }
+  }
+
+  // adjoint, layer l, for a chunk of channels:
+  //   IDFT -> grad_u (crop); u = t v from the checkpoint;
+  //   dL/dh += Re(conj(grad_u) c u) (accumulated over the chunk in registers);
+  //   grad_v = conj(t) grad_u -> pad -> DFT (skipped for the first layer)
+  template <bool FIRST>
+  __device__ static void row_adj(const PassArgs& a) {
+    const RowCtx rc = row_ctx(a);
+    const int t = rc.t;
+    const int row = blockIdx.x * ROWL + rc.l;
+    const bool ok = row < a.n;
+    const int rr = ok ? row : 0;
+    const int w0 = blockIdx.y * a.chunk;
+    const int w1 = min(a.nw, w0 + a.chunk);
+    const float* hrow = a.h + (size_t)rr * a.n;
+    float g[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) g[i] = 0.f;
+    for (int w = w0; w < w1; ++w) {
+      float2* srow = a.S + ((size_t)w * a.n + rr) * M;
+      const float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
+      float2 r[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
+      LF::template fft<true>(r, t, rc.z, rc.tw);
+      const ChanConst cc = a.chan[w];
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i;
+        if (x < a.n) {
+          const float2 au = r[i];
+          const float2 tt = transmission(hrow[x], cc);
+          const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
+          g[i] = fmaf(au.x, cu.x, fmaf(au.y, cu.y, g[i]));
+          r[i] = cmulc(au, tt);
+        } else {
+          r[i] = czero();
+        }
+      }
+      if constexpr (!FIRST) {
+        LF::template fft<false>(r, t, rc.z, rc.tw);
+        if (ok) {
+#pragma unroll
+          for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+        }
+      }
+    }
+    if (ok) {
+      float* prow = a.partial + ((size_t)blockIdx.y * a.n + row) * a.n;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i;
+        if (x < a.n) prow[x] = g[i];
+      }
+    }
+  }
+
+  // caller field -> pad -> row DFT (dos_propagate)
+  __device__ static void row_in(const PassArgs& a) {
+    const RowCtx rc = row_ctx(a);
+    const int t = rc.t;
+    const int w = blockIdx.y;
+    const int row = blockIdx.x * ROWL + rc.l;
+    const bool ok = row < a.n;
+    const int rr = ok ? row : 0;
+    const float2* frow = a.fin + ((size_t)w * a.n + rr) * a.n;
+    float2 r[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = t + T * i;
+      r[i] = x < a.n ? frow[x] : czero();
+    }
+    LF::template fft<false>(r, t, rc.z, rc.tw);
+    if (ok) {
+      float2* srow = a.S + ((size_t)w * a.n + row) * M;
+#pragma unroll
+      for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+    }
+  }
+
+  // row spectra -> IDFT -> crop -> caller field (dos_propagate)
+  __device__ static void row_back(const PassArgs& a) {
+    const RowCtx rc = row_ctx(a);
+    const int t = rc.t;
+    const int w = blockIdx.y;
+    const int row = blockIdx.x * ROWL + rc.l;
+    const bool ok = row < a.n;
+    const int rr = ok ? row : 0;
+    const float2* srow = a.S + ((size_t)w * a.n + rr) * M;
+    float2 r[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
+    LF::template fft<true>(r, t, rc.z, rc.tw);
+    if (ok) {
+      float2* frow = a.fout + ((size_t)w * a.n + row) * a.n;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i;
+        if (x < a.n) frow[x] = r[i];
+      }
+    }
+  }
+};
+
+// ------------------------------------------------------------------ kernels
+template <class LF, bool ADJ, bool APERTURE>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL) k_col(PassArgs a) {
+  Pass<LF>::template col<ADJ, APERTURE>(a);
+}
+template <class LF, bool SAVE>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_fwd(PassArgs a) {
+  Pass<LF>::template row_fwd<SAVE>(a);
+}
+template <class LF>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_out(PassArgs a) {
+  Pass<LF>::row_out(a);
+}
+template <class LF>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_seed(PassArgs a) {
+  Pass<LF>::row_seed(a);
+}
+template <class LF, bool FIRST>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_adj(PassArgs a) {
+  Pass<LF>::template row_adj<FIRST>(a);
+}
+template <class LF>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_in(PassArgs a) {
+  Pass<LF>::row_in(a);
+}
+template <class LF>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_back(PassArgs a) {
+  Pass<LF>::row_back(a);
+}
+
+template <typename K>
+static cudaError_t launch_k(K kernel, dim3 grid, int threads, size_t smem, const PassArgs& a,
+                            cudaStream_t s) {
+  if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kernel<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class LF>
+struct PassLaunch {
+  using PS = Pass<LF>;
+  static constexpr int RT = LF::T * PS::ROWL;
+  static constexpr int CT = LF::T * PS::COLL;
+  static int row_blocks(int rows) { return (rows + PS::ROWL - 1) / PS::ROWL; }
+
+  static cudaError_t col(const PassArgs& a, bool adj, bool ap, cudaStream_t s) {
+    const dim3 g((LF::M + PS::COLL - 1) / PS::COLL, a.nw);
+    const size_t sm = PS::smem_bytes(PS::COLL);
+    if (ap) return adj ? launch_k(k_col<LF, true, true>, g, CT, sm, a, s)
+                       : launch_k(k_col<LF, false, true>, g, CT, sm, a, s);
+    return adj ? launch_k(k_col<LF, true, false>, g, CT, sm, a, s)
+               : launch_k(k_col<LF, false, false>, g, CT, sm, a, s);
+  }
+  static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
+    const dim3 g(row_blocks(a.n), a.nw);
+    const size_t sm = PS::smem_bytes(PS::ROWL);
+    return save ? launch_k(k_row_fwd<LF, true>, g, RT, sm, a, s)
+                : launch_k(k_row_fwd<LF, false>, g, RT, sm, a, s);
+  }
+  static cudaError_t row_out(const PassArgs& a, cudaStream_t s) {
+    return launch_k(k_row_out<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+  }
+  static cudaError_t row_seed(const PassArgs& a, cudaStream_t s) {
+    return launch_k(k_row_seed<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+  }
+  static cudaError_t row_adj(const PassArgs& a, bool first, cudaStream_t s) {
+    const dim3 g(row_blocks(a.n), a.n_chunks);
+    const size_t sm = PS::smem_bytes(PS::ROWL);
+    return first ? launch_k(k_row_adj<LF, true>, g, RT, sm, a, s)
+                 : launch_k(k_row_adj<LF, false>, g, RT, sm, a, s);
+  }
+  static cudaError_t row_in(const PassArgs& a, cudaStream_t s) {
+    return launch_k(k_row_in<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+  }
+  static cudaError_t row_back(const PassArgs& a, cudaStream_t s) {
+    return launch_k(k_row_back<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+  }
+  static const PassOps* ops() {
+    static const PassOps o = {LF::M, LF::P, LF::Q, LF::T, PS::ROWL, PS::COLL,
+                              &col, &row_fwd, &row_out, &row_seed, &row_adj, &row_in, &row_back};
+    return &o;
+  }
+};
+
+}  // namespace dos
+
+// One translation unit per padded size: defines dos::pass_ops_<M>().
+#define DOS_DEFINE_PASS_OPS(M_, P_, Q_, T_)                                          \
+  namespace dos {                                                                    \
+  const PassOps* pass_ops_##M_() { return PassLaunch<Line<P_, Q_, T_>>::ops(); }     \
+  }

@@ -1,0 +1,101 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol that
+include/dos.h declares, and its host-side validation rejects bad designs
+before touching a GPU.  No compute call is made."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2604_02624_gb300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_2604_02624_gb300 import build
+        build.build()
+    return L.load()
+
+
+def _header_symbols():
+    text = open(os.path.join(ROOT, "include", "dos.h")).read()
+    return sorted(set(re.findall(r"DOS_API\s+[\w\s\*]+?\b(dos_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_exports():
+    assert _header_symbols() == sorted(L.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _header_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_library_hides_internal_symbols(lib):
+    # internal C++ kernels and helpers must not leak into the dynamic symbol table
+    with pytest.raises(AttributeError):
+        getattr(lib, "launch_htable")
+
+
+def test_supported_sizes_are_reported(lib):
+    ms = L.dos_supported_m()
+    for m in (128, 400, 512):
+        assert m in ms
+
+
+def _cfg(**over):
+    lam = np.array([500e-9, 600e-9])
+    keep = {"gaps": np.array([1e-5, 1e-5]), "lam": lam, "nidx": np.array([1.7, 1.7])}
+    c = L.DosConfig()
+    c.n, c.m, c.n_layers, c.n_lambda, c.n_lambda_total = 64, 128, 1, 2, 0
+    c.fov, c.aperture, c.pitch = 32, 0, 3e-7
+    c.gaps = L._dptr(keep["gaps"])
+    c.lambda_ = L._dptr(keep["lam"])
+    c.n_index = L._dptr(keep["nidx"])
+    c.kappa = None
+    c.n_medium, c.h_base, c.evanescent, c.loss, c.path = 1.0, 0.0, 0, 0, 0
+    for k, v in over.items():
+        if isinstance(v, np.ndarray):
+            keep[k] = v
+            v = L._dptr(v)
+        setattr(c, k, v)
+    return c, keep
+
+
+@pytest.mark.parametrize("over,msg", [
+    ({"n": 0}, "n must be"),
+    ({"m": 100}, "not a supported padded size"),
+    ({"m": 32}, "m must be >= n"),
+    ({"n_layers": 0}, "n_layers"),
+    ({"fov": 33}, "fov"),
+    ({"fov": 65}, "fov"),
+    ({"aperture": 31}, "aperture"),
+    ({"pitch": -1.0}, "pitch"),
+    ({"lambda_": np.array([500e-9, -1.0])}, "lambda"),
+    ({"gaps": np.array([1e-5, np.nan])}, "gaps"),
+    ({"n_medium": 0.0}, "n_medium"),
+    ({"evanescent": 7}, "evanescent"),
+    ({"loss": 9}, "loss"),
+    ({"n_lambda_total": 1}, "n_lambda_total"),
+])
+def test_invalid_designs_are_rejected_on_the_host(lib, over, msg):
+    cfg, keep = _cfg(**over)
+    h = ctypes.c_void_p(123)
+    rc = lib.dos_create(ctypes.byref(h), ctypes.byref(cfg), None)
+    assert rc == L.DOS_ERR_ARG
+    assert h.value is None
+    assert msg in L.dos_last_error()
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.dos_create(None, None, None) == L.DOS_ERR_ARG
+    h = ctypes.c_void_p()
+    assert lib.dos_create(ctypes.byref(h), None, None) == L.DOS_ERR_ARG
+    assert lib.dos_forward(None, None, None, 0) == L.DOS_ERR_ARG
+    assert lib.dos_backward(None, None, None, None) == L.DOS_ERR_ARG
+    lib.dos_destroy(None)  # no-op
+    assert lib.dos_workspace_bytes(None) == 0

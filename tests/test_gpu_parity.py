@@ -1,0 +1,258 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Same seeded inputs on both sides; element-by-element comparisons at sizes the
+oracle finishes in seconds (several tiles, ragged tails), and sampled
+channels / subset designs at the full workload sizes.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dos_oracle as O
+from paper_2604_02624_gb300 import workloads as W
+from paper_2604_02624_gb300 import _lib as L
+from paper_2604_02624_gb300.api import DiffractiveStack, DosFunction
+
+from gpu_cases import (TOL_FIELD, TOL_GRAD_FD, TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS,
+                       custom, oracle_model, rel_l2, replace)
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import os
+    if not os.path.exists(L.LIB_PATH):
+        from paper_2604_02624_gb300 import build
+        build.build()
+    L.load()
+    torch.cuda.set_device(DEV)
+
+
+def _stack(w, **kw):
+    return DiffractiveStack.from_workload(w, device=DEV, **kw)
+
+
+def _t(x, dtype=torch.float32):
+    return torch.tensor(np.asarray(x), dtype=dtype, device=DEV)
+
+
+def _np(x):
+    return x.detach().cpu().numpy()
+
+
+def _rand_fields(rng, nw, n):
+    return rng.standard_normal((nw, n, n)) + 1j * rng.standard_normal((nw, n, n))
+
+
+# ------------------------------------------------------------ single propagation
+@pytest.mark.parametrize("n,m,adj,evan", [
+    (64, 128, False, "decay"), (64, 128, True, "decay"), (200, 400, False, "decay"),
+    (200, 400, True, "zero"), (256, 512, False, "decay"), (256, 512, True, "decay"),
+    (50, 128, True, "decay"), (100, 200, False, "zero"), (1, 16, False, "decay"),
+    (64, 64, False, "decay"), (7, 16, True, "decay"), (30, 32, False, "decay"),
+])
+def test_propagate_matches_oracle(n, m, adj, evan):
+    w = custom(n, m, 1, [500, 587, 740], 40, n, name="prop")
+    rng = np.random.default_rng(n * 1000 + m)
+    f = _rand_fields(rng, w.n_lambda, n).astype(np.complex64)
+    st = _stack(w, evanescent=evan)
+    got = _np(st.propagate(torch.tensor(f, device=DEV), 0, adj)).astype(np.complex128)
+    ref = np.stack([(O.propagate_adjoint if adj else O.propagate)(
+        f[i].astype(np.complex128), O.transfer_function(w.lambdas[i], w.gaps[0], m, w.pitch, 1.0, evan))
+        for i in range(w.n_lambda)])
+    assert rel_l2(got, ref) <= TOL_FIELD
+    st.close()
+
+
+# ------------------------------------------------------------ forward model
+def _forward_case(w, evan="decay", loss="mse"):
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    st = _stack(w, evanescent=evan, loss=loss)
+    hd = _t(h)
+    I = st.forward(hd)
+    o = st.output_field()
+    ref = O.forward(h, **{k: v for k, v in oracle_model(w, evan).items()})
+    return st, h, T, hd, I, o, ref
+
+
+@pytest.mark.parametrize("name", ["tiny", "small"])
+def test_forward_fields_and_intensity(name):
+    w = W.workload(name)
+    st, h, T, hd, I, o, ref = _forward_case(w)
+    assert rel_l2(_np(o).astype(np.complex128), ref["o"]) <= TOL_FIELD
+    assert rel_l2(_np(I).astype(np.float64), ref["I"]) <= TOL_INTENSITY
+    for l in range(1, w.n_layers + 1):
+        v = _np(st.layer_field(l)).astype(np.complex128)
+        assert rel_l2(v, ref["v"][:, l - 1]) <= TOL_FIELD, l
+    assert st.last_launch_count == 2 * w.n_layers + 2
+    st.close()
+
+
+def test_forward_ragged_and_options():
+    """N = 100 in M = 200 (ragged row blocks and column tiles), three layers with
+    unequal gaps, a medium of index 1.33, base thickness, per-channel
+    dispersion and loss, zeroed evanescent bins, full-window aperture."""
+    lam = [455, 530, 610, 700, 745]
+    w = custom(100, 200, 3, lam, [30, 55, 30, 80], 40, aperture=100,
+               n_index=[1.52, 1.51, 1.50, 1.495, 1.49], kappa=[0.02, 0.0, 0.01, 0.03, 0.0],
+               n_medium=1.33, h_base=120e-9, name="ragged")
+    st, h, T, hd, I, o, ref = _forward_case(w, evan="zero")
+    assert rel_l2(_np(o).astype(np.complex128), ref["o"]) <= TOL_FIELD
+    assert rel_l2(_np(I).astype(np.float64), ref["I"]) <= TOL_INTENSITY
+    st.close()
+
+
+def test_forward_single_pixel_layer():
+    w = custom(1, 16, 2, [500, 700], 3, 1, name="one-pixel")
+    st, h, T, hd, I, o, ref = _forward_case(w)
+    assert rel_l2(_np(o).astype(np.complex128), ref["o"]) <= TOL_FIELD
+    st.close()
+
+
+# ------------------------------------------------------------ objective
+@pytest.mark.parametrize("loss", ["mse", "mse_scaled"])
+def test_loss_psnr_and_dldi(loss):
+    w = W.workload("small")
+    st, h, T, hd, I, o, ref = _forward_case(w, loss=loss)
+    val, psnr, dLdI = st.loss(_t(T))
+    L_ref, psnr_ref, dLdI_ref = O.mse_loss(ref["I"], T, scaled=(loss == "mse_scaled"))
+    assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref)
+    assert np.max(np.abs(_np(psnr) - psnr_ref)) <= 1e-3
+    assert rel_l2(_np(dLdI).astype(np.float64), dLdI_ref) <= TOL_INTENSITY
+    st.close()
+
+
+# ------------------------------------------------------------ gradient
+@pytest.mark.parametrize("name,loss", [("tiny", "mse"), ("small", "mse"), ("small", "mse_scaled")])
+def test_gradient_matches_oracle_and_finite_differences(name, loss):
+    w = W.workload(name)
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    st = _stack(w, loss=loss)
+    hd = _t(h)
+    st.forward(hd)
+    _, _, dLdI = st.loss(_t(T))
+    g = _np(st.backward(hd, dLdI)).astype(np.float64)
+    model = oracle_model(w)
+    L_ref, _, g_ref, _ = O.loss_and_grad(h, T, scaled=(loss == "mse_scaled"), **model)
+    assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
+    c = w.n // 2
+    pixels = [(0, c, c), (w.n_layers - 1, c - 7, c + 11), (0, c + 5, c - 9)]
+    fd = O.finite_difference(h, T, pixels, 1e-4 * w.lambda_mean, scaled=(loss == "mse_scaled"), **model)
+    got = np.array([g[p] for p in pixels])
+    assert np.max(np.abs(got - fd) / np.abs(fd)) <= TOL_GRAD_FD, (got, fd)
+    st.close()
+
+
+def test_autograd_function_composes_with_torch_loss():
+    """A torch objective of the intensities back-propagates through DosFunction
+    (dos_backward) to the FP64 oracle gradient of the same objective."""
+    w = W.workload("tiny")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    st = _stack(w)
+    hd = _t(h).requires_grad_(True)
+    I = DosFunction.apply(hd, st)
+    Td = _t(T)
+    loss = ((I - Td) ** 2).mean()
+    loss.backward()
+    L_ref, _, g_ref, _ = O.loss_and_grad(h, T, **oracle_model(w))
+    assert abs(loss.item() - L_ref) <= TOL_LOSS * L_ref
+    assert rel_l2(_np(hd.grad).astype(np.float64), g_ref) <= TOL_GRAD_ORACLE
+    st.close()
+
+
+def test_backward_is_bitwise_deterministic():
+    w = W.workload("small")
+    h = _t(W.thickness(w, 0))
+    st = _stack(w)
+    st.forward(h)
+    _, _, g = st.loss(_t(W.targets(w, 1)))
+    a = st.backward(h, g).clone()
+    b = st.backward(h, g).clone()
+    assert torch.equal(a, b)
+    st.close()
+
+
+def test_state_errors():
+    w = W.workload("tiny")
+    st = _stack(w)
+    h = _t(W.thickness(w, 0))
+    with pytest.raises(L.DosError) as e:
+        st.backward(h, torch.zeros((w.n_lambda, w.fov, w.fov), device=DEV))
+    assert e.value.code == L.DOS_ERR_STATE
+    with pytest.raises(L.DosError) as e:
+        st.loss(_t(W.targets(w, 1)))
+    assert e.value.code == L.DOS_ERR_STATE
+    st.forward(h, save_for_backward=False)
+    with pytest.raises(L.DosError) as e:
+        st.backward(h, torch.zeros((w.n_lambda, w.fov, w.fov), device=DEV))
+    assert e.value.code == L.DOS_ERR_STATE
+    st.close()
+
+
+# ------------------------------------------------------------ full workload sizes
+@pytest.mark.parametrize("name,count", [("massive", 5), ("precision", 3), ("batched", 4)])
+def test_full_size_forward_on_sampled_channels(name, count):
+    """All channels on the GPU in the bench's launch configuration; the oracle
+    checks evenly spread channels (every channel is independent)."""
+    w = W.workload(name)
+    h = W.thickness(w, 0)
+    st = _stack(w)
+    I = st.forward(_t(h), save_for_backward=False)
+    o = st.output_field()
+    idx = W.subset_indices(w.n_lambda, count)
+    ws = w.subset(idx)
+    ref = O.forward(h, keep_fields=False, **oracle_model(ws))
+    assert rel_l2(_np(o[idx]).astype(np.complex128), ref["o"]) <= TOL_FIELD
+    assert rel_l2(_np(I[idx]).astype(np.float64), ref["I"]) <= TOL_INTENSITY
+    st.close()
+
+
+@pytest.mark.parametrize("name", ["massive", "precision"])
+def test_full_geometry_gradient_on_channel_subset(name):
+    """Gradient of the full geometry on a 16-channel subset design (the same
+    layers, gaps and grid), against the FP64 oracle."""
+    w = W.workload(name)
+    ws = w.subset(W.subset_indices(w.n_lambda, 16))
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)[W.subset_indices(w.n_lambda, 16)]
+    st = _stack(ws)
+    hd = _t(h)
+    st.forward(hd)
+    _, _, dLdI = st.loss(_t(T))
+    g = _np(st.backward(hd, dLdI)).astype(np.float64)
+    _, _, g_ref, _ = O.loss_and_grad(h, T, **oracle_model(ws))
+    assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
+    st.close()
+
+
+def test_full_size_gradient_is_the_sum_of_channel_shards():
+    """At 4096 channels the gradient equals the sum of the gradients of two
+    channel shards that share the loss normalisation (the property that makes
+    wavelength sharding across GPUs exact)."""
+    w = W.workload("massive")
+    h = _t(W.thickness(w, 0))
+    T = W.targets(w, 1)
+    st = _stack(w)
+    st.forward(h)
+    L_full, _, dLdI = st.loss(_t(T))
+    g_full = st.backward(h, dLdI).clone()
+    st.close()
+    half = w.n_lambda // 2
+    g_sum = torch.zeros_like(g_full)
+    L_sum = 0.0
+    for lo, hi in ((0, half), (half, w.n_lambda)):
+        ws = w.subset(np.arange(lo, hi))
+        s = _stack(ws, n_lambda_total=w.n_lambda)
+        s.forward(h)
+        Ls, _, dl = s.loss(_t(T[lo:hi]))
+        g_sum += s.backward(h, dl)
+        L_sum += Ls
+        s.close()
+    assert abs(L_sum - L_full) <= 1e-9 * abs(L_full)
+    assert rel_l2(_np(g_sum).astype(np.float64), _np(g_full).astype(np.float64)) <= 1e-5
