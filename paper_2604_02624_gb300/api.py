@@ -113,6 +113,7 @@ class DiffractiveStack:
     # ------------------------------------------------------------------ compute
     def forward(self, h: torch.Tensor, save_for_backward: bool = True,
                 out: Optional[torch.Tensor] = None, want_intensity: bool = True):
+        h = h.contiguous()
         _need(h, torch.float32, (self.n_layers, self.n, self.n), "h", self.device)
         I = None
         if want_intensity:
@@ -125,6 +126,7 @@ class DiffractiveStack:
 
     def loss(self, T: torch.Tensor, read: bool = True, psnr: bool = True, grad: bool = True):
         """Returns (loss or None, psnr[N_w] or None, dL/dI or None)."""
+        T = T.contiguous()
         _need(T, torch.float32, (self.n_lambda, self.fov, self.fov), "T", self.device)
         p = torch.empty(self.n_lambda, dtype=torch.float32, device=self.device) if psnr else None
         g = torch.empty_like(T) if grad else None
@@ -138,6 +140,8 @@ class DiffractiveStack:
         return L.dos_read_loss(self._ctx)
 
     def backward(self, h: torch.Tensor, dLdI: torch.Tensor, out: Optional[torch.Tensor] = None):
+        h = h.contiguous()
+        dLdI = dLdI.contiguous()
         _need(h, torch.float32, (self.n_layers, self.n, self.n), "h", self.device)
         _need(dLdI, torch.float32, (self.n_lambda, self.fov, self.fov), "dLdI", self.device)
         g = out if out is not None else torch.empty_like(h)
@@ -159,6 +163,7 @@ class DiffractiveStack:
         return v
 
     def propagate(self, field: torch.Tensor, gap: int, adjoint: bool = False) -> torch.Tensor:
+        field = field.contiguous()
         _need(field, torch.complex64, (self.n_lambda, self.n, self.n), "field", self.device)
         out = torch.empty_like(field)
         self._bind()

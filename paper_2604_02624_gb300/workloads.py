@@ -161,7 +161,7 @@ def targets(w: Workload, seed: int = 1) -> np.ndarray:
     else:
         low = _box3_inbounds(rng.uniform(0.0, 1.0, size=(w.n_lambda, s, s)))
     t = _upsample_nearest(low, w.fov)
-    return t.astype(np.float32).astype(np.float64)
+    return np.ascontiguousarray(t.astype(np.float32).astype(np.float64))
 
 
 def subset_indices(n_lambda: int, count: int) -> np.ndarray:
