@@ -151,6 +151,39 @@ DOS_API int dos_forward(dos_ctx *ctx, const float *d_h, float *d_I, int save_for
 DOS_API int dos_loss(dos_ctx *ctx, const float *d_T, double *h_loss, float *d_psnr,
                      float *d_dLdI);
 
+/*
+ * Largest n_lambda that dos_loss_noalloc accepts: its scratch is a fixed
+ * array of DOS_NOALLOC_MAX_LAMBDA per-channel records of 32 bytes (2 MiB)
+ * plus one double, held by every GPU that loads this library until exit.
+ */
+#define DOS_NOALLOC_MAX_LAMBDA 65536
+
+/*
+ * Scoring without any memory allocation (the paper has no counterpart: this
+ * serves callers that cannot allocate device memory, e.g. code inside a
+ * framework that owns all device memory through its own pool or runs under a
+ * fixed budget, or a path where a cudaMalloc would stall the device).
+ * Computes what dos_loss computes, from caller intensities instead of a
+ * context, using only a fixed-size scratch array in the library itself.
+ *   d_I, d_T  [n_lambda][fov][fov] float32 intensities and targets.
+ *   n_lambda  1..DOS_NOALLOC_MAX_LAMBDA; larger values fail with DOS_ERR_ARG.
+ *   n_lambda_total, loss: as in dos_config; h_loss, d_psnr, d_dLdI: as in
+ *   dos_loss (h_loss may be NULL; then the loss is not read back).
+ *   cuda_stream  stream of the caller's device (NULL: legacy default stream).
+ * The first call on each device (with that device current) looks up the
+ * scratch address; make that first call before any stream capture.  Calls
+ * allocate nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Every call on a device shares the same scratch, which keeps the contents
+ * of the last call (each call overwrites what it reads, nothing has to be
+ * cleared): calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller.
+ * Errors: DOS_ERR_ARG, DOS_ERR_CUDA, DOS_ERR_UNSUPPORTED (device index > 63);
+ * the message is in dos_last_error().
+ */
+DOS_API int dos_loss_noalloc(const float *d_I, const float *d_T, int n_lambda, int fov,
+                             int n_lambda_total, int loss, double *h_loss, float *d_psnr,
+                             float *d_dLdI, void *cuda_stream);
+
 /* Copies the loss of the last dos_loss to *h_loss (waits for the stream). */
 DOS_API int dos_read_loss(dos_ctx *ctx, double *h_loss);
 

@@ -26,7 +26,10 @@ ERROR_NAMES = {1: "DOS_ERR_ARG", 2: "DOS_ERR_OOM", 3: "DOS_ERR_CUDA", 4: "DOS_ER
 EXPORTS = ("dos_supported_m", "dos_create", "dos_set_stream", "dos_forward", "dos_loss",
            "dos_read_loss", "dos_backward", "dos_output_field", "dos_layer_field",
            "dos_propagate", "dos_set_timing", "dos_kernel_time", "dos_workspace_bytes",
-           "dos_last_launch_count", "dos_path", "dos_destroy", "dos_last_error")
+           "dos_last_launch_count", "dos_path", "dos_destroy", "dos_last_error",
+           "dos_loss_noalloc")
+
+DOS_NOALLOC_MAX_LAMBDA = 65536
 
 KERNEL_KINDS = ("column_forward", "column_adjoint", "row_forward", "row_adjoint", "row_output",
                 "row_seed", "loss", "grad_reduce")
@@ -82,6 +85,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dos_path": (c_int, [p]),
         "dos_destroy": (None, [p]),
         "dos_last_error": (ctypes.c_char_p, []),
+        "dos_loss_noalloc": (c_int, [p, p, c_int, c_int, c_int, c_int, POINTER(c_double), p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -184,3 +188,13 @@ def dos_destroy(ctx: int) -> None:
 def dos_last_error() -> str:
     msg = load().dos_last_error()
     return msg.decode() if msg else ""
+
+
+def dos_loss_noalloc(d_I: int, d_T: int, n_lambda: int, fov: int, n_lambda_total: int, loss: int,
+                     read_loss: bool, d_psnr: int, d_dLdI: int, stream: int):
+    """Scoring with library-owned fixed scratch (no allocation); see include/dos.h."""
+    out = c_double()
+    _check(load().dos_loss_noalloc(d_I, d_T, n_lambda, fov, n_lambda_total, loss,
+                                   ctypes.byref(out) if read_loss else None, d_psnr or None,
+                                   d_dLdI or None, stream or None), "dos_loss_noalloc")
+    return out.value if read_loss else None

@@ -28,6 +28,10 @@ int fail(int code, const std::string& msg) {
 }
 }  // namespace
 
+namespace dos {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace dos
+
 #define DOS_TIMED(ctx, kind, expr, what)    \
   do {                                      \
     (ctx)->timer.begin((kind), (ctx)->stream); \

@@ -53,6 +53,9 @@ struct PassOps {
 };
 
 const PassOps* pass_ops_for_m(int m);
+
+// Message returned by dos_last_error() for the calling thread.
+void set_last_error(const char* msg);
 int supported_m_list(int* out, int cap);
 
 // Setup kernels (dos_setup.cu).
