@@ -75,17 +75,27 @@ enum {
   DOS_LOSS_MSE_SCALED = 1  /* same with sigma_w I, sigma_w = sum I T / sum I^2 per channel */
 };
 
-/* Implementation of the propagation passes. */
+/*
+ * Implementation of the propagation passes.
+ *  DOS_PATH_MULTIPASS: a row pass and a column pass kernel per gap over all
+ *    channels, row spectra staged in HBM (any supported M).
+ *  DOS_PATH_FUSED: one persistent launch per sweep (forward or adjoint) in
+ *    which a thread-block cluster carries one channel at a time through every
+ *    gap with the field held in distributed shared memory (needs N <= M/2 and
+ *    a compiled cluster configuration for M; see dos_describe).
+ *  DOS_PATH_AUTO: dos_create times one forward+backward of every available
+ *    configuration on the context's own buffers and keeps the fastest.
+ */
 enum {
-  DOS_PATH_AUTO = 0,       /* fastest available for the sizes                       */
-  DOS_PATH_MULTIPASS = 1,  /* row pass / column pass kernels, spectra staged in HBM */
-  DOS_PATH_FUSED = 2       /* one persistent launch per sweep, fields kept on chip   */
+  DOS_PATH_AUTO = 0,
+  DOS_PATH_MULTIPASS = 1,
+  DOS_PATH_FUSED = 2
 };
 
 typedef struct dos_config {
   int n;              /* N: thickness pixels per side of every layer (Section 4)     */
   int m;              /* M: zero-padded DFT size, M >= N, see dos_supported_m()      */
-  int n_layers;       /* K >= 1 diffractive layers                                   */
+  int n_layers;       /* K: 1 <= K <= 64 diffractive layers                          */
   int n_lambda;       /* N_w >= 1 wavelength channels handled by this context        */
   int n_lambda_total; /* channels of the whole design (loss normalisation); 0 = N_w  */
   int fov;            /* F: output field of view side, N - F even, 1 <= F <= N       */
@@ -231,7 +241,9 @@ enum {
   DOS_KERNEL_ROW_SEED = 5,        /* adjoint seed 2 dL/dI o                 */
   DOS_KERNEL_LOSS = 6,            /* objective, PSNR, dL/dI                 */
   DOS_KERNEL_GRAD_REDUCE = 7,     /* fixed-order sum of dL/dh partials      */
-  DOS_KERNEL_KINDS = 8
+  DOS_KERNEL_FUSED_FORWARD = 8,   /* cluster-resident forward sweep         */
+  DOS_KERNEL_FUSED_ADJOINT = 9,   /* cluster-resident adjoint sweep         */
+  DOS_KERNEL_KINDS = 10
 };
 
 /*
@@ -254,6 +266,13 @@ DOS_API int dos_last_launch_count(const dos_ctx *ctx);
 
 /* Implementation chosen for the context (DOS_PATH_MULTIPASS or DOS_PATH_FUSED). */
 DOS_API int dos_path(const dos_ctx *ctx);
+
+/*
+ * Writes a NUL-terminated, human-readable description of the chosen
+ * implementation (path, cluster size, threads, clusters in flight) and of the
+ * autotuner's timings to buf (at most cap bytes).  Returns the full length.
+ */
+DOS_API int dos_describe(const dos_ctx *ctx, char *buf, int cap);
 
 /* Frees every resource of the context (waits for its stream).  NULL is a no-op. */
 DOS_API void dos_destroy(dos_ctx *ctx);

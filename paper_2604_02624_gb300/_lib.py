@@ -26,13 +26,13 @@ ERROR_NAMES = {1: "DOS_ERR_ARG", 2: "DOS_ERR_OOM", 3: "DOS_ERR_CUDA", 4: "DOS_ER
 EXPORTS = ("dos_supported_m", "dos_create", "dos_set_stream", "dos_forward", "dos_loss",
            "dos_read_loss", "dos_backward", "dos_output_field", "dos_layer_field",
            "dos_propagate", "dos_set_timing", "dos_kernel_time", "dos_workspace_bytes",
-           "dos_last_launch_count", "dos_path", "dos_destroy", "dos_last_error",
+           "dos_last_launch_count", "dos_path", "dos_describe", "dos_destroy", "dos_last_error",
            "dos_loss_noalloc")
 
 DOS_NOALLOC_MAX_LAMBDA = 65536
 
 KERNEL_KINDS = ("column_forward", "column_adjoint", "row_forward", "row_adjoint", "row_output",
-                "row_seed", "loss", "grad_reduce")
+                "row_seed", "loss", "grad_reduce", "fused_forward", "fused_adjoint")
 
 
 class DosError(RuntimeError):
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dos_workspace_bytes": (c_size_t, [p]),
         "dos_last_launch_count": (c_int, [p]),
         "dos_path": (c_int, [p]),
+        "dos_describe": (c_int, [p, ctypes.c_char_p, c_int]),
         "dos_destroy": (None, [p]),
         "dos_last_error": (ctypes.c_char_p, []),
         "dos_loss_noalloc": (c_int, [p, p, c_int, c_int, c_int, c_int, POINTER(c_double), p, p, p]),
@@ -178,6 +179,12 @@ def dos_last_launch_count(ctx: int) -> int:
 
 def dos_path(ctx: int) -> int:
     return int(load().dos_path(ctx))
+
+
+def dos_describe(ctx: int) -> str:
+    buf = ctypes.create_string_buffer(4096)
+    load().dos_describe(ctx, buf, 4096)
+    return buf.value.decode()
 
 
 def dos_destroy(ctx: int) -> None:

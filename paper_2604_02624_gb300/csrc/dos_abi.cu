@@ -11,12 +11,17 @@
 //             fixed-order reduction of the partials over channel chunks.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
 #include "../../include/dos.h"
+#include "dos_fused.cuh"
 #include "dos_internal.h"
 
 namespace {
@@ -123,6 +128,12 @@ struct dos_ctx {
   int chunk = 1, n_chunks = 1;
   bool have_fwd = false, have_ckpt = false, have_loss = false;
   int launches = 0;
+  // cluster-resident path
+  std::vector<const dos::FusedOps*> fcands;
+  std::vector<int> fcand_clusters;
+  const dos::FusedOps* fops = nullptr;
+  int n_clusters = 0;
+  std::string describe;
 
   template <typename T>
   int alloc(T** p, size_t count, const char* what) {
@@ -184,7 +195,7 @@ int validate(const dos_config* c) {
     for (int i = 0; i < k; ++i) s += " " + std::to_string(l[i]);
     return fail(DOS_ERR_ARG, s + ")");
   }
-  if (c->n_layers < 1) return fail(DOS_ERR_ARG, "n_layers must be >= 1");
+  if (c->n_layers < 1 || c->n_layers > dos::kMaxGaps - 1) return fail(DOS_ERR_ARG, "n_layers must be in [1, 64]");
   if (c->n_lambda < 1 || c->n_lambda > 65535) return fail(DOS_ERR_ARG, "n_lambda must be in [1, 65535]");
   if (c->n_lambda_total != 0 && c->n_lambda_total < c->n_lambda)
     return fail(DOS_ERR_ARG, "n_lambda_total must be 0 or >= n_lambda");
@@ -213,6 +224,8 @@ int validate(const dos_config* c) {
   return DOS_OK;
 }
 
+int choose_path(dos_ctx* x, int requested);
+
 int build(dos_ctx* x, const dos_config* c) {
   x->n = c->n;
   x->m = c->m;
@@ -229,8 +242,6 @@ int build(dos_ctx* x, const dos_config* c) {
   x->h_base = c->h_base;
   x->evan = c->evanescent;
   x->loss = c->loss;
-  if (c->path == DOS_PATH_FUSED)
-    return fail(DOS_ERR_UNSUPPORTED, "DOS_PATH_FUSED is not available in this build");
   x->path = DOS_PATH_MULTIPASS;
   x->gaps.assign(c->gaps, c->gaps + c->n_layers + 1);
   x->lam.assign(c->lambda, c->lambda + c->n_lambda);
@@ -260,6 +271,21 @@ int build(dos_ctx* x, const dos_config* c) {
   x->n_chunks = (x->nw + x->chunk - 1) / x->chunk;
 
   const size_t n2 = (size_t)x->n * x->n;
+  // cluster-resident configurations that fit this design
+  size_t partial_count = (size_t)x->K * x->n_chunks * n2;
+  if (2 * x->n <= x->m) {
+    const dos::FusedOps* list[16];
+    const int k = dos::fused_ops_for_m(x->m, list, 16);
+    for (int i = 0; i < k; ++i) {
+      if (list[i]->smem(x->n) > 227 * 1024) continue;
+      const int mc = list[i]->max_clusters(x->n);
+      if (mc <= 0) continue;
+      const int ncl = std::min(mc, x->nw);
+      x->fcands.push_back(list[i]);
+      x->fcand_clusters.push_back(ncl);
+      partial_count = std::max(partial_count, (size_t)ncl * x->K * n2);
+    }
+  }
   int rc;
   if ((rc = x->alloc(&x->S, (size_t)x->nw * x->n * x->m, "row spectra"))) return rc;
   if ((rc = x->alloc(&x->ckpt, (size_t)x->K * x->nw * n2, "layer checkpoints"))) return rc;
@@ -268,7 +294,7 @@ int build(dos_ctx* x, const dos_config* c) {
   if ((rc = x->alloc(&x->arow, (size_t)x->m, "aperture spectrum"))) return rc;
   if ((rc = x->alloc(&x->tw, (size_t)x->ops->Q * (x->ops->P + 1), "twiddles"))) return rc;
   if ((rc = x->alloc(&x->chan, (size_t)x->nw, "channel constants"))) return rc;
-  if ((rc = x->alloc(&x->partial, (size_t)x->K * x->n_chunks * n2, "gradient partials"))) return rc;
+  if ((rc = x->alloc(&x->partial, partial_count, "gradient partials"))) return rc;
   if ((rc = x->alloc(&x->stats, (size_t)x->nw, "loss statistics"))) return rc;
   if ((rc = x->alloc(&x->d_loss, 1, "loss"))) return rc;
   DOS_CUDA(cudaMallocHost(&x->h_loss, sizeof(double)), "cudaMallocHost(loss)");
@@ -291,6 +317,251 @@ int build(dos_ctx* x, const dos_config* c) {
   const int RP = x->ops->P % 2 == 0 ? x->ops->P + 1 : x->ops->P;
   DOS_CUDA(dos::launch_twiddles(x->tw, x->ops->P, x->ops->Q, RP, x->m, x->stream), "twiddles");
   DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
+  if ((rc = choose_path(x, c->path))) return rc;
+  DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
+  return DOS_OK;
+}
+
+// ------------------------------------------------------------ launch sequences
+int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
+  const size_t n2 = (size_t)c->n * c->n;
+  c->launches = 0;
+  if (c->path == DOS_PATH_FUSED) {
+    dos::FusedArgs f;
+    std::memset(&f, 0, sizeof(f));
+    f.Hq = c->Hq;
+    f.hq_slot_stride = (size_t)c->nw * c->hs * c->hs;
+    for (int g = 0; g <= c->K; ++g) f.gap_slot[g] = c->gap_slot[g];
+    f.arow = c->arow;
+    f.tw = c->tw;
+    f.chan = c->chan;
+    f.h = d_h;
+    f.ckpt = c->ckpt;
+    f.o = c->o;
+    f.I = d_I;
+    f.n = c->n;
+    f.nw = c->nw;
+    f.K = c->K;
+    f.fov = c->fov;
+    f.of = c->of;
+    f.hs = c->hs;
+    f.save = save != 0;
+    DOS_TIMED(c, DOS_KERNEL_FUSED_FORWARD, c->fops->launch(f, false, c->n_clusters, c->stream),
+              "fused forward sweep");
+    c->launches = 1;
+    return DOS_OK;
+  }
+  const dos::PassOps* op = c->ops;
+  dos::PassArgs a = c->base();
+  // gap 0: the aperture field has the separable spectrum Arow[ky] Arow[kx]
+  a.Hq = c->hq_slot(0);
+  a.out_r0 = 0;
+  a.out_r1 = c->n;
+  DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, true, c->stream), "forward column pass (aperture)");
+  ++c->launches;
+  for (int l = 1; l <= c->K; ++l) {
+    a.h = d_h + (size_t)(l - 1) * n2;
+    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
+    DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_fwd(a, save != 0, c->stream), "forward row pass");
+    a.Hq = c->hq_slot(l);
+    a.in_r0 = 0;
+    a.in_r1 = c->n;
+    a.out_r0 = l == c->K ? c->of : 0;
+    a.out_r1 = l == c->K ? c->of + c->fov : c->n;
+    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, false, c->stream), "forward column pass");
+    c->launches += 2;
+  }
+  a.I = d_I;
+  DOS_TIMED(c, DOS_KERNEL_ROW_OUTPUT, op->row_out(a, c->stream), "output row pass");
+  ++c->launches;
+  return DOS_OK;
+}
+
+int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
+  const size_t n2 = (size_t)c->n * c->n;
+  c->launches = 0;
+  if (c->path == DOS_PATH_FUSED) {
+    dos::FusedArgs f;
+    std::memset(&f, 0, sizeof(f));
+    f.Hq = c->Hq;
+    f.hq_slot_stride = (size_t)c->nw * c->hs * c->hs;
+    for (int g = 0; g <= c->K; ++g) f.gap_slot[g] = c->gap_slot[g];
+    f.arow = c->arow;
+    f.tw = c->tw;
+    f.chan = c->chan;
+    f.h = d_h;
+    f.ckpt = c->ckpt;
+    f.o = c->o;
+    f.dLdI = d_dLdI;
+    f.partial = c->partial;
+    f.n = c->n;
+    f.nw = c->nw;
+    f.K = c->K;
+    f.fov = c->fov;
+    f.of = c->of;
+    f.hs = c->hs;
+    DOS_TIMED(c, DOS_KERNEL_FUSED_ADJOINT, c->fops->launch(f, true, c->n_clusters, c->stream),
+              "fused adjoint sweep");
+    DOS_TIMED(c, DOS_KERNEL_GRAD_REDUCE,
+              dos::launch_grad_reduce_flat(c->partial, d_dLdh, std::min(c->n_clusters, c->nw), (size_t)c->K * n2,
+                                           c->stream),
+              "gradient reduction");
+    c->launches = 2;
+    return DOS_OK;
+  }
+  const dos::PassOps* op = c->ops;
+  dos::PassArgs a = c->base();
+  a.dLdI = d_dLdI;
+  DOS_TIMED(c, DOS_KERNEL_ROW_SEED, op->row_seed(a, c->stream), "adjoint seed row pass");
+  ++c->launches;
+  for (int l = c->K; l >= 1; --l) {
+    a.Hq = c->hq_slot(l);
+    a.in_r0 = l == c->K ? c->of : 0;
+    a.in_r1 = l == c->K ? c->of + c->fov : c->n;
+    a.out_r0 = 0;
+    a.out_r1 = c->n;
+    DOS_TIMED(c, DOS_KERNEL_COLUMN_ADJOINT, op->col(a, true, false, c->stream), "adjoint column pass");
+    a.h = d_h + (size_t)(l - 1) * n2;
+    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
+    a.partial = c->partial + (size_t)(l - 1) * c->n_chunks * n2;
+    DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT, op->row_adj(a, l == 1, c->stream), "adjoint row pass");
+    c->launches += 2;
+  }
+  DOS_TIMED(c, DOS_KERNEL_GRAD_REDUCE,
+            dos::launch_grad_reduce(c->partial, d_dLdh, c->n_chunks, (size_t)c->K * n2, n2, c->stream),
+            "gradient reduction");
+  ++c->launches;
+  return DOS_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+std::string choice_name(const dos::FusedOps* f) {
+  if (!f) return "multipass";
+  return "fused:C" + std::to_string(f->C) + ":L" + std::to_string(f->lines);
+}
+
+std::string tune_key(const dos_ctx* x) {
+  cudaDeviceProp p;
+  std::string dev = "gpu";
+  if (cudaGetDeviceProperties(&p, x->device) == cudaSuccess) dev = std::string(p.name) + "/" + std::to_string(p.multiProcessorCount);
+  for (char& ch : dev)
+    if (ch == ' ') ch = '_';
+  std::ostringstream k;
+  k << dev << " n" << x->n << " m" << x->m << " K" << x->K << " w" << x->nw << " f" << x->fov;
+  return k.str();
+}
+
+void set_choice(dos_ctx* x, int idx) {
+  if (idx < 0) {
+    x->path = DOS_PATH_MULTIPASS;
+    x->fops = nullptr;
+    x->n_clusters = 0;
+  } else {
+    x->path = DOS_PATH_FUSED;
+    x->fops = x->fcands[idx];
+    x->n_clusters = x->fcand_clusters[idx];
+  }
+}
+
+// time forward(save) + backward of the current choice on zero thickness / zero seed
+int time_choice(dos_ctx* x, const float* h0, const float* g0, float* d0, float* ms_out) {
+  int rc;
+  if ((rc = run_forward(x, h0, nullptr, 1)) || (rc = run_backward(x, h0, g0, d0))) return rc;
+  cudaEvent_t a, b;
+  DOS_CUDA(cudaEventCreate(&a), "tune event");
+  DOS_CUDA(cudaEventCreate(&b), "tune event");
+  float best = 1e30f;
+  for (int rep = 0; rep < 2; ++rep) {
+    cudaEventRecord(a, x->stream);
+    if ((rc = run_forward(x, h0, nullptr, 1)) || (rc = run_backward(x, h0, g0, d0))) break;
+    cudaEventRecord(b, x->stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    if (e != cudaSuccess) {
+      rc = fail(DOS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+      break;
+    }
+    best = std::min(best, t);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms_out = best;
+  return rc;
+}
+
+int choose_path(dos_ctx* x, int requested) {
+  std::ostringstream d;
+  if (requested == DOS_PATH_MULTIPASS || x->fcands.empty()) {
+    if (requested == DOS_PATH_FUSED)
+      return fail(DOS_ERR_UNSUPPORTED, "no cluster-resident configuration fits this design (needs n <= m/2 and a "
+                                       "compiled configuration for m)");
+    set_choice(x, -1);
+    x->describe = "path=multipass (" + std::string(requested == DOS_PATH_MULTIPASS ? "requested" : "no fused configuration") + ")";
+    return DOS_OK;
+  }
+  // cached decision
+  const char* cache = std::getenv("DOS_TUNE_CACHE");
+  const std::string key = tune_key(x);
+  if (cache && *cache) {
+    std::ifstream in(cache);
+    std::string line;
+    while (std::getline(in, line)) {
+      if (line.compare(0, key.size() + 1, key + "\t") != 0) continue;
+      const std::string v = line.substr(key.size() + 1);
+      if (v == "multipass" && requested == DOS_PATH_AUTO) {
+        set_choice(x, -1);
+        x->describe = "path=multipass (tuning cache)";
+        return DOS_OK;
+      }
+      for (size_t i = 0; i < x->fcands.size(); ++i)
+        if (choice_name(x->fcands[i]) == v) {
+          set_choice(x, (int)i);
+          x->describe = "path=" + v + " clusters=" + std::to_string(x->n_clusters) + " (tuning cache)";
+          return DOS_OK;
+        }
+    }
+  }
+  const size_t n2 = (size_t)x->n * x->n;
+  float *h0 = nullptr, *g0 = nullptr, *d0 = nullptr;
+  DOS_CUDA(cudaMalloc(&h0, sizeof(float) * x->K * n2), "autotune buffers");
+  cudaError_t e = cudaMalloc(&g0, sizeof(float) * (size_t)x->nw * x->fov * x->fov);
+  if (e == cudaSuccess) e = cudaMalloc(&d0, sizeof(float) * x->K * n2);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h0, 0, sizeof(float) * x->K * n2, x->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g0, 0, sizeof(float) * (size_t)x->nw * x->fov * x->fov, x->stream);
+  int rc = DOS_OK;
+  if (e != cudaSuccess) rc = fail(DOS_ERR_CUDA, std::string("autotune buffers: ") + cudaGetErrorString(e));
+  int best = -2;
+  float best_ms = 1e30f;
+  d << "tuned (fwd+bwd ms):";
+  for (int i = (requested == DOS_PATH_AUTO ? -1 : 0); rc == DOS_OK && i < (int)x->fcands.size(); ++i) {
+    set_choice(x, i);
+    float ms = 0.f;
+    rc = time_choice(x, h0, g0, d0, &ms);
+    if (rc) break;
+    d << " " << choice_name(i < 0 ? nullptr : x->fcands[i]);
+    if (i >= 0) d << "x" << x->fcand_clusters[i];
+    d << "=" << ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = i;
+    }
+  }
+  cudaFree(h0);
+  cudaFree(g0);
+  cudaFree(d0);
+  if (rc) return rc;
+  set_choice(x, best);
+  std::ostringstream head;
+  head << "path=" << choice_name(x->fops);
+  if (x->fops)
+    head << " threads=" << x->fops->threads << " clusters=" << x->n_clusters
+         << " smem=" << x->fops->smem(x->n);
+  x->describe = head.str() + " | " + d.str();
+  if (cache && *cache) {
+    std::ofstream out(cache, std::ios::app);
+    out << key << "\t" << choice_name(x->fops) << "\n";
+  }
   return DOS_OK;
 }
 
@@ -348,32 +619,8 @@ DOS_API int dos_forward(dos_ctx* c, const float* d_h, float* d_I, int save_for_b
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!d_h) return fail(DOS_ERR_ARG, "d_h is NULL");
-  const dos::PassOps* op = c->ops;
-  const size_t n2 = (size_t)c->n * c->n;
   c->have_fwd = c->have_ckpt = c->have_loss = false;
-  c->launches = 0;
-  dos::PassArgs a = c->base();
-  // gap 0: the aperture field has the separable spectrum Arow[ky] Arow[kx]
-  a.Hq = c->hq_slot(0);
-  a.out_r0 = 0;
-  a.out_r1 = c->n;
-  DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, true, c->stream), "forward column pass (aperture)");
-  ++c->launches;
-  for (int l = 1; l <= c->K; ++l) {
-    a.h = d_h + (size_t)(l - 1) * n2;
-    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
-    DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_fwd(a, save_for_backward != 0, c->stream), "forward row pass");
-    a.Hq = c->hq_slot(l);
-    a.in_r0 = 0;
-    a.in_r1 = c->n;
-    a.out_r0 = l == c->K ? c->of : 0;
-    a.out_r1 = l == c->K ? c->of + c->fov : c->n;
-    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, false, c->stream), "forward column pass");
-    c->launches += 2;
-  }
-  a.I = d_I;
-  DOS_TIMED(c, DOS_KERNEL_ROW_OUTPUT, op->row_out(a, c->stream), "output row pass");
-  ++c->launches;
+  if ((rc = run_forward(c, d_h, d_I, save_for_backward))) return rc;
   c->have_fwd = true;
   c->have_ckpt = save_for_backward != 0;
   return DOS_OK;
@@ -418,30 +665,7 @@ DOS_API int dos_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, floa
   if (rc) return rc;
   if (!c->have_ckpt) return fail(DOS_ERR_STATE, "dos_backward needs dos_forward(save_for_backward=1) first");
   if (!d_h || !d_dLdI || !d_dLdh) return fail(DOS_ERR_ARG, "d_h, d_dLdI and d_dLdh are required");
-  const dos::PassOps* op = c->ops;
-  const size_t n2 = (size_t)c->n * c->n;
-  c->launches = 0;
-  dos::PassArgs a = c->base();
-  a.dLdI = d_dLdI;
-  DOS_TIMED(c, DOS_KERNEL_ROW_SEED, op->row_seed(a, c->stream), "adjoint seed row pass");
-  ++c->launches;
-  for (int l = c->K; l >= 1; --l) {
-    a.Hq = c->hq_slot(l);
-    a.in_r0 = l == c->K ? c->of : 0;
-    a.in_r1 = l == c->K ? c->of + c->fov : c->n;
-    a.out_r0 = 0;
-    a.out_r1 = c->n;
-    DOS_TIMED(c, DOS_KERNEL_COLUMN_ADJOINT, op->col(a, true, false, c->stream), "adjoint column pass");
-    a.h = d_h + (size_t)(l - 1) * n2;
-    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
-    a.partial = c->partial + (size_t)(l - 1) * c->n_chunks * n2;
-    DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT, op->row_adj(a, l == 1, c->stream), "adjoint row pass");
-    c->launches += 2;
-  }
-  DOS_TIMED(c, DOS_KERNEL_GRAD_REDUCE, dos::launch_grad_reduce(c->partial, d_dLdh, c->n_chunks, (size_t)c->K * n2, n2, c->stream),
-            "gradient reduction");
-  ++c->launches;
-  return DOS_OK;
+  return run_backward(c, d_h, d_dLdI, d_dLdh);
 }
 
 DOS_API int dos_output_field(dos_ctx* c, float* d_o) {
@@ -514,6 +738,16 @@ DOS_API size_t dos_workspace_bytes(const dos_ctx* c) { return c ? c->bytes : 0; 
 DOS_API int dos_last_launch_count(const dos_ctx* c) { return c ? c->launches : 0; }
 
 DOS_API int dos_path(const dos_ctx* c) { return c ? c->path : 0; }
+
+DOS_API int dos_describe(const dos_ctx* c, char* buf, int cap) {
+  const std::string d = c ? c->describe : std::string();
+  if (buf && cap > 0) {
+    const size_t k = std::min((size_t)cap - 1, d.size());
+    std::memcpy(buf, d.data(), k);
+    buf[k] = 0;
+  }
+  return (int)d.size();
+}
 
 DOS_API void dos_destroy(dos_ctx* c) {
   if (!c) return;

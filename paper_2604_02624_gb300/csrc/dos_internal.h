@@ -82,5 +82,7 @@ cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, fl
                         int fov2, double norm, int mode, cudaStream_t s);
 cudaError_t launch_grad_reduce(const float* partial, float* grad, int n_chunks, size_t count,
                                size_t chunk_stride, cudaStream_t s);
+cudaError_t launch_grad_reduce_flat(const float* partial, float* grad, int n_parts, size_t count,
+                                    cudaStream_t s);
 
 }  // namespace dos

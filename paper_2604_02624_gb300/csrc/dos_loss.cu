@@ -132,3 +132,21 @@ cudaError_t launch_grad_reduce(const float* partial, float* grad, int n_chunks, 
 }
 
 }  // namespace dos
+
+namespace dos {
+// grad[g] = sum over c < n_parts (in order) of partial[c * count + g]
+__global__ void k_grad_reduce_flat(const float* __restrict__ partial, float* __restrict__ grad,
+                                   int n_parts, size_t count) {
+  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  double acc = 0.0;
+  for (int c = 0; c < n_parts; ++c) acc += (double)partial[(size_t)c * count + g];
+  grad[g] = (float)acc;
+}
+
+cudaError_t launch_grad_reduce_flat(const float* partial, float* grad, int n_parts, size_t count,
+                                    cudaStream_t s) {
+  k_grad_reduce_flat<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(partial, grad, n_parts, count);
+  return cudaGetLastError();
+}
+}  // namespace dos

@@ -31,6 +31,9 @@ def _built():
     torch.cuda.set_device(DEV)
 
 
+PATHS = ["multipass", "fused"]
+
+
 def _stack(w, **kw):
     return DiffractiveStack.from_workload(w, device=DEV, **kw)
 
@@ -68,10 +71,10 @@ def test_propagate_matches_oracle(n, m, adj, evan):
 
 
 # ------------------------------------------------------------ forward model
-def _forward_case(w, evan="decay", loss="mse"):
+def _forward_case(w, evan="decay", loss="mse", path="multipass"):
     h = W.thickness(w, 0)
     T = W.targets(w, 1)
-    st = _stack(w, evanescent=evan, loss=loss)
+    st = _stack(w, evanescent=evan, loss=loss, path=path)
     hd = _t(h)
     I = st.forward(hd)
     o = st.output_field()
@@ -79,16 +82,18 @@ def _forward_case(w, evan="decay", loss="mse"):
     return st, h, T, hd, I, o, ref
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("name", ["tiny", "small"])
-def test_forward_fields_and_intensity(name):
+def test_forward_fields_and_intensity(name, path):
     w = W.workload(name)
-    st, h, T, hd, I, o, ref = _forward_case(w)
+    st, h, T, hd, I, o, ref = _forward_case(w, path=path)
+    assert st.path == path
     assert rel_l2(_np(o).astype(np.complex128), ref["o"]) <= TOL_FIELD
     assert rel_l2(_np(I).astype(np.float64), ref["I"]) <= TOL_INTENSITY
     for l in range(1, w.n_layers + 1):
         v = _np(st.layer_field(l)).astype(np.complex128)
         assert rel_l2(v, ref["v"][:, l - 1]) <= TOL_FIELD, l
-    assert st.last_launch_count == 2 * w.n_layers + 2
+    assert st.last_launch_count == (2 * w.n_layers + 2 if path == "multipass" else 1)
     st.close()
 
 
@@ -117,7 +122,7 @@ def test_forward_single_pixel_layer():
 @pytest.mark.parametrize("loss", ["mse", "mse_scaled"])
 def test_loss_psnr_and_dldi(loss):
     w = W.workload("small")
-    st, h, T, hd, I, o, ref = _forward_case(w, loss=loss)
+    st, h, T, hd, I, o, ref = _forward_case(w, loss=loss, path="fused")
     val, psnr, dLdI = st.loss(_t(T))
     L_ref, psnr_ref, dLdI_ref = O.mse_loss(ref["I"], T, scaled=(loss == "mse_scaled"))
     assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref)
@@ -127,12 +132,13 @@ def test_loss_psnr_and_dldi(loss):
 
 
 # ------------------------------------------------------------ gradient
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("name,loss", [("tiny", "mse"), ("small", "mse"), ("small", "mse_scaled")])
-def test_gradient_matches_oracle_and_finite_differences(name, loss):
+def test_gradient_matches_oracle_and_finite_differences(name, loss, path):
     w = W.workload(name)
     h = W.thickness(w, 0)
     T = W.targets(w, 1)
-    st = _stack(w, loss=loss)
+    st = _stack(w, loss=loss, path=path)
     hd = _t(h)
     st.forward(hd)
     _, _, dLdI = st.loss(_t(T))
@@ -148,13 +154,14 @@ def test_gradient_matches_oracle_and_finite_differences(name, loss):
     st.close()
 
 
-def test_autograd_function_composes_with_torch_loss():
+@pytest.mark.parametrize("path", PATHS)
+def test_autograd_function_composes_with_torch_loss(path):
     """A torch objective of the intensities back-propagates through DosFunction
     (dos_backward) to the FP64 oracle gradient of the same objective."""
     w = W.workload("tiny")
     h = W.thickness(w, 0)
     T = W.targets(w, 1)
-    st = _stack(w)
+    st = _stack(w, path=path)
     hd = _t(h).requires_grad_(True)
     I = DosFunction.apply(hd, st)
     Td = _t(T)
@@ -166,10 +173,11 @@ def test_autograd_function_composes_with_torch_loss():
     st.close()
 
 
-def test_backward_is_bitwise_deterministic():
+@pytest.mark.parametrize("path", PATHS)
+def test_backward_is_bitwise_deterministic(path):
     w = W.workload("small")
     h = _t(W.thickness(w, 0))
-    st = _stack(w)
+    st = _stack(w, path=path)
     st.forward(h)
     _, _, g = st.loss(_t(W.targets(w, 1)))
     a = st.backward(h, g).clone()
@@ -196,13 +204,14 @@ def test_state_errors():
 
 
 # ------------------------------------------------------------ full workload sizes
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("name,count", [("massive", 5), ("precision", 3), ("batched", 4)])
-def test_full_size_forward_on_sampled_channels(name, count):
+def test_full_size_forward_on_sampled_channels(name, count, path):
     """All channels on the GPU in the bench's launch configuration; the oracle
     checks evenly spread channels (every channel is independent)."""
     w = W.workload(name)
     h = W.thickness(w, 0)
-    st = _stack(w)
+    st = _stack(w, path=path)
     I = st.forward(_t(h), save_for_backward=False)
     o = st.output_field()
     idx = W.subset_indices(w.n_lambda, count)
@@ -213,15 +222,16 @@ def test_full_size_forward_on_sampled_channels(name, count):
     st.close()
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("name", ["massive", "precision"])
-def test_full_geometry_gradient_on_channel_subset(name):
+def test_full_geometry_gradient_on_channel_subset(name, path):
     """Gradient of the full geometry on a 16-channel subset design (the same
     layers, gaps and grid), against the FP64 oracle."""
     w = W.workload(name)
     ws = w.subset(W.subset_indices(w.n_lambda, 16))
     h = W.thickness(w, 0)
     T = W.targets(w, 1)[W.subset_indices(w.n_lambda, 16)]
-    st = _stack(ws)
+    st = _stack(ws, path=path)
     hd = _t(h)
     st.forward(hd)
     _, _, dLdI = st.loss(_t(T))
@@ -231,14 +241,15 @@ def test_full_geometry_gradient_on_channel_subset(name):
     st.close()
 
 
-def test_full_size_gradient_is_the_sum_of_channel_shards():
+@pytest.mark.parametrize("path", PATHS)
+def test_full_size_gradient_is_the_sum_of_channel_shards(path):
     """At 4096 channels the gradient equals the sum of the gradients of two
     channel shards that share the loss normalisation (the property that makes
     wavelength sharding across GPUs exact)."""
     w = W.workload("massive")
     h = _t(W.thickness(w, 0))
     T = W.targets(w, 1)
-    st = _stack(w)
+    st = _stack(w, path=path)
     st.forward(h)
     L_full, _, dLdI = st.loss(_t(T))
     g_full = st.backward(h, dLdI).clone()
@@ -248,7 +259,7 @@ def test_full_size_gradient_is_the_sum_of_channel_shards():
     L_sum = 0.0
     for lo, hi in ((0, half), (half, w.n_lambda)):
         ws = w.subset(np.arange(lo, hi))
-        s = _stack(ws, n_lambda_total=w.n_lambda)
+        s = _stack(ws, n_lambda_total=w.n_lambda, path=path)
         s.forward(h)
         Ls, _, dl = s.loss(_t(T[lo:hi]))
         g_sum += s.backward(h, dl)
@@ -256,3 +267,36 @@ def test_full_size_gradient_is_the_sum_of_channel_shards():
         s.close()
     assert abs(L_sum - L_full) <= 1e-9 * abs(L_full)
     assert rel_l2(_np(g_sum).astype(np.float64), _np(g_full).astype(np.float64)) <= 1e-5
+
+
+def test_paths_agree_at_full_size():
+    """The cluster-resident and the multi-pass implementations of the massive
+    step give the same intensities and gradient (both FP32, different orders)."""
+    w = W.workload("massive")
+    h = _t(W.thickness(w, 0))
+    T = _t(W.targets(w, 1))
+    out = {}
+    for path in PATHS:
+        st = _stack(w, path=path)
+        I = st.forward(h).clone()
+        _, _, g = st.loss(T)
+        out[path] = (I, st.backward(h, g).clone())
+        st.close()
+    assert rel_l2(_np(out["fused"][0]).astype(np.float64), _np(out["multipass"][0]).astype(np.float64)) <= 1e-5
+    assert rel_l2(_np(out["fused"][1]).astype(np.float64), _np(out["multipass"][1]).astype(np.float64)) <= 1e-4
+
+
+def test_auto_path_is_tuned_and_described():
+    w = W.workload("batched")
+    st = _stack(w, path="auto")
+    d = L.dos_describe(st.handle)
+    assert d.startswith("path=") and "tuned" in d, d
+    assert st.path in PATHS
+    st.close()
+
+
+def test_fused_path_refuses_layers_wider_than_half_the_grid():
+    w = custom(64, 64, 1, [500, 600], 10, 64, name="no-pad")
+    with pytest.raises(L.DosError) as e:
+        _stack(w, path="fused")
+    assert e.value.code == L.DOS_ERR_UNSUPPORTED
