@@ -85,6 +85,10 @@ enum {
  *    a compiled cluster configuration for M; see dos_describe).
  *  DOS_PATH_AUTO: dos_create times one forward+backward of every available
  *    configuration on the context's own buffers and keeps the fastest.
+ * Environment: DOS_FORCE_CONFIG="multipass" or "fused:C<c>:L<lines>" (names as
+ * printed by dos_describe) selects a configuration without timing, when it is
+ * compatible with the requested path; DOS_TUNE_CACHE=<file> stores and reuses
+ * the autotuner's decision per (device, N, M, K, N_w, F).
  */
 enum {
   DOS_PATH_AUTO = 0,

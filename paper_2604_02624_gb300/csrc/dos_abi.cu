@@ -500,6 +500,24 @@ int choose_path(dos_ctx* x, int requested) {
     x->describe = "path=multipass (" + std::string(requested == DOS_PATH_MULTIPASS ? "requested" : "no fused configuration") + ")";
     return DOS_OK;
   }
+  // explicit override (profiling, reproducible benchmarks): "multipass" or "fused:C<c>:L<lines>"
+  const char* force = std::getenv("DOS_FORCE_CONFIG");
+  if (force && *force) {
+    const std::string v(force);
+    if (v == "multipass" && requested != DOS_PATH_FUSED) {
+      set_choice(x, -1);
+      x->describe = "path=multipass (DOS_FORCE_CONFIG)";
+      return DOS_OK;
+    }
+    for (size_t i = 0; i < x->fcands.size(); ++i)
+      if (choice_name(x->fcands[i]) == v && requested != DOS_PATH_MULTIPASS) {
+        set_choice(x, (int)i);
+        x->describe = "path=" + v + " threads=" + std::to_string(x->fops->threads) + " clusters=" +
+                      std::to_string(x->n_clusters) + " smem=" + std::to_string(x->fops->smem(x->n)) +
+                      " (DOS_FORCE_CONFIG)";
+        return DOS_OK;
+      }
+  }
   // cached decision
   const char* cache = std::getenv("DOS_TUNE_CACHE");
   const std::string key = tune_key(x);
