@@ -67,6 +67,22 @@ struct Fused {
   static_assert(E % PERIOD == 0, "elements per thread must cover whole periods");
   static_assert(LF::P % 2 == 0 && LF::Q % 2 == 0 && E % 2 == 0, "pruned halves");
 
+  // Transfer-table values of a column are issued before its forward DFT when
+  // the register budget (65536 / threads) leaves room for them.
+  static constexpr bool kPrefetchH = NT <= 400;
+
+  // H(|ky|, |kx|) for the thread's frequencies k = t + T*i of column cc:
+  // |k| = k below M/2 and M - k above, both affine in i at compile time.
+  __device__ static __forceinline__ void load_h(float2 (&hreg)[E], const float2* __restrict__ Hw, int hs, int t,
+                                                int cc) {
+    const int bc = min(cc, M - cc);
+    const float2* lo = Hw + (size_t)t * hs + bc;
+    const float2* hi = Hw + (size_t)(M - t) * hs + bc;
+#pragma unroll
+    for (int i = 0; i < E; ++i)
+      hreg[i] = i < EH ? __ldg(lo + (size_t)T * i * hs) : __ldg(hi - (size_t)T * i * hs);
+  }
+
   static size_t smem_bytes(int n) {
     const int R = (n + C - 1) / C;
     return sizeof(float2) * ((size_t)R * ZS + (size_t)LINES * ZL + ZS);
@@ -115,6 +131,8 @@ struct Fused {
       const bool ok = (cb + l) < MC && c < M;
       const int cc = ok ? c : c0;
       float2 r[E];
+      float2 hreg[E];
+      if constexpr (kPrefetchH) load_h(hreg, Hw, hs, t, cc);
       if constexpr (APERTURE) {
         const float2 ac = arow[cc];
 #pragma unroll
@@ -128,13 +146,9 @@ struct Fused {
         }
         LF::template fft<false, PH>(r, t, z, s.tw);
       }
-      const int bc = min(cc, M - cc);
+      if constexpr (!kPrefetchH) load_h(hreg, Hw, hs, t, cc);
 #pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int k = t + T * i;
-        const float2 hv = __ldg(Hw + min(k, M - k) * hs + bc);
-        r[i] = ADJ ? cmulc(r[i], hv) : cmul(r[i], hv);
-      }
+      for (int i = 0; i < E; ++i) r[i] = ADJ ? cmulc(r[i], hreg[i]) : cmul(r[i], hreg[i]);
       LF::template fft<true, LF::P, QH>(r, t, z, s.tw);
 #pragma unroll
       for (int i = 0; i < EH; ++i) {
