@@ -49,13 +49,15 @@ def _args():
 
 
 def _workload(name, rank, world):
+    from paper_2604_02624_gb300 import sharding
     from paper_2604_02624_gb300 import workloads as W
     w = W.workload(name)
     if world > 1:
-        # weak scaling: the design holds world * N_w channels, rank r owns shard r
+        # weak scaling: the design holds world * N_w channels, rank r owns one shard
         nw = w.n_lambda
         big = W.workload(name, n_lambda=nw * world) if name in ("batched", "massive", "precision") else w
-        w = big.subset(np.arange(rank * nw, (rank + 1) * nw))
+        lo, hi = sharding.shard_range(big.n_lambda, rank, world)
+        w = big.subset(np.arange(lo, hi))
     return w
 
 
@@ -308,6 +310,20 @@ def run_ours(a):
     kernel_share = {k: {"launches": v[0], "ms": v[1], "share": v[1] / max(1e-9, sum(x[1] for x in kernel.values()))}
                     for k, v in kernel.items() if v[0]}
 
+    # ---- the same step replayed as one CUDA graph (dos_step)
+    graph_ms = None
+    for _ in range(2):
+        stack.step(h, T, grad_out=g, intensity_out=I)
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(a.steps):
+        stack.step(h, T, grad_out=g, intensity_out=I)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / a.steps
+
     # ---- end to end through the public API with pinned host buffers
     e2e = None
     if not a.no_e2e:
@@ -355,7 +371,9 @@ def run_ours(a):
             "config": _config(w, world), "path": stack.path,
             "path_detail": L.dos_describe(stack.handle), "roofline": roof,
             "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches[0], "clocks": clk}
+            "gpu_launches": launches[0], "clocks": clk,
+            "graph_step": {"ms_per_step": graph_ms, "value": units_per_step / (graph_ms * 1e-3),
+                           "note": "forward + loss + backward replayed as one CUDA graph (dos_step)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     stack.close()

@@ -214,6 +214,21 @@ DOS_API int dos_read_loss(dos_ctx *ctx, double *h_loss);
 DOS_API int dos_backward(dos_ctx *ctx, const float *d_h, const float *d_dLdI, float *d_dLdh);
 
 /*
+ * One design step: dos_forward(save) + dos_loss + dos_backward, replayed as a
+ * CUDA graph.  The first call for a given set of pointers captures the step
+ * on a stream private to the context (ordered after the context's stream by
+ * an event, and the context's stream after it); later calls with the same
+ * pointers replay the graph.
+ *   d_h [K][N][N], d_T [N_w][F][F] inputs; d_dLdh [K][N][N] output (all required).
+ *   d_I [N_w][F][F] and d_psnr [N_w] optional outputs (NULL to skip).
+ *   h_loss: when non-NULL receives L (waits for the stream).
+ * Afterwards the context holds the same state as after the three calls.
+ * Errors: DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_step(dos_ctx *ctx, const float *d_h, const float *d_T, float *d_dLdh, float *d_I,
+                     float *d_psnr, double *h_loss);
+
+/*
  * Copies the complex output field o of the last forward, [N_w][F][F] complex64
  * (interleaved floats), to d_o.  Errors: DOS_ERR_STATE, DOS_ERR_ARG, DOS_ERR_CUDA.
  */

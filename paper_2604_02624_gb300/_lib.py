@@ -24,7 +24,7 @@ ERROR_NAMES = {1: "DOS_ERR_ARG", 2: "DOS_ERR_OOM", 3: "DOS_ERR_CUDA", 4: "DOS_ER
 
 # every symbol include/dos.h declares (checked by the CPU tests)
 EXPORTS = ("dos_supported_m", "dos_create", "dos_set_stream", "dos_forward", "dos_loss",
-           "dos_read_loss", "dos_backward", "dos_output_field", "dos_layer_field",
+           "dos_read_loss", "dos_backward", "dos_step", "dos_output_field", "dos_layer_field",
            "dos_propagate", "dos_set_timing", "dos_kernel_time", "dos_workspace_bytes",
            "dos_last_launch_count", "dos_path", "dos_describe", "dos_destroy", "dos_last_error",
            "dos_loss_noalloc")
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dos_loss": (c_int, [p, p, POINTER(c_double), p, p]),
         "dos_read_loss": (c_int, [p, POINTER(c_double)]),
         "dos_backward": (c_int, [p, p, p, p]),
+        "dos_step": (c_int, [p, p, p, p, p, p, POINTER(c_double)]),
         "dos_output_field": (c_int, [p, p]),
         "dos_layer_field": (c_int, [p, c_int, p]),
         "dos_propagate": (c_int, [p, c_int, p, p, c_int]),
@@ -143,6 +144,13 @@ def dos_read_loss(ctx: int) -> float:
 
 def dos_backward(ctx: int, d_h: int, d_dLdI: int, d_dLdh: int) -> None:
     _check(load().dos_backward(ctx, d_h, d_dLdI, d_dLdh), "dos_backward")
+
+
+def dos_step(ctx: int, d_h: int, d_T: int, d_dLdh: int, d_I: int, d_psnr: int, read_loss: bool):
+    out = c_double()
+    _check(load().dos_step(ctx, d_h, d_T, d_dLdh, d_I or None, d_psnr or None,
+                           ctypes.byref(out) if read_loss else None), "dos_step")
+    return out.value if read_loss else None
 
 
 def dos_output_field(ctx: int, d_o: int) -> None:

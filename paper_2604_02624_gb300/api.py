@@ -150,6 +150,25 @@ class DiffractiveStack:
         L.dos_backward(self._ctx, h.data_ptr(), dLdI.data_ptr(), g.data_ptr())
         return g
 
+    def step(self, h: torch.Tensor, T: torch.Tensor, grad_out: Optional[torch.Tensor] = None,
+             intensity_out: Optional[torch.Tensor] = None, psnr_out: Optional[torch.Tensor] = None,
+             read: bool = False):
+        """Forward + loss + backward in one call, replayed as a CUDA graph.
+        Returns (loss or None, dL/dh).  Reusing the same tensors reuses the graph."""
+        _need(h, torch.float32, (self.n_layers, self.n, self.n), "h", self.device)
+        _need(T, torch.float32, (self.n_lambda, self.fov, self.fov), "T", self.device)
+        g = grad_out if grad_out is not None else torch.empty_like(h)
+        _need(g, torch.float32, (self.n_layers, self.n, self.n), "grad_out", self.device)
+        if intensity_out is not None:
+            _need(intensity_out, torch.float32, (self.n_lambda, self.fov, self.fov), "intensity_out", self.device)
+        if psnr_out is not None:
+            _need(psnr_out, torch.float32, (self.n_lambda,), "psnr_out", self.device)
+        self._bind()
+        val = L.dos_step(self._ctx, h.data_ptr(), T.data_ptr(), g.data_ptr(),
+                         intensity_out.data_ptr() if intensity_out is not None else 0,
+                         psnr_out.data_ptr() if psnr_out is not None else 0, read)
+        return val, g
+
     def output_field(self) -> torch.Tensor:
         o = torch.empty((self.n_lambda, self.fov, self.fov), dtype=torch.complex64, device=self.device)
         self._bind()

@@ -134,6 +134,12 @@ struct dos_ctx {
   const dos::FusedOps* fops = nullptr;
   int n_clusters = 0;
   std::string describe;
+  // graph of one design step (dos_step)
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  float* dLdI_step = nullptr;  // [nw][fov][fov] seed buffer of dos_step
 
   template <typename T>
   int alloc(T** p, size_t count, const char* what) {
@@ -153,6 +159,14 @@ struct dos_ctx {
   }
   void release() {
     cudaStreamSynchronize(stream);
+    if (gstream) cudaStreamSynchronize(gstream);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (gstream) cudaStreamDestroy(gstream);
+    gexec = nullptr;
+    gstream = nullptr;
+    ev_in = ev_out = nullptr;
     timer.destroy();
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
@@ -297,6 +311,7 @@ int build(dos_ctx* x, const dos_config* c) {
   if ((rc = x->alloc(&x->partial, partial_count, "gradient partials"))) return rc;
   if ((rc = x->alloc(&x->stats, (size_t)x->nw, "loss statistics"))) return rc;
   if ((rc = x->alloc(&x->d_loss, 1, "loss"))) return rc;
+  if ((rc = x->alloc(&x->dLdI_step, (size_t)x->nw * x->fov * x->fov, "step seed"))) return rc;
   DOS_CUDA(cudaMallocHost(&x->h_loss, sizeof(double)), "cudaMallocHost(loss)");
 
   double *d_lam = nullptr, *d_nidx = nullptr, *d_kap = nullptr;
@@ -684,6 +699,64 @@ DOS_API int dos_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, floa
   if (!c->have_ckpt) return fail(DOS_ERR_STATE, "dos_backward needs dos_forward(save_for_backward=1) first");
   if (!d_h || !d_dLdI || !d_dLdh) return fail(DOS_ERR_ARG, "d_h, d_dLdI and d_dLdh are required");
   return run_backward(c, d_h, d_dLdI, d_dLdh);
+}
+
+DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dLdh, float* d_I, float* d_psnr,
+                     double* h_loss) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!d_h || !d_T || !d_dLdh) return fail(DOS_ERR_ARG, "d_h, d_T and d_dLdh are required");
+  if (!c->gstream) {
+    DOS_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking), "step stream");
+    DOS_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "step event");
+    DOS_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming), "step event");
+  }
+  const void* key[5] = {d_h, d_T, d_dLdh, d_I, d_psnr};
+  bool same = c->gexec != nullptr;
+  for (int i = 0; i < 5; ++i) same = same && key[i] == c->gkey[i];
+  DOS_CUDA(cudaEventRecord(c->ev_in, c->stream), "step order");
+  DOS_CUDA(cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "step order");
+  if (!same) {
+    const bool timing = c->timer.on;
+    c->timer.on = false;
+    cudaStream_t user = c->stream;
+    c->stream = c->gstream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      const int fov2 = c->fov * c->fov;
+      const double norm = (double)c->nw_total * fov2;
+      rc = run_forward(c, d_h, d_I, 1);
+      if (!rc) e = dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, fov2, c->gstream);
+      if (!rc && e == cudaSuccess)
+        e = dos::launch_loss_final(c->stats, c->nw, fov2, norm, c->loss, c->d_loss, d_psnr, c->gstream);
+      if (!rc && e == cudaSuccess)
+        e = dos::launch_dldi(c->o, d_T, c->stats, c->dLdI_step, c->nw, fov2, norm, c->loss, c->gstream);
+      if (!rc && e == cudaSuccess) rc = run_backward(c, d_h, c->dLdI_step, d_dLdh);
+      cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    c->timer.on = timing;
+    if (rc || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc) return rc;
+      return fail(DOS_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(e));
+    }
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(DOS_ERR_CUDA, std::string("step instantiate: ") + cudaGetErrorString(e));
+    for (int i = 0; i < 5; ++i) c->gkey[i] = key[i];
+  }
+  DOS_CUDA(cudaGraphLaunch(c->gexec, c->gstream), "step graph launch");
+  DOS_CUDA(cudaEventRecord(c->ev_out, c->gstream), "step order");
+  DOS_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "step order");
+  c->launches = (c->path == DOS_PATH_FUSED ? 1 : 2 * c->K + 2) + 3 + (c->path == DOS_PATH_FUSED ? 2 : 2 * c->K + 2);
+  c->have_fwd = c->have_ckpt = c->have_loss = true;
+  if (h_loss) return dos_read_loss(c, h_loss);
+  return DOS_OK;
 }
 
 DOS_API int dos_output_field(dos_ctx* c, float* d_o) {

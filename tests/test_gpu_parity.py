@@ -300,3 +300,31 @@ def test_fused_path_refuses_layers_wider_than_half_the_grid():
     with pytest.raises(L.DosError) as e:
         _stack(w, path="fused")
     assert e.value.code == L.DOS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_graph_step_matches_separate_calls(path):
+    """dos_step (captured once as a CUDA graph, then replayed) gives the same
+    loss, intensities, PSNR and gradient as forward + loss + backward."""
+    w = W.workload("small")
+    h = _t(W.thickness(w, 0))
+    T = _t(W.targets(w, 1))
+    st = _stack(w, path=path)
+    I_ref = st.forward(h).clone()
+    L_ref, p_ref, dl = st.loss(T)
+    g_ref = st.backward(h, dl).clone()
+    I = torch.empty_like(I_ref)
+    p = torch.empty_like(p_ref)
+    g = torch.empty_like(g_ref)
+    for _ in range(3):  # capture, then two replays
+        val, _ = st.step(h, T, grad_out=g, intensity_out=I, psnr_out=p, read=True)
+        torch.cuda.synchronize()
+        assert val == L_ref
+        assert torch.equal(I, I_ref) and torch.equal(p, p_ref) and torch.equal(g, g_ref)
+    h2 = h * 0.5
+    val2, g2 = st.step(h2, T, grad_out=g, read=True)   # new pointers: re-capture
+    st.forward(h2)
+    L2, _, dl2 = st.loss(T)
+    assert val2 == L2
+    assert torch.equal(g2, st.backward(h2, dl2))
+    st.close()
