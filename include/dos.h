@@ -83,8 +83,12 @@ enum {
  *    which a thread-block cluster carries one channel at a time through every
  *    gap with the field held in distributed shared memory (needs N <= M/2 and
  *    a compiled cluster configuration for M; see dos_describe).
+ *  DOS_PATH_DFT_GEMM: the 2D DFTs as dense complex GEMMs on the tcgen05
+ *    tensor cores in split-BF16 (three terms hi*hi + hi*lo + lo*hi, FP32
+ *    accumulation in tensor memory), channels processed in chunks; only on
+ *    request (it trades accuracy, ~1e-5..1e-4, and speed for tensor cores).
  *  DOS_PATH_AUTO: dos_create times one forward+backward of every available
- *    configuration on the context's own buffers and keeps the fastest.
+ *    multi-pass / cluster-resident configuration and keeps the fastest.
  * Environment: DOS_FORCE_CONFIG="multipass" or "fused:C<c>:L<lines>" (names as
  * printed by dos_describe) selects a configuration without timing, when it is
  * compatible with the requested path; DOS_TUNE_CACHE=<file> stores and reuses
@@ -93,7 +97,8 @@ enum {
 enum {
   DOS_PATH_AUTO = 0,
   DOS_PATH_MULTIPASS = 1,
-  DOS_PATH_FUSED = 2
+  DOS_PATH_FUSED = 2,
+  DOS_PATH_DFT_GEMM = 3
 };
 
 typedef struct dos_config {
@@ -262,7 +267,9 @@ enum {
   DOS_KERNEL_GRAD_REDUCE = 7,     /* fixed-order sum of dL/dh partials      */
   DOS_KERNEL_FUSED_FORWARD = 8,   /* cluster-resident forward sweep         */
   DOS_KERNEL_FUSED_ADJOINT = 9,   /* cluster-resident adjoint sweep         */
-  DOS_KERNEL_KINDS = 10
+  DOS_KERNEL_GEMM_PROPAGATION = 10, /* one split-BF16 DFT-GEMM propagation (4 GEMMs + 5 conversions) */
+  DOS_KERNEL_GEMM_FIELD = 11,     /* field conversions / seed / adjoint layer of the GEMM path */
+  DOS_KERNEL_KINDS = 12
 };
 
 /*
@@ -283,7 +290,7 @@ DOS_API size_t dos_workspace_bytes(const dos_ctx *ctx);
 /* Number of kernel launches queued by the last dos_forward / dos_loss / dos_backward. */
 DOS_API int dos_last_launch_count(const dos_ctx *ctx);
 
-/* Implementation chosen for the context (DOS_PATH_MULTIPASS or DOS_PATH_FUSED). */
+/* Implementation chosen for the context (DOS_PATH_MULTIPASS, _FUSED or _DFT_GEMM). */
 DOS_API int dos_path(const dos_ctx *ctx);
 
 /*

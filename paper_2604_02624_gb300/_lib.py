@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libdos.so")
 DOS_OK, DOS_ERR_ARG, DOS_ERR_OOM, DOS_ERR_CUDA, DOS_ERR_STATE, DOS_ERR_TIMEOUT, DOS_ERR_UNSUPPORTED = range(7)
 DOS_EVAN_DECAY, DOS_EVAN_ZERO = 0, 1
 DOS_LOSS_MSE, DOS_LOSS_MSE_SCALED = 0, 1
-DOS_PATH_AUTO, DOS_PATH_MULTIPASS, DOS_PATH_FUSED = 0, 1, 2
+DOS_PATH_AUTO, DOS_PATH_MULTIPASS, DOS_PATH_FUSED, DOS_PATH_DFT_GEMM = 0, 1, 2, 3
 
 ERROR_NAMES = {1: "DOS_ERR_ARG", 2: "DOS_ERR_OOM", 3: "DOS_ERR_CUDA", 4: "DOS_ERR_STATE",
                5: "DOS_ERR_TIMEOUT", 6: "DOS_ERR_UNSUPPORTED"}
@@ -32,7 +32,8 @@ EXPORTS = ("dos_supported_m", "dos_create", "dos_set_stream", "dos_forward", "do
 DOS_NOALLOC_MAX_LAMBDA = 65536
 
 KERNEL_KINDS = ("column_forward", "column_adjoint", "row_forward", "row_adjoint", "row_output",
-                "row_seed", "loss", "grad_reduce", "fused_forward", "fused_adjoint")
+                "row_seed", "loss", "grad_reduce", "fused_forward", "fused_adjoint",
+                "gemm_propagation", "gemm_field")
 
 
 class DosError(RuntimeError):

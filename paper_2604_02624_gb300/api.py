@@ -68,7 +68,7 @@ class DiffractiveStack:
         cfg.evanescent = {"decay": L.DOS_EVAN_DECAY, "zero": L.DOS_EVAN_ZERO}[evanescent]
         cfg.loss = {"mse": L.DOS_LOSS_MSE, "mse_scaled": L.DOS_LOSS_MSE_SCALED}[loss]
         cfg.path = {"auto": L.DOS_PATH_AUTO, "multipass": L.DOS_PATH_MULTIPASS,
-                    "fused": L.DOS_PATH_FUSED}[path]
+                    "fused": L.DOS_PATH_FUSED, "dft_gemm": L.DOS_PATH_DFT_GEMM}[path]
         self._ctx = None
         with torch.cuda.device(self.device):
             self._ctx = L.dos_create(cfg, torch.cuda.current_stream(self.device).cuda_stream)
@@ -108,7 +108,7 @@ class DiffractiveStack:
 
     @property
     def path(self) -> str:
-        return {1: "multipass", 2: "fused"}[L.dos_path(self._ctx)]
+        return {1: "multipass", 2: "fused", 3: "dft_gemm"}[L.dos_path(self._ctx)]
 
     # ------------------------------------------------------------------ compute
     def forward(self, h: torch.Tensor, save_for_backward: bool = True,

@@ -22,6 +22,7 @@
 
 #include "../../include/dos.h"
 #include "dos_fused.cuh"
+#include "dos_gemm.cuh"
 #include "dos_internal.h"
 
 namespace {
@@ -140,6 +141,10 @@ struct dos_ctx {
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   float* dLdI_step = nullptr;  // [nw][fov][fov] seed buffer of dos_step
+  // split-BF16 DFT-GEMM path
+  dos::GemmPlan gp = {};
+  int gchunks = 0;
+  int* h_gerr = nullptr;  // pinned
 
   template <typename T>
   int alloc(T** p, size_t count, const char* what) {
@@ -172,6 +177,8 @@ struct dos_ctx {
     allocs.clear();
     if (h_loss) cudaFreeHost(h_loss);
     h_loss = nullptr;
+    if (h_gerr) cudaFreeHost(h_gerr);
+    h_gerr = nullptr;
   }
   float2* hq_slot(int gap) const { return Hq + (size_t)gap_slot[gap] * nw * hs * hs; }
   dos::PassArgs base() const {
@@ -233,8 +240,7 @@ int validate(const dos_config* c) {
     return fail(DOS_ERR_ARG, "evanescent must be DOS_EVAN_DECAY or DOS_EVAN_ZERO");
   if (c->loss != DOS_LOSS_MSE && c->loss != DOS_LOSS_MSE_SCALED)
     return fail(DOS_ERR_ARG, "loss must be DOS_LOSS_MSE or DOS_LOSS_MSE_SCALED");
-  if (c->path != DOS_PATH_AUTO && c->path != DOS_PATH_MULTIPASS && c->path != DOS_PATH_FUSED)
-    return fail(DOS_ERR_ARG, "path must be a DOS_PATH_* value");
+  if (c->path < DOS_PATH_AUTO || c->path > DOS_PATH_DFT_GEMM) return fail(DOS_ERR_ARG, "path must be a DOS_PATH_* value");
   return DOS_OK;
 }
 
@@ -300,7 +306,38 @@ int build(dos_ctx* x, const dos_config* c) {
       partial_count = std::max(partial_count, (size_t)ncl * x->K * n2);
     }
   }
+  // split-BF16 DFT-GEMM plan (only when requested)
+  if (c->path == DOS_PATH_DFT_GEMM) {
+    auto pad = [](int v, int q) { return (v + q - 1) / q * q; };
+    x->gp.n = x->n;
+    x->gp.m = x->m;
+    x->gp.nwc = std::min(x->nw, 256);
+    x->gp.kp1 = pad(2 * x->n, 64);
+    x->gp.kp2 = pad(2 * x->m, 64);
+    x->gp.rp1 = pad(2 * x->m, 128);
+    x->gp.rp2 = pad(2 * x->n, 128);
+    x->gchunks = (x->nw + x->gp.nwc - 1) / x->gp.nwc;
+    partial_count = std::max(partial_count, (size_t)x->gchunks * x->K * n2);
+  }
   int rc;
+  if (c->path == DOS_PATH_DFT_GEMM) {
+    dos::GemmPlan& g = x->gp;
+    const size_t nwc = (size_t)g.nwc;
+    const size_t xsz = std::max({nwc * g.m * g.kp1, nwc * g.m * g.kp2, nwc * g.n * g.kp1, nwc * g.n * g.kp2});
+    const size_t dsz = std::max({(size_t)g.rp1 * nwc * g.m, (size_t)g.rp2 * nwc * g.m, (size_t)g.rp1 * nwc * g.n});
+    if ((rc = x->alloc(&g.Fh, (size_t)g.rp1 * g.kp1, "DFT matrix"))) return rc;
+    if ((rc = x->alloc(&g.Fl, (size_t)g.rp1 * g.kp1, "DFT matrix"))) return rc;
+    if ((rc = x->alloc(&g.Gh, (size_t)g.rp2 * g.kp2, "IDFT matrix"))) return rc;
+    if ((rc = x->alloc(&g.Gl, (size_t)g.rp2 * g.kp2, "IDFT matrix"))) return rc;
+    if ((rc = x->alloc(&g.Xh, xsz, "GEMM operand"))) return rc;
+    if ((rc = x->alloc(&g.Xl, xsz, "GEMM operand"))) return rc;
+    if ((rc = x->alloc(&g.D, dsz, "GEMM output"))) return rc;
+    if ((rc = x->alloc(&g.fld, nwc * n2, "GEMM field"))) return rc;
+    if ((rc = x->alloc(&g.err, 1, "GEMM error flag"))) return rc;
+    DOS_CUDA(cudaMemsetAsync(g.err, 0, sizeof(int), x->stream), "GEMM error flag");
+    DOS_CUDA(cudaMallocHost(&x->h_gerr, sizeof(int)), "cudaMallocHost(error flag)");
+    DOS_CUDA(dos::launch_build_dft(g, x->stream), "DFT matrices");
+  }
   if ((rc = x->alloc(&x->S, (size_t)x->nw * x->n * x->m, "row spectra"))) return rc;
   if ((rc = x->alloc(&x->ckpt, (size_t)x->K * x->nw * n2, "layer checkpoints"))) return rc;
   if ((rc = x->alloc(&x->o, (size_t)x->nw * x->fov * x->fov, "output field"))) return rc;
@@ -337,10 +374,91 @@ int build(dos_ctx* x, const dos_config* c) {
   return DOS_OK;
 }
 
+// ------------------------------------------------------------ split-BF16 DFT-GEMM path
+int gemm_check(dos_ctx* c) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DOS_CUDA(cudaStreamIsCapturing(c->stream, &cs), "capture status");
+  if (cs != cudaStreamCaptureStatusNone) return DOS_OK;  // checked by the next synchronising call
+  DOS_CUDA(cudaMemcpyAsync(c->h_gerr, c->gp.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "GEMM flag");
+  DOS_CUDA(cudaStreamSynchronize(c->stream), "GEMM flag");
+  if (*c->h_gerr) {
+    DOS_CUDA(cudaMemsetAsync(c->gp.err, 0, sizeof(int), c->stream), "GEMM flag");
+    return fail(DOS_ERR_TIMEOUT, "a tensor-core wait gave up (bounded mbarrier wait expired)");
+  }
+  return DOS_OK;
+}
+
+int gemm_forward(dos_ctx* c, const float* d_h, float* d_I) {
+  dos::GemmPlan& g = c->gp;
+  const size_t n2 = (size_t)c->n * c->n, hs2 = (size_t)c->hs * c->hs, f2 = (size_t)c->fov * c->fov;
+  c->launches = 0;
+  for (int w0 = 0; w0 < c->nw; w0 += g.nwc) {
+    const int nc = std::min(g.nwc, c->nw - w0);
+    DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
+              dos::gemm_prep_field(g, nc, nullptr, nullptr, nullptr, nullptr, 2, c->oa, c->ap, c->stream),
+              "GEMM aperture field");
+    for (int gap = 0; gap <= c->K; ++gap) {
+      const bool last = gap == c->K;
+      DOS_TIMED(c, DOS_KERNEL_GEMM_PROPAGATION,
+                dos::gemm_propagate(g, nc, c->hq_slot(gap) + (size_t)w0 * hs2, c->hs, false,
+                                    last ? c->o + (size_t)w0 * f2 : nullptr,
+                                    (last && d_I) ? d_I + (size_t)w0 * f2 : nullptr, c->of, c->fov, c->stream),
+                "GEMM propagation");
+      if (!last)
+        DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
+                  dos::gemm_prep_field(g, nc, g.fld, c->ckpt + ((size_t)gap * c->nw + w0) * n2, d_h + (size_t)gap * n2,
+                                       c->chan + w0, 1, 0, 0, c->stream),
+                  "GEMM layer modulation");
+      c->launches += last ? 9 : 10;
+    }
+    c->launches += 1;
+  }
+  return gemm_check(c);
+}
+
+int gemm_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
+  dos::GemmPlan& g = c->gp;
+  const size_t n2 = (size_t)c->n * c->n, hs2 = (size_t)c->hs * c->hs, f2 = (size_t)c->fov * c->fov;
+  c->launches = 0;
+  int chunk = 0;
+  for (int w0 = 0; w0 < c->nw; w0 += g.nwc, ++chunk) {
+    const int nc = std::min(g.nwc, c->nw - w0);
+    DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
+              dos::gemm_seed(g, nc, c->o + (size_t)w0 * f2, d_dLdI + (size_t)w0 * f2, c->of, c->fov, c->stream),
+              "GEMM adjoint seed");
+    DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
+              dos::gemm_prep_field(g, nc, g.fld, nullptr, nullptr, nullptr, 0, 0, 0, c->stream), "GEMM field");
+    c->launches += 2;
+    for (int l = c->K; l >= 1; --l) {
+      DOS_TIMED(c, DOS_KERNEL_GEMM_PROPAGATION,
+                dos::gemm_propagate(g, nc, c->hq_slot(l) + (size_t)w0 * hs2, c->hs, true, nullptr, nullptr, c->of,
+                                    c->fov, c->stream),
+                "GEMM adjoint propagation");
+      DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
+                dos::gemm_adj_layer(g, nc, c->ckpt + ((size_t)(l - 1) * c->nw + w0) * n2, n2,
+                                    d_h + (size_t)(l - 1) * n2, c->chan + w0,
+                                    c->partial + ((size_t)chunk * c->K + (l - 1)) * n2, c->stream),
+                "GEMM adjoint layer");
+      c->launches += 10;
+      if (l > 1) {
+        DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
+                  dos::gemm_prep_field(g, nc, g.fld, nullptr, nullptr, nullptr, 0, 0, 0, c->stream), "GEMM field");
+        ++c->launches;
+      }
+    }
+  }
+  DOS_TIMED(c, DOS_KERNEL_GRAD_REDUCE,
+            dos::launch_grad_reduce_flat(c->partial, d_dLdh, c->gchunks, (size_t)c->K * n2, c->stream),
+            "gradient reduction");
+  ++c->launches;
+  return gemm_check(c);
+}
+
 // ------------------------------------------------------------ launch sequences
 int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
   const size_t n2 = (size_t)c->n * c->n;
   c->launches = 0;
+  if (c->path == DOS_PATH_DFT_GEMM) return gemm_forward(c, d_h, d_I);
   if (c->path == DOS_PATH_FUSED) {
     dos::FusedArgs f;
     std::memset(&f, 0, sizeof(f));
@@ -395,6 +513,7 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
 int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
   const size_t n2 = (size_t)c->n * c->n;
   c->launches = 0;
+  if (c->path == DOS_PATH_DFT_GEMM) return gemm_backward(c, d_h, d_dLdI, d_dLdh);
   if (c->path == DOS_PATH_FUSED) {
     dos::FusedArgs f;
     std::memset(&f, 0, sizeof(f));
@@ -507,6 +626,14 @@ int time_choice(dos_ctx* x, const float* h0, const float* g0, float* d0, float* 
 
 int choose_path(dos_ctx* x, int requested) {
   std::ostringstream d;
+  if (requested == DOS_PATH_DFT_GEMM) {
+    x->path = DOS_PATH_DFT_GEMM;
+    x->fops = nullptr;
+    x->describe = "path=dft_gemm chunk=" + std::to_string(x->gp.nwc) + " kp=" + std::to_string(x->gp.kp1) + "/" +
+                  std::to_string(x->gp.kp2) + " rows=" + std::to_string(x->gp.rp1) + "/" + std::to_string(x->gp.rp2) +
+                  " (split-BF16, 3 terms, tcgen05)";
+    return DOS_OK;
+  }
   if (requested == DOS_PATH_MULTIPASS || x->fcands.empty()) {
     if (requested == DOS_PATH_FUSED)
       return fail(DOS_ERR_UNSUPPORTED, "no cluster-resident configuration fits this design (needs n <= m/2 and a "

@@ -1,0 +1,438 @@
+// dos_gemm.cu - split-BF16 DFT-GEMM form of the propagation (tcgen05, TMEM).
+//
+// See dos_gemm.cuh for the formulation.  The GEMM kernel: one CTA computes a
+// 128 x 256 FP32 tile in tensor memory; K is consumed in chunks of 64 bf16
+// staged in shared memory in the canonical K-major, non-swizzled core-matrix
+// layout (8 rows x 16 bytes per core matrix; 128 B between core matrices
+// along K, 1024 B between 8-row groups).  Two stages alternate: while the
+// tensor core works on one chunk (issued by one thread, completion signalled
+// to an mbarrier by tcgen05.commit) the block stages the next.  Every wait is
+// bounded: on expiry the kernel records an error flag and finishes cleanly.
+#include <cuda_bf16.h>
+
+#include "dos_gemm.cuh"
+#include "dos_internal.h"
+#include "dos_pass.cuh"
+
+namespace dos {
+
+constexpr int GTM = 128, GTN = 256, GTK = 64;
+constexpr int kGemmThreads = 128;
+constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier wait (a fraction of a second)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
+  // start >> 4 | LBO 128 B (next 8 k) | SBO 1024 B (next 8 rows) | descriptor version 1 | no swizzle
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GTN >> 3) << 17) |
+                            ((uint32_t)(GTM >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < kSpinLimit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  }
+  return done != 0;
+}
+
+struct __align__(1024) GemmSmem {
+  uint8_t a[2][GTM * GTK * 2];  // 2 x 16 KB
+  uint8_t b[2][GTN * GTK * 2];  // 2 x 32 KB
+  uint64_t bar[2];
+  uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
+  extern __shared__ __align__(1024) uint8_t gsm_raw[];
+  GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gsm_raw);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int n0 = blockIdx.x * GTN, m0 = blockIdx.y * GTM;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
+                 "r"(GTN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = sm.tmem;
+  const int kchunks = g.K / GTK;
+  const int total = g.nseg * kchunks;
+  bool ok = true;
+  int issued = 0;  // iterations whose MMAs were committed
+  for (int it = 0; it < total; ++it) {
+    const int buf = it & 1;
+    if (it >= 2) {
+      if (!mbar_wait(smem_addr(&sm.bar[buf]), (uint32_t)(((it - 2) >> 1) & 1))) ok = false;
+    }
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    const int seg = it / kchunks;
+    const int k0 = (it % kchunks) * GTK;
+    const __nv_bfloat16* A = g.a[seg];
+    const __nv_bfloat16* B = g.b[seg];
+    for (int c = tid; c < GTM * (GTK / 8); c += kGemmThreads) {
+      const int r = c / (GTK / 8), kc = c % (GTK / 8);
+      const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + r) * g.K + k0 + kc * 8);
+      *reinterpret_cast<uint4*>(sm.a[buf] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16) = v;
+    }
+    for (int c = tid; c < GTN * (GTK / 8); c += kGemmThreads) {
+      const int r = c / (GTK / 8), kc = c % (GTK / 8);
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (n0 + r < g.cols) v = *reinterpret_cast<const uint4*>(B + (size_t)(n0 + r) * g.K + k0 + kc * 8);
+      *reinterpret_cast<uint4*>(sm.b[buf] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16) = v;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t sa = smem_addr(sm.a[buf]), sb = smem_addr(sm.b[buf]);
+#pragma unroll
+      for (int kk = 0; kk < GTK / 16; ++kk) {
+        const uint64_t da = kmajor_desc(sa + kk * 256), db = kmajor_desc(sb + kk * 256);
+        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(&sm.bar[buf])));
+    }
+    issued = it + 1;
+  }
+  // the last commit covers every MMA issued before it
+  if (ok && total > 0) {
+    const int last = total - 1;
+    if (!mbar_wait(smem_addr(&sm.bar[last & 1]), (uint32_t)((last >> 1) & 1))) ok = false;
+  }
+  ok = __syncthreads_and(ok);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    float* drow = g.D + (size_t)row * g.ldd;
+    for (int c0 = 0; c0 < GTN; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(addr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      const int cb = n0 + c0;
+      if (cb + 32 <= g.cols && (g.ldd & 3) == 0) {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<float4*>(drow + cb + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                                  __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (cb + j < g.cols) drow[cb + j] = __uint_as_float(r[j]);
+      }
+    }
+  } else {
+    // give the MMAs still in flight a bounded chance to finish before the
+    // tensor memory they write is released
+    if (issued > 0) (void)mbar_wait(smem_addr(&sm.bar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
+    if (tid == 0) atomicExch(g.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GTN));
+}
+
+cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s) {
+  const size_t sm = sizeof(GemmSmem) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid((g.cols + GTN - 1) / GTN, g.rows / GTM);
+  k_tc_gemm<<<grid, kGemmThreads, sm, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ constant matrices
+__device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t i, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[i] = h;
+  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// W rows r: output o = r / 2 (re for even r, im for odd r); K index c: input
+// element c (its real part) for c < kin, input c - kin (imaginary part) for
+// kin <= c < 2 kin.  Entry exp(sign 2 pi j o x / m) in FP64, split into bf16.
+__global__ void k_dft_matrix(__nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int rows_pad, int kpad,
+                             int nout, int kin, int m, int sign) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)rows_pad * kpad) return;
+  const int r = (int)(i / kpad), c = (int)(i % kpad);
+  const int o = r / 2;
+  float v = 0.f;
+  if (o < nout && c < 2 * kin) {
+    const int x = c < kin ? c : c - kin;
+    const long e = ((long)o * x) % m;
+    double s, co;
+    sincospi(2.0 * sign * (double)e / (double)m, &s, &co);
+    // row 2o: [Re W, -Im W];  row 2o+1: [Im W, Re W]
+    if ((r & 1) == 0) v = (float)(c < kin ? co : -s);
+    else v = (float)(c < kin ? s : co);
+  }
+  split_store(hi, lo, i, v);
+}
+
+cudaError_t launch_build_dft(GemmPlan& p, cudaStream_t s) {
+  const size_t nf = (size_t)p.rp1 * p.kp1, ng = (size_t)p.rp2 * p.kp2;
+  k_dft_matrix<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(p.Fh, p.Fl, p.rp1, p.kp1, p.m, p.n, p.m, -1);
+  k_dft_matrix<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(p.Gh, p.Gl, p.rp2, p.kp2, p.n, p.m, p.m, +1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ conversion kernels
+// field (complex [w][y][x]) -> X rows (w, y): [Re(u), Im(u), 0 ...] of length kp.
+// mode 0: u = v;  mode 1: checkpoint v, u = t(h) v (forward layer);  mode 2: aperture.
+__global__ void k_prep_field(const float2* __restrict__ v, float2* __restrict__ ckpt, const float* __restrict__ h,
+                             const ChanConst* __restrict__ chan, __nv_bfloat16* __restrict__ Xh,
+                             __nv_bfloat16* __restrict__ Xl, int n, int kp, int mode, int a_off, int a_w) {
+  const int wy = blockIdx.x;  // w * n + y
+  const int w = wy / n, y = wy % n;
+  const size_t base = (size_t)wy * kp;
+  for (int c = threadIdx.x; c < kp; c += blockDim.x) {
+    float val = 0.f;
+    if (c < 2 * n) {
+      const int x = c < n ? c : c - n;
+      float2 u;
+      if (mode == 2) {
+        const bool in = y >= a_off && y < a_off + a_w && x >= a_off && x < a_off + a_w;
+        u = make_float2(in ? 1.f : 0.f, 0.f);
+      } else {
+        const float2 vv = v[(size_t)wy * n + x];
+        if (mode == 1) {
+          if (c < n) ckpt[(size_t)wy * n + x] = vv;
+          u = cmul(transmission(h[(size_t)y * n + x], chan[w]), vv);
+        } else {
+          u = vv;
+        }
+      }
+      val = c < n ? u.x : u.y;
+    }
+    split_store(Xh, Xl, base + c, val);
+  }
+}
+
+// D (rows 2k+{0,1}, cols (w, j) of width nj) -> X rows (w, k): [Re over j, Im over j, 0 ...]
+__global__ void k_prep_rows(const float* __restrict__ D, size_t ldd, __nv_bfloat16* __restrict__ Xh,
+                            __nv_bfloat16* __restrict__ Xl, int nk, int nj, int kp) {
+  const int wk = blockIdx.x;  // w * nk + k
+  const int w = wk / nk, k = wk % nk;
+  const size_t base = (size_t)wk * kp;
+  const float* dre = D + (size_t)(2 * k) * ldd + (size_t)w * nj;
+  const float* dim = dre + ldd;
+  for (int c = threadIdx.x; c < kp; c += blockDim.x) {
+    float val = 0.f;
+    if (c < nj) val = dre[c];
+    else if (c < 2 * nj) val = dim[c - nj];
+    split_store(Xh, Xl, base + c, val);
+  }
+}
+
+// D (rows 2ky+{0,1}, cols (w, kx) of width m) times H_w(|ky|,|kx|) (conj if adj)
+// -> X rows (w, kx): [Re over ky, Im over ky, 0 ...] (32 x 32 transpose in smem)
+__global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const float2* __restrict__ Hq, int hs,
+                                __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl, int m, int kp,
+                                int adj) {
+  __shared__ float2 tile[32][33];
+  const int w = blockIdx.z;
+  const int ky0 = blockIdx.y * 32, kx0 = blockIdx.x * 32;
+  const float2* Hw = Hq + (size_t)w * hs * hs;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int ky = ky0 + r, kx = kx0 + threadIdx.x;
+    float2 val = make_float2(0.f, 0.f);
+    if (ky < m && kx < m) {
+      const size_t col = (size_t)w * m + kx;
+      const float2 b = make_float2(D[(size_t)(2 * ky) * ldd + col], D[(size_t)(2 * ky + 1) * ldd + col]);
+      const float2 hv = Hw[(size_t)min(ky, m - ky) * hs + min(kx, m - kx)];
+      val = adj ? cmulc(b, hv) : cmul(b, hv);
+    }
+    tile[r][threadIdx.x] = val;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int kx = kx0 + r, ky = ky0 + threadIdx.x;
+    if (kx < m && ky < m) {
+      const float2 val = tile[threadIdx.x][r];
+      const size_t base = ((size_t)w * m + kx) * kp;
+      split_store(Xh, Xl, base + ky, val.x);
+      split_store(Xh, Xl, base + m + ky, val.y);
+    }
+  }
+  // zero the K padding of the rows this block owns (once, by the ky0 == 0 blocks)
+  if (blockIdx.y == 0) {
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int kx = kx0 + r;
+      if (kx >= m) continue;
+      const size_t base = ((size_t)w * m + kx) * kp;
+      for (int c = 2 * m + threadIdx.x; c < kp; c += 32) split_store(Xh, Xl, base + c, 0.f);
+    }
+  }
+}
+
+// D (rows 2x+{0,1}, cols (w, y)) -> field[w][y][x] (32 x 32 transpose); when o
+// is given, only the FOV is written, to o and I.
+__global__ void k_prep_out(const float* __restrict__ D, size_t ldd, float2* __restrict__ field, float2* __restrict__ o,
+                           float* __restrict__ I, int n, int of, int fov) {
+  __shared__ float2 tile[32][33];
+  const int w = blockIdx.z;
+  const int x0 = blockIdx.y * 32, y0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int x = x0 + r, y = y0 + threadIdx.x;
+    float2 val = make_float2(0.f, 0.f);
+    if (x < n && y < n) {
+      const size_t col = (size_t)w * n + y;
+      val = make_float2(D[(size_t)(2 * x) * ldd + col], D[(size_t)(2 * x + 1) * ldd + col]);
+    }
+    tile[r][threadIdx.x] = val;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int y = y0 + r, x = x0 + threadIdx.x;
+    if (x >= n || y >= n) continue;
+    const float2 val = tile[threadIdx.x][r];
+    if (o) {
+      const int fy = y - of, fx = x - of;
+      if (fy >= 0 && fy < fov && fx >= 0 && fx < fov) {
+        const size_t q = ((size_t)w * fov + fy) * fov + fx;
+        o[q] = val;
+        if (I) I[q] = fmaf(val.x, val.x, val.y * val.y);
+      }
+    } else {
+      field[((size_t)w * n + y) * n + x] = val;
+    }
+  }
+}
+
+// adjoint seed on the FOV: 2 dL/dI o, zero elsewhere
+__global__ void k_field_seed(float2* __restrict__ field, const float2* __restrict__ o, const float* __restrict__ dLdI,
+                             int n, int of, int fov, size_t total) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const size_t w = i / ((size_t)n * n);
+  const int y = (int)((i / n) % n), x = (int)(i % n);
+  const int fy = y - of, fx = x - of;
+  float2 g = make_float2(0.f, 0.f);
+  if (fy >= 0 && fy < fov && fx >= 0 && fx < fov) {
+    const size_t q = (w * fov + fy) * fov + fx;
+    g = cscale(o[q], 2.0f * dLdI[q]);
+  }
+  field[i] = g;
+}
+
+// adjoint layer: per pixel, over the chunk's channels in order:
+//   partial += Re(conj(grad_u) c t v);  grad_v = conj(t) grad_u (in place)
+__global__ void k_field_adj(float2* __restrict__ field, const float2* __restrict__ ckpt, size_t ckpt_stride,
+                            const float* __restrict__ h, const ChanConst* __restrict__ chan, float* __restrict__ partial,
+                            int nwc, int n) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t n2 = (size_t)n * n;
+  if (p >= n2) return;
+  const float hv = h[p];
+  float acc = 0.f;
+  for (int w = 0; w < nwc; ++w) {
+    const ChanConst cc = chan[w];
+    const float2 au = field[w * n2 + p];
+    const float2 tt = transmission(hv, cc);
+    const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ckpt[(size_t)w * ckpt_stride + p]));
+    acc = fmaf(au.x, cu.x, fmaf(au.y, cu.y, acc));
+    field[w * n2 + p] = cmulc(au, tt);
+  }
+  partial[p] = acc;
+}
+
+// ------------------------------------------------------------ one propagation
+struct GemmProp {
+  GemmPlan* p;
+  cudaStream_t s;
+  cudaError_t gemm(const __nv_bfloat16* Wh, const __nv_bfloat16* Wl, int rows, int K, int cols) {
+    GemmArgs g;
+    g.a[0] = Wh;
+    g.b[0] = p->Xh;
+    g.a[1] = Wh;
+    g.b[1] = p->Xl;
+    g.a[2] = Wl;
+    g.b[2] = p->Xh;
+    g.nseg = 3;
+    g.rows = rows;
+    g.cols = cols;
+    g.K = K;
+    g.D = p->D;
+    g.ldd = (size_t)cols;
+    g.err = p->err;
+    return launch_tc_gemm(g, s);
+  }
+};
+
+// X rows (w, y) of the chunk hold the field; computes the propagated field
+// (into fld) or, with o non-null, the output plane.
+cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool adj, float2* o, float* I, int of,
+                           int fov, cudaStream_t s) {
+  GemmProp g{&p, s};
+  const int n = p.n, m = p.m;
+  cudaError_t e;
+  const int c1 = nwc * n, c2 = nwc * m;
+  if ((e = g.gemm(p.Fh, p.Fl, p.rp1, p.kp1, c1)) != cudaSuccess) return e;        // row DFT
+  k_prep_rows<<<nwc * m, 128, 0, s>>>(p.D, (size_t)c1, p.Xh, p.Xl, m, n, p.kp1);
+  if ((e = g.gemm(p.Fh, p.Fl, p.rp1, p.kp1, c2)) != cudaSuccess) return e;        // column DFT
+  k_prep_spectrum<<<dim3((m + 31) / 32, (m + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c2, Hq, hs, p.Xh,
+                                                                                  p.Xl, m, p.kp2, adj ? 1 : 0);
+  if ((e = g.gemm(p.Gh, p.Gl, p.rp2, p.kp2, c2)) != cudaSuccess) return e;        // column IDFT
+  k_prep_rows<<<nwc * n, 128, 0, s>>>(p.D, (size_t)c2, p.Xh, p.Xl, n, m, p.kp2);
+  if ((e = g.gemm(p.Gh, p.Gl, p.rp2, p.kp2, c1)) != cudaSuccess) return e;        // row IDFT
+  k_prep_out<<<dim3((n + 31) / 32, (n + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c1, p.fld, o, I, n, of,
+                                                                             fov);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_prep_field(GemmPlan& p, int nwc, const float2* v, float2* ckpt, const float* h,
+                            const ChanConst* chan, int mode, int a_off, int a_w, cudaStream_t s) {
+  k_prep_field<<<nwc * p.n, 128, 0, s>>>(v, ckpt, h, chan, p.Xh, p.Xl, p.n, p.kp1, mode, a_off, a_w);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_seed(GemmPlan& p, int nwc, const float2* o, const float* dLdI, int of, int fov, cudaStream_t s) {
+  const size_t total = (size_t)nwc * p.n * p.n;
+  k_field_seed<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(p.fld, o, dLdI, p.n, of, fov, total);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_adj_layer(GemmPlan& p, int nwc, const float2* ckpt, size_t ckpt_stride, const float* h,
+                           const ChanConst* chan, float* partial, cudaStream_t s) {
+  const size_t n2 = (size_t)p.n * p.n;
+  k_field_adj<<<(unsigned)((n2 + 255) / 256), 256, 0, s>>>(p.fld, ckpt, ckpt_stride, h, chan, partial, nwc, p.n);
+  return cudaGetLastError();
+}
+
+}  // namespace dos
+

@@ -1,0 +1,72 @@
+// dos_gemm.cuh - split-BF16 DFT-as-GEMM propagation on the tcgen05 tensor cores.
+//
+// The 2D DFTs of the angular-spectrum step (Eq. 4-5) are dense complex matrix
+// products with two constant matrices shared by every channel:
+//   F[k][x] = exp(-2 pi j k x / M)   (M x N: DFT of N non-zero inputs)
+//   G[x][k] = exp(+2 pi j x k / M)   (N x M: inverse DFT keeping N outputs)
+// One propagation of a field U (N x N) is
+//   A = F U^T-rows  (row DFT),  B = F A (column DFT),  B *= H,
+//   C = G B (column IDFT),      V = C G^T-rows (row IDFT),
+// each written as Y = W X with the data matrix X stacked over channels.
+//
+// Precision: every operand is split into bf16 hi + lo (x = hi + lo to ~2^-16);
+// a product keeps three terms, W_hi X_hi + W_hi X_lo + W_lo X_hi, accumulated
+// in FP32 in tensor memory.  In real form a complex W (m x k) is a 2m x 2k
+// matrix whose row 2o is [Re W_o, -Im W_o] and row 2o+1 is [Im W_o, Re W_o];
+// the data column is [Re x; Im x], so lanes 2o / 2o+1 of the accumulator hold
+// the real / imaginary part of output o.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace dos {
+
+// One GEMM D[rows][cols] (f32, row-major, leading dimension ldd) =
+//   sum over segments s of A_s[rows][K] * B_s[cols][K]^T, A_s / B_s bf16 K-major.
+// rows % 128 == 0, K % 64 == 0; cols may be ragged (tile of 256).
+struct GemmArgs {
+  const __nv_bfloat16* a[3];
+  const __nv_bfloat16* b[3];
+  int nseg;
+  int rows, cols, K;
+  float* D;
+  size_t ldd;
+  int* err;  // set to 1 when a bounded wait gave up
+};
+
+cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s);
+
+// Context-level buffers and constants of the DFT-GEMM path.
+struct GemmPlan {
+  int n, m, nwc;            // layer side, padded size, channels per chunk
+  int kp1, kp2;             // padded K of the N- and M-point products (multiples of 64)
+  int rp1, rp2;             // padded rows of F (2M) and G (2N) (multiples of 128)
+  __nv_bfloat16 *Fh, *Fl;   // [rp1][kp1]
+  __nv_bfloat16 *Gh, *Gl;   // [rp2][kp2]
+  __nv_bfloat16 *Xh, *Xl;   // data operand, [max cols][max kp]
+  float* D;                 // GEMM output, [max rows][max cols]
+  float2* fld;              // FP32 working field [nwc][n][n]
+  int* err;
+};
+
+cudaError_t launch_build_dft(GemmPlan& p, cudaStream_t s);
+
+struct ChanConst;
+
+// One propagation (forward H or conj H) of the chunk's field held in X rows
+// (w, y); the result goes to p.fld, or to o / I on the FOV when o is given.
+cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool adj, float2* o, float* I, int of,
+                           int fov, cudaStream_t s);
+// field -> X rows: mode 0 copy, mode 1 checkpoint + Eq. 1 modulation, mode 2 aperture.
+cudaError_t gemm_prep_field(GemmPlan& p, int nwc, const float2* v, float2* ckpt, const float* h,
+                            const ChanConst* chan, int mode, int a_off, int a_w, cudaStream_t s);
+// p.fld = 2 dL/dI o on the FOV, zero elsewhere
+cudaError_t gemm_seed(GemmPlan& p, int nwc, const float2* o, const float* dLdI, int of, int fov, cudaStream_t s);
+// gradient partial of one layer over the chunk, p.fld <- conj(t) p.fld
+cudaError_t gemm_adj_layer(GemmPlan& p, int nwc, const float2* ckpt, size_t ckpt_stride, const float* h,
+                           const ChanConst* chan, float* partial, cudaStream_t s);
+
+}  // namespace dos
