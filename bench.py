@@ -45,6 +45,7 @@ def _args():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-split", action="store_true", help="skip the split-BF16 DFT-GEMM comparison")
     return p.parse_args()
 
 
@@ -358,6 +359,12 @@ def run_ours(a):
                "h2d_bytes_per_step": int(h_host.numel() * 4 + T_host.numel() * 4),
                "d2h_bytes_per_step": int(g_host.numel() * 4 + 8)}
 
+    # ---- split-BF16 DFT-GEMM form vs the FP32 path, on the precision workload
+    split = None
+    if rank == 0 and not a.no_split and world == 1:
+        stack.close()
+        split = _split_compare(dev, L, DiffractiveStack, W)
+
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
         v, c, s = _oracle_sample(w, a.cpu_seconds, h_np, T_np)
@@ -374,12 +381,51 @@ def run_ours(a):
             "gpu_launches": launches[0], "clocks": clk,
             "graph_step": {"ms_per_step": graph_ms, "value": units_per_step / (graph_ms * 1e-3),
                            "note": "forward + loss + backward replayed as one CUDA graph (dos_step)"}}
+    line["split_bf16"] = split
     if rank == 0:
         print(json.dumps(line), flush=True)
     stack.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _split_compare(dev, L, DiffractiveStack, W):
+    """Speed and deviation of the split-BF16 tensor-core DFT-GEMM path against
+    the FP32 path on the same GPU (precision workload: 4096 lambda, K = 8,
+    256 -> 512).  Errors against the FP64 oracle are measured by the tests."""
+    import torch
+    w = W.workload("precision")
+    h = torch.tensor(W.thickness(w, 0), dtype=torch.float32, device=dev)
+    T = torch.tensor(W.targets(w, 1), dtype=torch.float32, device=dev)
+    res = {}
+    outs = {}
+    for path in ("auto", "dft_gemm"):
+        st = DiffractiveStack.from_workload(w, device=dev, path=path)
+        for _ in range(1):
+            st.forward(h)
+            _, _, dl = st.loss(T, read=False)
+            st.backward(h, dl)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record()
+        for _ in range(reps):
+            I = st.forward(h)
+            _, _, dl = st.loss(T, read=False)
+            g = st.backward(h, dl)
+        e1.record()
+        torch.cuda.synchronize()
+        res[path] = {"ms_per_step": e0.elapsed_time(e1) / reps, "detail": L.dos_describe(st.handle)[:120]}
+        outs[path] = (I.double(), g.double())
+        st.close()
+    dI = float(torch.linalg.vector_norm(outs["dft_gemm"][0] - outs["auto"][0]) / torch.linalg.vector_norm(outs["auto"][0]))
+    dg = float(torch.linalg.vector_norm(outs["dft_gemm"][1] - outs["auto"][1]) / torch.linalg.vector_norm(outs["auto"][1]))
+    return {"workload": "precision: 4096 lambda x 8 layers, 256x256 padded to 512x512",
+            "fp32_path": res["auto"], "split_bf16_dft_gemm": res["dft_gemm"],
+            "speedup_vs_fp32": res["auto"]["ms_per_step"] / res["dft_gemm"]["ms_per_step"],
+            "rel_l2_intensity_vs_fp32": dI, "rel_l2_gradient_vs_fp32": dg}
 
 
 def main():

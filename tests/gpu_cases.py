@@ -15,6 +15,16 @@ TOL_INTENSITY = 1e-4
 TOL_GRAD_ORACLE = 1e-4
 TOL_GRAD_FD = 1e-3
 TOL_LOSS = 1e-4
+# Split-BF16 DFT-GEMM path.  Spec target: 1e-4.  Bound derived from the
+# arithmetic: a value held as bf16 hi + lo is exact to ~2^-18 relative and the
+# dropped lo*lo product is of the same order, so one GEMM adds ~3 * 2^-18 ~ 1.1e-5
+# relative L2 error; G chained GEMMs give ~1.1e-5 sqrt(G) on the field (twice that
+# on |o|^2).  Tests allow 4x that estimate.
+SPLIT_GEMM_EPS = 3 * 2.0 ** -18
+
+
+def split_bound(n_gemms: int, intensity: bool = False) -> float:
+    return 4 * SPLIT_GEMM_EPS * n_gemms ** 0.5 * (2 if intensity else 1)
 
 
 def rel_l2(a, b) -> float:

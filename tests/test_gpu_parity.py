@@ -14,7 +14,7 @@ from paper_2604_02624_gb300 import _lib as L
 from paper_2604_02624_gb300.api import DiffractiveStack, DosFunction
 
 from gpu_cases import (TOL_FIELD, TOL_GRAD_FD, TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS,
-                       custom, oracle_model, rel_l2, replace)
+                       custom, oracle_model, rel_l2, replace, split_bound)
 
 pytestmark = pytest.mark.gpu
 
@@ -327,4 +327,35 @@ def test_graph_step_matches_separate_calls(path):
     L2, _, dl2 = st.loss(T)
     assert val2 == L2
     assert torch.equal(g2, st.backward(h2, dl2))
+    st.close()
+
+
+# ------------------------------------------------------------ split-BF16 DFT-GEMM form
+@pytest.mark.parametrize("name,sub", [("tiny", None), ("small", None), ("massive", 16), ("precision", 16)])
+def test_split_bf16_dft_gemm_against_oracle(name, sub):
+    """The 2D DFTs as split-BF16 tcgen05 GEMMs: field, intensity and gradient
+    against the FP64 oracle within the bound the split arithmetic allows
+    (4 GEMMs per gap, K+1 gaps forward)."""
+    w = W.workload(name)
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    if sub:
+        idx = W.subset_indices(w.n_lambda, sub)
+        w, T = w.subset(idx), T[idx]
+    st = _stack(w, path="dft_gemm")
+    assert st.path == "dft_gemm"
+    hd = _t(h)
+    I = st.forward(hd)
+    o = st.output_field()
+    _, _, dl = st.loss(_t(T))
+    g = _np(st.backward(hd, dl)).astype(np.float64)
+    L_ref, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    n_gemms = 4 * (w.n_layers + 1)
+    e_field = rel_l2(_np(o).astype(np.complex128), fwd["o"])
+    e_int = rel_l2(_np(I).astype(np.float64), fwd["I"])
+    assert e_field <= split_bound(n_gemms), e_field
+    assert e_int <= split_bound(n_gemms, intensity=True), e_int
+    assert rel_l2(g, g_ref) <= TOL_GRAD_FD
+    if name in ("tiny", "small"):
+        assert e_int <= 1e-4  # north-star split-BF16 target holds for the short cascades
     st.close()
