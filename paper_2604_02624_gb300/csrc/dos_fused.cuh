@@ -126,6 +126,21 @@ struct Fused {
       rb[p] = cl.map_shared_rank(s.sp, (unsigned)(row % C)) + (size_t)(row / C) * ZS;
     }
     const int c0 = rank * MC;
+    // the next round's column values are fetched from the peers' shared memory
+    // while the current round computes (software pipeline over rounds)
+    float2 rnext[EH];
+    auto fetch = [&](int cb, float2 (&dst)[EH]) {
+      const int c = c0 + cb + l;
+      const bool ok = (cb + l) < MC && c < M;
+      const int cc = ok ? c : c0;
+#pragma unroll
+      for (int i = 0; i < EH; ++i) {
+        const int row = t + T * i;
+        const float2* src = rb[i % PERIOD] + (size_t)(i / PERIOD) * LR_STEP * ZS + cc;
+        dst[i] = (ok && row >= in_r0 && row < in_r1) ? *src : czero();
+      }
+    };
+    if constexpr (!APERTURE) fetch(0, rnext);
     for (int cb = 0; cb < MC; cb += LINES) {
       const int c = c0 + cb + l;
       const bool ok = (cb + l) < MC && c < M;
@@ -139,11 +154,8 @@ struct Fused {
         for (int i = 0; i < E; ++i) r[i] = cmul(arow[t + T * i], ac);
       } else {
 #pragma unroll
-        for (int i = 0; i < EH; ++i) {
-          const int row = t + T * i;
-          const float2* src = rb[i % PERIOD] + (size_t)(i / PERIOD) * LR_STEP * ZS + cc;
-          r[i] = (ok && row >= in_r0 && row < in_r1) ? *src : czero();
-        }
+        for (int i = 0; i < EH; ++i) r[i] = rnext[i];
+        if (cb + LINES < MC) fetch(cb + LINES, rnext);
         LF::template fft<false, PH>(r, t, z, s.tw);
       }
       if constexpr (!kPrefetchH) load_h(hreg, Hw, hs, t, cc);

@@ -3,6 +3,7 @@
 
 namespace dos {
 const FusedOps* fused_ops_m400_c4l16();
+const FusedOps* fused_ops_m400_c4l17();
 const FusedOps* fused_ops_m400_c5();
 const FusedOps* fused_ops_m400_c5l16();
 const FusedOps* fused_ops_m400_c8();
@@ -22,6 +23,7 @@ int fused_ops_for_m(int m, const FusedOps** out, int cap) {
       list[k++] = fused_ops_m400_c5();
       list[k++] = fused_ops_m400_c5l16();
       list[k++] = fused_ops_m400_c4l16();
+      list[k++] = fused_ops_m400_c4l17();
       list[k++] = fused_ops_m400_c8();
       list[k++] = fused_ops_m400_c8l16();
       list[k++] = fused_ops_m400_c10();
