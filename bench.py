@@ -359,6 +359,8 @@ def run_ours(a):
                "h2d_bytes_per_step": int(h_host.numel() * 4 + T_host.numel() * 4),
                "d2h_bytes_per_step": int(g_host.numel() * 4 + 8)}
 
+    path_name = stack.path
+    path_detail = L.dos_describe(stack.handle)
     # ---- split-BF16 DFT-GEMM form vs the FP32 path, on the precision workload
     split = None
     if rank == 0 and not a.no_split and world == 1:
@@ -375,8 +377,8 @@ def run_ours(a):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(w, world), "path": stack.path,
-            "path_detail": L.dos_describe(stack.handle), "roofline": roof,
+            "config": _config(w, world), "path": path_name,
+            "path_detail": path_detail, "roofline": roof,
             "kernels": kernel_share, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches[0], "clocks": clk,
             "graph_step": {"ms_per_step": graph_ms, "value": units_per_step / (graph_ms * 1e-3),
