@@ -121,6 +121,7 @@ struct dos_ctx {
   std::vector<void*> allocs;
   size_t bytes = 0;
   float2 *S = nullptr, *ckpt = nullptr, *o = nullptr, *Hq = nullptr, *arow = nullptr, *tw = nullptr;
+  float2* ckt = nullptr;  // transmission checkpoints of the cluster-resident path
   dos::ChanConst* chan = nullptr;
   float* partial = nullptr;
   dos::LossStats* stats = nullptr;
@@ -340,6 +341,8 @@ int build(dos_ctx* x, const dos_config* c) {
   }
   if ((rc = x->alloc(&x->S, (size_t)x->nw * x->n * x->m, "row spectra"))) return rc;
   if ((rc = x->alloc(&x->ckpt, (size_t)x->K * x->nw * n2, "layer checkpoints"))) return rc;
+  if (!x->fcands.empty() && (rc = x->alloc(&x->ckt, (size_t)x->K * x->nw * n2, "transmission checkpoints")))
+    return rc;
   if ((rc = x->alloc(&x->o, (size_t)x->nw * x->fov * x->fov, "output field"))) return rc;
   if ((rc = x->alloc(&x->Hq, (size_t)x->n_slots * x->nw * x->hs * x->hs, "transfer tables"))) return rc;
   if ((rc = x->alloc(&x->arow, (size_t)x->m, "aperture spectrum"))) return rc;
@@ -470,6 +473,7 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
     f.chan = c->chan;
     f.h = d_h;
     f.ckpt = c->ckpt;
+    f.ckt = c->ckt;
     f.o = c->o;
     f.I = d_I;
     f.n = c->n;
@@ -525,6 +529,7 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
     f.chan = c->chan;
     f.h = d_h;
     f.ckpt = c->ckpt;
+    f.ckt = c->ckt;
     f.o = c->o;
     f.dLdI = d_dLdI;
     f.partial = c->partial;

@@ -295,12 +295,15 @@ struct Line {
       static_for<0, NOQ>([&](auto k2) { r[j + PJ * k2] = b[k2]; });
     });
   }
-  template <bool INV, int NZP = P, int NOQ = Q>
+  // TRAIL: end with a barrier so that z may be rewritten right away; callers
+  // that next write a different buffer (and reach another barrier before
+  // reusing z) pass false.
+  template <bool INV, int NZP = P, int NOQ = Q, bool TRAIL = true>
   __device__ static __forceinline__ void fft(float2 (&r)[E], int t, float2* z, const float2* tw) {
     step1<INV, NZP>(r, t, z, tw);
     __syncthreads();
     step2<INV, NOQ>(r, t, z);
-    __syncthreads();
+    if constexpr (TRAIL) __syncthreads();
   }
 };
 

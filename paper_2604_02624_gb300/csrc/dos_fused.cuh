@@ -42,7 +42,8 @@ struct FusedArgs {
   const float2* tw;          // [Q * RP]
   const ChanConst* chan;     // [nw]
   const float* h;            // [K][n][n]
-  float2* ckpt;              // [K][nw][n][n]
+  float2* ckpt;              // [K][nw][n][n] incoming field v of each layer
+  float2* ckt;               // [K][nw][n][n] transmission t of each layer and channel
   float2* o;                 // [nw][fov][fov]
   float* I;                  // [nw][fov][fov] or null
   const float* dLdI;         // [nw][fov][fov]
@@ -177,7 +178,9 @@ struct Fused {
     int t, l;
   };
 
-  // forward, layer l (0-based): IDFT -> v -> [checkpoint] -> t v -> pad -> DFT
+  // forward, layer l (0-based): IDFT -> v -> [checkpoint v, t] -> t v -> pad -> DFT.
+  // The IDFT exchanges through the row's own slot, the DFT through the line's
+  // column buffer (idle in this phase), so a round needs three barriers.
   __device__ static void row_fwd_phase(const cg::cluster_group& cl, const Sm& s, const FusedArgs& a,
                                        int layer, int w) {
     const int t = threadIdx.x % T;
@@ -186,11 +189,13 @@ struct Fused {
     const ChanConst cc = a.chan[w];
     const float* hl = a.h + (size_t)layer * a.n * a.n;
     float2* ck = a.ckpt + ((size_t)layer * a.nw + w) * a.n * a.n;
+    float2* ct = a.ckt + ((size_t)layer * a.nw + w) * a.n * a.n;
+    float2* zc = s.colz + l * ZL;
     for (int j0 = 0; j0 < s.R; j0 += LINES) {
       const int j = j0 + l;
       const int row = rank + C * j;
       const bool ok = j < s.R && row < a.n;
-      float2* z = j < s.R ? s.sp + (size_t)j * ZS : s.colz + l * ZL;
+      float2* z = j < s.R ? s.sp + (size_t)j * ZS : zc;
       const float* hrow = hl + (size_t)(ok ? row : 0) * a.n;
       float hv[EH];
 #pragma unroll
@@ -202,24 +207,28 @@ struct Fused {
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = z[t + T * i];
       __syncthreads();
-      LF::template fft<true, LF::P, QH>(r, t, z, s.tw);
-      float2* ckrow = ck + (size_t)(ok ? row : 0) * a.n;
+      LF::template fft<true, LF::P, QH, false>(r, t, z, s.tw);
+      const size_t ro = (size_t)(ok ? row : 0) * a.n;
 #pragma unroll
       for (int i = 0; i < EH; ++i) {
         const int x = t + T * i;
         if (x < a.n) {
           const float2 v = r[i];
-          if (ok && a.save) ckrow[x] = v;
-          r[i] = cmul(transmission(hv[i], cc), v);
+          const float2 tt = transmission(hv[i], cc);
+          if (ok && a.save) {
+            ck[ro + x] = v;
+            ct[ro + x] = tt;
+          }
+          r[i] = cmul(tt, v);
         } else {
           r[i] = czero();
         }
       }
-      LF::template fft<false, PH>(r, t, z, s.tw);
+      LF::template fft<false, PH, LF::Q, false>(r, t, zc, s.tw);
 #pragma unroll
       for (int i = 0; i < E; ++i) z[t + T * i] = r[i];
-      __syncthreads();
     }
+    __syncthreads();
   }
 
   // first local slot whose row is >= r0
@@ -288,32 +297,34 @@ struct Fused {
     }
   }
 
-  // adjoint, layer l: IDFT -> grad_u; u = t v; partial += Re(conj(grad_u) c u);
-  // grad_v = conj(t) grad_u -> pad -> DFT (not for the first layer)
+  // adjoint, layer l: IDFT -> grad_u; u = t v (both checkpointed by the forward
+  // sweep); partial += Re(conj(grad_u) c u); grad_v = conj(t) grad_u -> pad ->
+  // DFT (not for the first layer)
   __device__ static void row_adj_phase(const cg::cluster_group& cl, const Sm& s, const FusedArgs& a,
                                        int layer, int w, float* part, bool first_channel) {
     const int t = threadIdx.x % T;
     const int l = threadIdx.x / T;
     const int rank = (int)cl.block_rank();
     const ChanConst cc = a.chan[w];
-    const float* hl = a.h + (size_t)layer * a.n * a.n;
     const float2* ck = a.ckpt + ((size_t)layer * a.nw + w) * a.n * a.n;
+    const float2* ct = a.ckt + ((size_t)layer * a.nw + w) * a.n * a.n;
     float* pl = part + (size_t)layer * a.n * a.n;
     const bool last = layer == 0;
+    float2* zc = s.colz + l * ZL;
     for (int j0 = 0; j0 < s.R; j0 += LINES) {
       const int j = j0 + l;
       const int row = rank + C * j;
       const bool ok = j < s.R && row < a.n;
-      float2* z = j < s.R ? s.sp + (size_t)j * ZS : s.colz + l * ZL;
+      float2* z = j < s.R ? s.sp + (size_t)j * ZS : zc;
       const size_t ro = (size_t)(ok ? row : 0) * a.n;
-      float hv[EH];
+      float2 tv[EH];
       float2 vv[EH];
       float pv[EH];
 #pragma unroll
       for (int i = 0; i < EH; ++i) {
         const int x = t + T * i;
         const bool in = ok && x < a.n;
-        hv[i] = in ? __ldg(hl + ro + x) : 0.f;
+        tv[i] = in ? ct[ro + x] : czero();
         vv[i] = in ? ck[ro + x] : czero();
         pv[i] = (in && !first_channel) ? pl[ro + x] : 0.f;
       }
@@ -321,28 +332,27 @@ struct Fused {
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = z[t + T * i];
       __syncthreads();
-      LF::template fft<true, LF::P, QH>(r, t, z, s.tw);
+      LF::template fft<true, LF::P, QH, false>(r, t, z, s.tw);
       const float2 cf = make_float2(cc.c_re, cc.c_im);
 #pragma unroll
       for (int i = 0; i < EH; ++i) {
         const int x = t + T * i;
         if (x < a.n) {
           const float2 au = r[i];
-          const float2 tt = transmission(hv[i], cc);
-          const float2 cu = cmul(cf, cmul(tt, vv[i]));
+          const float2 cu = cmul(cf, cmul(tv[i], vv[i]));
           if (ok) pl[ro + x] = fmaf(au.x, cu.x, fmaf(au.y, cu.y, pv[i]));
-          r[i] = cmulc(au, tt);
+          r[i] = cmulc(au, tv[i]);
         } else {
           r[i] = czero();
         }
       }
       if (!last) {
-        LF::template fft<false, PH>(r, t, z, s.tw);
+        LF::template fft<false, PH, LF::Q, false>(r, t, zc, s.tw);
 #pragma unroll
         for (int i = 0; i < E; ++i) z[t + T * i] = r[i];
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
 
   __device__ static const float2* table(const FusedArgs& a, int gap, int w) {
