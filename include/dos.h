@@ -203,6 +203,26 @@ DOS_API int dos_loss_noalloc(const float *d_I, const float *d_T, int n_lambda, i
                              int n_lambda_total, int loss, double *h_loss, float *d_psnr,
                              float *d_dLdI, void *cuda_stream);
 
+/*
+ * Output diffraction efficiency of every channel of the last forward (Section
+ * 2, Figs. 5-6): eta_w = sum over the FOV of |o_w|^2 divided by the power of
+ * the unit-amplitude input aperture (A^2).  d_eta [N_w] float32.
+ * Errors: DOS_ERR_STATE (no forward yet), DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_efficiency(dos_ctx *ctx, float *d_eta);
+
+/*
+ * Phase bit depth B of the diffractive features (Section 2, Fig. 7): every
+ * thickness, limited to [0, h_max], is replaced by the nearest of the 2^B
+ * levels k h_max / (2^B - 1).  The level index is decided in FP32:
+ * k = rint(fp32(clamp(h)) * fp32((2^B - 1) / h_max)), value k * fp32(h_max / (2^B - 1)).
+ *   d_h, d_hq  `count` float32 values (may alias); h_max > 0 [m]; 1 <= bits <= 24.
+ *   cuda_stream  stream to queue on (NULL: legacy default stream).
+ * Errors: DOS_ERR_ARG, DOS_ERR_CUDA.
+ */
+DOS_API int dos_quantize_thickness(const float *d_h, float *d_hq, size_t count, double h_max, int bits,
+                                   void *cuda_stream);
+
 /* Copies the loss of the last dos_loss to *h_loss (waits for the stream). */
 DOS_API int dos_read_loss(dos_ctx *ctx, double *h_loss);
 

@@ -288,3 +288,29 @@ def rayleigh_sommerfeld_direct(u: np.ndarray, lam: float, z: float, pitch: float
             * np.exp(1j * TWO_PI * n_medium * r / lam)
         out[p] = np.sum(us * w) * pitch ** 2
     return out.reshape(n, n)
+
+
+# --------------------------------------------------------------------------
+# Evaluation variants of a trained design (Section 2 Fig. 5-7, Section 3)
+# --------------------------------------------------------------------------
+def quantize_thickness(h, h_max, bits):
+    """Phase bit depth B (Fig. 7): the learnable thickness, limited to
+    [0, h_max], takes one of 2^B evenly spaced levels k h_max / (2^B - 1).
+
+    The level index is an integer decided by floating point, so it is taken
+    in FP32 exactly as the CUDA path takes it: k = rint(fp32(clip(h)) * s)
+    with s = fp32((2^B - 1) / h_max), value = fp32(k * fp32(h_max / (2^B - 1))).
+    """
+    levels = 2 ** bits - 1
+    s = np.float32(levels / h_max)
+    step = np.float32(h_max / levels)
+    hc = np.clip(np.asarray(h, np.float32), np.float32(0.0), np.float32(h_max))
+    k = np.rint(hc * s).astype(np.float32)
+    return (k * step).astype(np.float32)
+
+
+def diffraction_efficiency(I, aperture):
+    """Output diffraction efficiency (Section 2, Fig. 5): power on the output
+    FOV over the power of the unit-amplitude input aperture (A^2 pixels)."""
+    I = np.asarray(I, np.float64)
+    return I.reshape(I.shape[0], -1).sum(axis=1) / float(aperture * aperture)

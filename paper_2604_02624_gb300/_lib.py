@@ -27,7 +27,7 @@ EXPORTS = ("dos_supported_m", "dos_create", "dos_set_stream", "dos_forward", "do
            "dos_read_loss", "dos_backward", "dos_step", "dos_output_field", "dos_layer_field",
            "dos_propagate", "dos_set_timing", "dos_kernel_time", "dos_workspace_bytes",
            "dos_last_launch_count", "dos_path", "dos_describe", "dos_destroy", "dos_last_error",
-           "dos_loss_noalloc")
+           "dos_loss_noalloc", "dos_efficiency", "dos_quantize_thickness")
 
 DOS_NOALLOC_MAX_LAMBDA = 65536
 
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dos_destroy": (None, [p]),
         "dos_last_error": (ctypes.c_char_p, []),
         "dos_loss_noalloc": (c_int, [p, p, c_int, c_int, c_int, c_int, POINTER(c_double), p, p, p]),
+        "dos_efficiency": (c_int, [p, p]),
+        "dos_quantize_thickness": (c_int, [p, p, c_size_t, c_double, c_int, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -214,3 +216,11 @@ def dos_loss_noalloc(d_I: int, d_T: int, n_lambda: int, fov: int, n_lambda_total
                                    ctypes.byref(out) if read_loss else None, d_psnr or None,
                                    d_dLdI or None, stream or None), "dos_loss_noalloc")
     return out.value if read_loss else None
+
+
+def dos_efficiency(ctx: int, d_eta: int) -> None:
+    _check(load().dos_efficiency(ctx, d_eta), "dos_efficiency")
+
+
+def dos_quantize_thickness(d_h: int, d_hq: int, count: int, h_max: float, bits: int, stream: int) -> None:
+    _check(load().dos_quantize_thickness(d_h, d_hq, count, h_max, bits, stream or None), "dos_quantize_thickness")

@@ -169,6 +169,13 @@ class DiffractiveStack:
                          psnr_out.data_ptr() if psnr_out is not None else 0, read)
         return val, g
 
+    def efficiency(self) -> torch.Tensor:
+        """Output diffraction efficiency of every channel of the last forward."""
+        eta = torch.empty(self.n_lambda, dtype=torch.float32, device=self.device)
+        self._bind()
+        L.dos_efficiency(self._ctx, eta.data_ptr())
+        return eta
+
     def output_field(self) -> torch.Tensor:
         o = torch.empty((self.n_lambda, self.fov, self.fov), dtype=torch.complex64, device=self.device)
         self._bind()
@@ -207,3 +214,41 @@ class DosFunction(torch.autograd.Function):
         (h,) = ctx.saved_tensors
         g = ctx.stack.backward(h, gI.contiguous().to(torch.float32))
         return g, None
+
+
+def quantize_thickness(h: torch.Tensor, h_max: float, bits: int) -> torch.Tensor:
+    """Thickness limited to [0, h_max] and rounded to 2^bits levels (phase bit depth)."""
+    if not h.is_cuda or h.dtype != torch.float32:
+        raise TypeError("h must be a float32 CUDA tensor")
+    h = h.contiguous()
+    out = torch.empty_like(h)
+    L.dos_quantize_thickness(h.data_ptr(), out.data_ptr(), h.numel(), float(h_max), int(bits),
+                             torch.cuda.current_stream(h.device).cuda_stream)
+    return out
+
+
+def detuning_psnr(design: dict, h: torch.Tensor, T: torch.Tensor, offsets, path: str = "auto",
+                  device=None) -> torch.Tensor:
+    """PSNR of every channel when it is probed at lambda_w + delta for each
+    delta in ``offsets`` [m] (Section 3: robustness to probe-wavelength drift).
+
+    ``design`` holds the DiffractiveStack keyword arguments of the trained
+    design; the probe design evaluates all N_w x len(offsets) wavelengths in one
+    context (material index and loss of the nominal channel).  Returns a
+    [N_w, len(offsets)] tensor."""
+    offsets = np.asarray(offsets, dtype=np.float64)
+    lam = np.asarray(design["lambdas"], dtype=np.float64)
+    nw, npr = lam.shape[0], offsets.shape[0]
+    probe = dict(design)
+    probe["lambdas"] = (lam[:, None] + offsets[None, :]).ravel()
+    for key in ("n_index", "kappa"):
+        if probe.get(key) is not None:
+            probe[key] = np.repeat(np.broadcast_to(np.asarray(probe[key], np.float64), (nw,)), npr)
+    st = DiffractiveStack(path=path, device=device or h.device, **probe)
+    try:
+        st.forward(h, save_for_backward=False, want_intensity=False)
+        Tp = T.repeat_interleave(npr, dim=0).contiguous()
+        _, psnr, _ = st.loss(Tp, read=False, psnr=True, grad=False)
+        return psnr.view(nw, npr).clone()
+    finally:
+        st.close()

@@ -813,6 +813,26 @@ DOS_API int dos_loss(dos_ctx* c, const float* d_T, double* h_loss, float* d_psnr
   return DOS_OK;
 }
 
+DOS_API int dos_efficiency(dos_ctx* c, float* d_eta) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  if (!c->have_fwd) return fail(DOS_ERR_STATE, "dos_efficiency needs a dos_forward first");
+  if (!d_eta) return fail(DOS_ERR_ARG, "d_eta is NULL");
+  DOS_CUDA(dos::launch_efficiency(c->o, d_eta, c->nw, c->fov * c->fov, c->ap, c->stream), "efficiency");
+  c->launches = 1;
+  return DOS_OK;
+}
+
+DOS_API int dos_quantize_thickness(const float* d_h, float* d_hq, size_t count, double h_max, int bits,
+                                   void* cuda_stream) {
+  if (!d_h || !d_hq) return fail(DOS_ERR_ARG, "d_h and d_hq are required");
+  if (!(h_max > 0) || !std::isfinite(h_max)) return fail(DOS_ERR_ARG, "h_max must be > 0");
+  if (bits < 1 || bits > 24) return fail(DOS_ERR_ARG, "bits must be in [1, 24]");
+  if (count == 0) return DOS_OK;
+  DOS_CUDA(dos::launch_quantize(d_h, d_hq, count, h_max, bits, static_cast<cudaStream_t>(cuda_stream)), "quantize");
+  return DOS_OK;
+}
+
 DOS_API int dos_read_loss(dos_ctx* c, double* h_loss) {
   int rc = check_ctx(c);
   if (rc) return rc;

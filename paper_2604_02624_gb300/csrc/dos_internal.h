@@ -85,4 +85,8 @@ cudaError_t launch_grad_reduce(const float* partial, float* grad, int n_chunks, 
 cudaError_t launch_grad_reduce_flat(const float* partial, float* grad, int n_parts, size_t count,
                                     cudaStream_t s);
 
+// Evaluation variants (dos_eval.cu).
+cudaError_t launch_quantize(const float* h, float* q, size_t count, double h_max, int bits, cudaStream_t s);
+cudaError_t launch_efficiency(const float2* o, float* eta, int nw, int fov2, int aperture, cudaStream_t s);
+
 }  // namespace dos

@@ -1,0 +1,79 @@
+"""GPU parity of the evaluation variants (NEXT-2): phase bit depth,
+diffraction efficiency and probe-wavelength detuning, against the oracle."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dos_oracle as O
+from paper_2604_02624_gb300 import _lib as L
+from paper_2604_02624_gb300 import workloads as W
+from paper_2604_02624_gb300.api import DiffractiveStack, detuning_psnr, quantize_thickness
+
+from gpu_cases import TOL_INTENSITY, oracle_model, rel_l2
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not os.path.exists(L.LIB_PATH):
+        from paper_2604_02624_gb300 import build
+        build.build()
+    L.load()
+    torch.cuda.set_device(DEV)
+
+
+@pytest.mark.parametrize("bits", [1, 4, 6, 8, 16])
+def test_quantisation_is_bit_exact(bits):
+    rng = np.random.default_rng(bits)
+    hmax = 664.5e-9
+    h = rng.uniform(-0.2 * hmax, 1.2 * hmax, 100003).astype(np.float32)
+    q = quantize_thickness(torch.tensor(h, device=DEV), hmax, bits).cpu().numpy()
+    assert np.array_equal(q, O.quantize_thickness(h, hmax, bits))
+
+
+def test_quantised_design_forward_matches_oracle():
+    w = W.workload("small")
+    h = W.thickness(w, 0)
+    hq = quantize_thickness(torch.tensor(h, dtype=torch.float32, device=DEV), 664.5e-9, 4)
+    st = DiffractiveStack.from_workload(w, device=DEV)
+    I = st.forward(hq)
+    ref = O.forward(hq.cpu().numpy().astype(np.float64), **oracle_model(w))
+    assert rel_l2(I.cpu().numpy().astype(np.float64), ref["I"]) <= TOL_INTENSITY
+    st.close()
+
+
+@pytest.mark.parametrize("path", ["multipass", "fused"])
+def test_efficiency_matches_oracle(path):
+    w = W.workload("small")
+    h = W.thickness(w, 0)
+    st = DiffractiveStack.from_workload(w, device=DEV, path=path)
+    st.forward(torch.tensor(h, dtype=torch.float32, device=DEV))
+    eta = st.efficiency().cpu().numpy().astype(np.float64)
+    ref = O.diffraction_efficiency(O.forward(h, keep_fields=False, **oracle_model(w))["I"], w.aperture)
+    assert rel_l2(eta, ref) <= TOL_INTENSITY
+    st.close()
+
+
+def test_detuning_psnr():
+    w = W.workload("tiny")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    design = dict(n=w.n, m=w.m, n_layers=w.n_layers, lambdas=w.lambdas, gaps=w.gaps, pitch=w.pitch,
+                  n_index=w.n_index, kappa=w.kappa, fov=w.fov, aperture=w.aperture)
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    Td = torch.tensor(T, dtype=torch.float32, device=DEV)
+    offsets = np.array([-2e-9, 0.0, 2e-9])
+    p = detuning_psnr(design, hd, Td, offsets, path="multipass").cpu().numpy()
+    st = DiffractiveStack(path="multipass", device=DEV, **design)
+    st.forward(hd)
+    _, nominal, _ = st.loss(Td)
+    assert np.array_equal(p[:, 1], nominal.cpu().numpy())
+    ws = w.subset(np.arange(w.n_lambda))
+    ws.lambdas = w.lambdas + offsets[2]
+    ref = O.mse_loss(O.forward(h, keep_fields=False, **oracle_model(ws))["I"], T)[1]
+    assert np.max(np.abs(p[:, 2] - ref)) <= 1e-3
+    st.close()

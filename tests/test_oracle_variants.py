@@ -1,0 +1,45 @@
+"""Pins of the oracle's evaluation variants (quantisation, efficiency)."""
+import numpy as np
+
+from oracle import dos_oracle as O
+
+
+def test_one_bit_keeps_the_two_end_levels():
+    h = np.array([0.0, 0.2, 0.49, 0.51, 0.9, 1.0, 1.7, -0.3]) * 664.5e-9
+    q = O.quantize_thickness(h, 664.5e-9, 1)
+    assert set(np.round(q / 664.5e-9, 6)) <= {0.0, 1.0}
+    assert q[0] == 0 and q[2] == 0 and q[3] > 0 and q[6] == q[5]
+
+
+def test_quantisation_error_is_at_most_half_a_step_and_idempotent():
+    rng = np.random.default_rng(0)
+    hmax = 664.5e-9
+    h = rng.uniform(0, hmax, 10000)
+    for bits in (4, 6, 8, 16):
+        q = O.quantize_thickness(h, hmax, bits)
+        step = hmax / (2 ** bits - 1)
+        # half a step, plus the FP32 rounding of the level decision h * s (ulp of
+        # a number near 2^B is 2^(B-23) steps) and of the stored values
+        slack = 0.5 * step * 2.0 ** (bits - 22) + 4 * np.spacing(np.float32(hmax))
+        assert np.max(np.abs(q - h.astype(np.float32))) <= 0.5 * step + slack
+        assert np.array_equal(O.quantize_thickness(q, hmax, bits), q)
+        assert len(np.unique(q)) <= 2 ** bits
+
+
+def test_efficiency_of_an_unobstructed_zero_gap_system():
+    """With zero gaps and lossless flat layers the output equals the input
+    aperture, so the efficiency is the fraction of the aperture the FOV sees."""
+    n, a, f = 16, 10, 6
+    out = O.forward(np.zeros((1, n, n)), [600e-9], [0.0, 0.0], 0.3e-6, 32, f, a, 1.5, 0.0)
+    eta = O.diffraction_efficiency(out["I"], a)
+    assert abs(eta[0] - f * f / (a * a)) < 1e-14
+    out2 = O.forward(np.zeros((1, n, n)), [600e-9], [0.0, 0.0], 0.3e-6, 32, 12, 8, 1.5, 0.0)
+    assert abs(O.diffraction_efficiency(out2["I"], 8)[0] - 1.0) < 1e-14
+
+
+def test_efficiency_never_exceeds_one_for_lossless_propagation():
+    rng = np.random.default_rng(1)
+    h = rng.uniform(0, 600e-9, (2, 24, 24))
+    out = O.forward(h, [500e-9, 700e-9], [5e-6, 7e-6, 6e-6], 0.3e-6, 48, 24, 12, 1.6, 0.0)
+    eta = O.diffraction_efficiency(out["I"], 12)
+    assert np.all(eta <= 1 + 1e-12) and np.all(eta > 0)
