@@ -77,3 +77,20 @@ def test_detuning_psnr():
     ref = O.mse_loss(O.forward(h, keep_fields=False, **oracle_model(ws))["I"], T)[1]
     assert np.max(np.abs(p[:, 2] - ref)) <= 1e-3
     st.close()
+
+
+def test_fine_tune_after_channel_swap_lowers_the_loss():
+    """The fine-tuning driver (Adam on h through the graph-captured step) lowers
+    the swapped design's loss."""
+    from paper_2604_02624_gb300.design import channel_swap, fine_tune
+    w = W.workload("small")
+    h = torch.tensor(W.thickness(w, 0), dtype=torch.float32, device=DEV)
+    T = torch.tensor(W.targets(w, 1), dtype=torch.float32, device=DEV)
+    st = DiffractiveStack.from_workload(w, device=DEV, loss="mse_scaled")
+    st.forward(h)
+    _, psnr, _ = st.loss(T)
+    perm = channel_swap(psnr.cpu().numpy(), w.lambdas)
+    Ts = T[torch.tensor(perm, device=DEV)].contiguous()
+    _, losses = fine_tune(st, h, Ts, steps=30, lr=1e-2, h_max=664.5e-9)
+    assert losses[-1] < 0.9 * losses[0], losses
+    st.close()
