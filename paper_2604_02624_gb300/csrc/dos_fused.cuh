@@ -190,7 +190,9 @@ struct Fused {
     const float* hl = a.h + (size_t)layer * a.n * a.n;
     float2* ck = a.ckpt + ((size_t)layer * a.nw + w) * a.n * a.n;
     float2* ct = a.ckt + ((size_t)layer * a.nw + w) * a.n * a.n;
-    float2* zc = s.colz + l * ZL;
+    // the column buffers double as row-phase exchange space, at the row-slot
+    // stride (ZS): with the row phase's thread layout that stride is conflict-free
+    float2* zc = s.colz + l * ZS;
     for (int j0 = 0; j0 < s.R; j0 += LINES) {
       const int j = j0 + l;
       const int row = rank + C * j;
@@ -310,7 +312,9 @@ struct Fused {
     const float2* ct = a.ckt + ((size_t)layer * a.nw + w) * a.n * a.n;
     float* pl = part + (size_t)layer * a.n * a.n;
     const bool last = layer == 0;
-    float2* zc = s.colz + l * ZL;
+    // the column buffers double as row-phase exchange space, at the row-slot
+    // stride (ZS): with the row phase's thread layout that stride is conflict-free
+    float2* zc = s.colz + l * ZS;
     for (int j0 = 0; j0 < s.R; j0 += LINES) {
       const int j = j0 + l;
       const int row = rank + C * j;
