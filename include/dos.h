@@ -204,6 +204,22 @@ DOS_API int dos_loss_noalloc(const float *d_I, const float *d_T, int n_lambda, i
                              float *d_dLdI, void *cuda_stream);
 
 /*
+ * Misaligned layers (Section 3, "vaccination" against lateral and axial
+ * displacements during training).  h_disp [K][3] holds the displacement
+ * (dx, dy, dz) [m] of layers 1..K, or NULL to restore the aligned design.
+ * The input aperture and the output plane stay fixed.  A layer displaced by D
+ * modulates with t(r - D); as free space is shift invariant this equals
+ * giving gap g the transfer function
+ *   H(z_g + dz_{g+1} - dz_g) * exp(-2 pi j (fx a_x + fy a_y)),  a = D_g - D_{g+1},
+ * which is how the engine applies it (exact up to the layer window).
+ * Applies to every later dos_forward / dos_backward / dos_step / dos_propagate
+ * until changed; a backward must follow a forward with the same setting.
+ * The first call builds a table of sqrt(|q|) (N_w (M/2+1)^2 floats, FP64 roots).
+ * Errors: DOS_ERR_ARG, DOS_ERR_OOM, DOS_ERR_CUDA.
+ */
+DOS_API int dos_set_misalignment(dos_ctx *ctx, const double *h_disp);
+
+/*
  * Output diffraction efficiency of every channel of the last forward (Section
  * 2, Figs. 5-6): eta_w = sum over the FOV of |o_w|^2 divided by the power of
  * the unit-amplitude input aperture (A^2).  d_eta [N_w] float32.

@@ -89,6 +89,31 @@ def transfer_function(lam: float, z: float, m: int, pitch: float,
     return H
 
 
+def gap_transfer(lam, gaps, g, m, pitch, n_medium=1.0, evanescent="decay", displacements=None):
+    """Transfer function of gap g (from plane g to plane g+1; plane 0 is the
+    input aperture, plane K+1 the detector, both fixed).
+
+    ``displacements`` (K x 3: dx, dy, dz of layers 1..K [m]) describe
+    misaligned layers (Section 3, "vaccination").  A layer displaced by D
+    modulates with t(r - D); because free space is shift invariant this equals
+    shifting the field by -D before the modulation and by +D after it, so gap g
+    carries the lateral shift D_g - D_{g+1}, i.e. the factor
+    exp(-2 pi j (fx a_x + fy a_y)), and its length becomes z_g + dz_{g+1} - dz_g.
+    """
+    z = gaps[g]
+    if displacements is None:
+        return transfer_function(lam, z, m, pitch, n_medium, evanescent)
+    d = np.asarray(displacements, np.float64)
+    k = d.shape[0]
+    pad = np.zeros((k + 2, 3))
+    pad[1:k + 1] = d
+    a = pad[g] - pad[g + 1]
+    H = transfer_function(lam, z + pad[g + 1, 2] - pad[g, 2], m, pitch, n_medium, evanescent)
+    f = spatial_frequencies(m, pitch)
+    ramp = np.exp(-1j * TWO_PI * (f[None, :] * a[0] + f[:, None] * a[1]))
+    return H * ramp
+
+
 def propagate(u: np.ndarray, H: np.ndarray) -> np.ndarray:
     """P_z(u) = crop_N( IDFT( H * DFT( pad_M(u) ) ) ).
 
@@ -137,7 +162,7 @@ def aperture_field(n: int, a: int) -> np.ndarray:
 # Forward model of one design (all channels)
 # --------------------------------------------------------------------------
 def forward(h, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
-            n_medium=1.0, h_base=0.0, evanescent="decay", keep_fields=True):
+            n_medium=1.0, h_base=0.0, evanescent="decay", keep_fields=True, displacements=None):
     """Run every channel through the K-layer cascade.
 
     h: (K, N, N) thicknesses.  Returns a dict with
@@ -160,13 +185,13 @@ def forward(h, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
     for w in range(nw):
         lam = lambdas[w]
         v = propagate(aperture_field(n, aperture),
-                      transfer_function(lam, gaps[0], m, pitch, n_medium, evanescent))
+                      gap_transfer(lam, gaps, 0, m, pitch, n_medium, evanescent, displacements))
         for l in range(k_layers):
             if keep_fields:
                 v_all[w, l] = v
             u = transmission(h[l], lam, n_index[w], kappa[w], n_medium, h_base) * v
-            v = propagate(u, transfer_function(lam, gaps[l + 1], m, pitch, n_medium,
-                                               evanescent))
+            v = propagate(u, gap_transfer(lam, gaps, l + 1, m, pitch, n_medium, evanescent,
+                                          displacements))
         o_all[w] = v[of:of + fov, of:of + fov]
     return {"o": o_all, "I": np.abs(o_all) ** 2, "v": v_all}
 
@@ -204,7 +229,7 @@ def mse_loss(I, T, scaled=False):
 # Gradient by the adjoint of the cascade
 # --------------------------------------------------------------------------
 def backward(h, fwd, dLdI, lambdas, gaps, pitch, m, fov, n_index, kappa,
-             n_medium=1.0, h_base=0.0, evanescent="decay"):
+             n_medium=1.0, h_base=0.0, evanescent="decay", displacements=None):
     """dL/dh (K, N, N) for a real loss with gradient ``dLdI`` w.r.t. I = |o|^2.
 
     Convention: for complex z, grad_z L = dL/dRe z + j dL/dIm z.
@@ -228,7 +253,7 @@ def backward(h, fwd, dLdI, lambdas, gaps, pitch, m, fov, n_index, kappa,
         g = np.zeros((n, n), dtype=np.complex128)
         g[of:of + fov, of:of + fov] = 2.0 * dLdI[w] * fwd["o"][w]
         for l in reversed(range(k_layers)):
-            H = transfer_function(lam, gaps[l + 1], m, pitch, n_medium, evanescent)
+            H = gap_transfer(lam, gaps, l + 1, m, pitch, n_medium, evanescent, displacements)
             a_u = propagate_adjoint(g, H)
             t = transmission(h[l], lam, n_index[w], kappa[w], n_medium, h_base)
             u = t * fwd["v"][w, l]
@@ -239,19 +264,19 @@ def backward(h, fwd, dLdI, lambdas, gaps, pitch, m, fov, n_index, kappa,
 
 
 def loss_and_grad(h, T, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
-                  n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False):
+                  n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False, displacements=None):
     fwd = forward(h, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
-                  n_medium, h_base, evanescent)
+                  n_medium, h_base, evanescent, displacements=displacements)
     L, psnr, dLdI = mse_loss(fwd["I"], T, scaled)
     grad = backward(h, fwd, dLdI, lambdas, gaps, pitch, m, fov, n_index, kappa,
-                    n_medium, h_base, evanescent)
+                    n_medium, h_base, evanescent, displacements=displacements)
     return L, psnr, grad, fwd
 
 
 def loss_only(h, T, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
-              n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False):
+              n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False, displacements=None):
     fwd = forward(h, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
-                  n_medium, h_base, evanescent, keep_fields=False)
+                  n_medium, h_base, evanescent, keep_fields=False, displacements=displacements)
     return mse_loss(fwd["I"], T, scaled)[0]
 
 

@@ -27,7 +27,7 @@ EXPORTS = ("dos_supported_m", "dos_create", "dos_set_stream", "dos_forward", "do
            "dos_read_loss", "dos_backward", "dos_step", "dos_output_field", "dos_layer_field",
            "dos_propagate", "dos_set_timing", "dos_kernel_time", "dos_workspace_bytes",
            "dos_last_launch_count", "dos_path", "dos_describe", "dos_destroy", "dos_last_error",
-           "dos_loss_noalloc", "dos_efficiency", "dos_quantize_thickness")
+           "dos_loss_noalloc", "dos_efficiency", "dos_quantize_thickness", "dos_set_misalignment")
 
 DOS_NOALLOC_MAX_LAMBDA = 65536
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dos_last_error": (ctypes.c_char_p, []),
         "dos_loss_noalloc": (c_int, [p, p, c_int, c_int, c_int, c_int, POINTER(c_double), p, p, p]),
         "dos_efficiency": (c_int, [p, p]),
+        "dos_set_misalignment": (c_int, [p, POINTER(c_double)]),
         "dos_quantize_thickness": (c_int, [p, p, c_size_t, c_double, c_int, p]),
     }
     for name, (res, args) in sig.items():
@@ -224,3 +225,13 @@ def dos_efficiency(ctx: int, d_eta: int) -> None:
 
 def dos_quantize_thickness(d_h: int, d_hq: int, count: int, h_max: float, bits: int, stream: int) -> None:
     _check(load().dos_quantize_thickness(d_h, d_hq, count, h_max, bits, stream or None), "dos_quantize_thickness")
+
+
+def dos_set_misalignment(ctx: int, disp) -> None:
+    """disp: None or a (K, 3) float64 array of layer displacements [m]."""
+    if disp is None:
+        _check(load().dos_set_misalignment(ctx, None), "dos_set_misalignment")
+        return
+    import numpy as np
+    arr = np.ascontiguousarray(disp, dtype=np.float64)
+    _check(load().dos_set_misalignment(ctx, arr.ctypes.data_as(POINTER(c_double))), "dos_set_misalignment")

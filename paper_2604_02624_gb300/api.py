@@ -169,6 +169,14 @@ class DiffractiveStack:
                          psnr_out.data_ptr() if psnr_out is not None else 0, read)
         return val, g
 
+    def set_misalignment(self, displacements=None) -> None:
+        """Displace layers 1..K by (dx, dy, dz) [m] (a (K, 3) array), or None."""
+        if displacements is not None:
+            displacements = np.asarray(displacements, dtype=np.float64)
+            if displacements.shape != (self.n_layers, 3):
+                raise ValueError("displacements must have shape (n_layers, 3)")
+        L.dos_set_misalignment(self._ctx, displacements)
+
     def efficiency(self) -> torch.Tensor:
         """Output diffraction efficiency of every channel of the last forward."""
         eta = torch.empty(self.n_lambda, dtype=torch.float32, device=self.device)

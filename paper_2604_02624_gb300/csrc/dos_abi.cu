@@ -140,8 +140,23 @@ struct dos_ctx {
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  const void* gkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   float* dLdI_step = nullptr;  // [nw][fov][fov] seed buffer of dos_step
+  // misaligned layers (Section 3, "vaccination")
+  double* d_lam = nullptr;      // wavelengths on the device (kept for the root table)
+  float* sq = nullptr;          // signed sqrt(|q|) quadrant table, built on first use
+  bool mis_on = false;
+  std::vector<float> mis;       // (K+1) x 3 per gap: lateral shift x, y and length change [m]
+  long mis_gen = 0;
+  dos::Misalign gap_mis(int g) const {
+    dos::Misalign m;
+    m.sq = mis_on ? sq : nullptr;
+    m.df = (float)(1.0 / ((double)this->m * pitch));
+    m.ax = mis_on ? mis[3 * g] : 0.f;
+    m.ay = mis_on ? mis[3 * g + 1] : 0.f;
+    m.dz = mis_on ? mis[3 * g + 2] : 0.f;
+    return m;
+  }
   // split-BF16 DFT-GEMM path
   dos::GemmPlan gp = {};
   int gchunks = 0;
@@ -356,6 +371,7 @@ int build(dos_ctx* x, const dos_config* c) {
 
   double *d_lam = nullptr, *d_nidx = nullptr, *d_kap = nullptr;
   if ((rc = x->alloc(&d_lam, (size_t)x->nw, "wavelengths"))) return rc;
+  x->d_lam = d_lam;
   if ((rc = x->alloc(&d_nidx, (size_t)x->nw, "indices"))) return rc;
   if ((rc = x->alloc(&d_kap, (size_t)x->nw, "extinction"))) return rc;
   const size_t db = sizeof(double) * x->nw;
@@ -402,10 +418,12 @@ int gemm_forward(dos_ctx* c, const float* d_h, float* d_I) {
               "GEMM aperture field");
     for (int gap = 0; gap <= c->K; ++gap) {
       const bool last = gap == c->K;
+      dos::Misalign mg = c->gap_mis(gap);
+      if (mg.sq) mg.sq += (size_t)w0 * hs2;
       DOS_TIMED(c, DOS_KERNEL_GEMM_PROPAGATION,
                 dos::gemm_propagate(g, nc, c->hq_slot(gap) + (size_t)w0 * hs2, c->hs, false,
                                     last ? c->o + (size_t)w0 * f2 : nullptr,
-                                    (last && d_I) ? d_I + (size_t)w0 * f2 : nullptr, c->of, c->fov, c->stream),
+                                    (last && d_I) ? d_I + (size_t)w0 * f2 : nullptr, c->of, c->fov, mg, c->stream),
                 "GEMM propagation");
       if (!last)
         DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
@@ -433,9 +451,11 @@ int gemm_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dL
               dos::gemm_prep_field(g, nc, g.fld, nullptr, nullptr, nullptr, 0, 0, 0, c->stream), "GEMM field");
     c->launches += 2;
     for (int l = c->K; l >= 1; --l) {
+      dos::Misalign mg = c->gap_mis(l);
+      if (mg.sq) mg.sq += (size_t)w0 * hs2;
       DOS_TIMED(c, DOS_KERNEL_GEMM_PROPAGATION,
                 dos::gemm_propagate(g, nc, c->hq_slot(l) + (size_t)w0 * hs2, c->hs, true, nullptr, nullptr, c->of,
-                                    c->fov, c->stream),
+                                    c->fov, mg, c->stream),
                 "GEMM adjoint propagation");
       DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
                 dos::gemm_adj_layer(g, nc, c->ckpt + ((size_t)(l - 1) * c->nw + w0) * n2, n2,
@@ -476,6 +496,14 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
     f.ckt = c->ckt;
     f.o = c->o;
     f.I = d_I;
+    f.sq = c->mis_on ? c->sq : nullptr;
+    f.df = (float)(1.0 / ((double)c->m * c->pitch));
+    for (int g = 0; g <= c->K; ++g) {
+      const dos::Misalign mg = c->gap_mis(g);
+      f.mis[g][0] = mg.ax;
+      f.mis[g][1] = mg.ay;
+      f.mis[g][2] = mg.dz;
+    }
     f.n = c->n;
     f.nw = c->nw;
     f.K = c->K;
@@ -492,6 +520,7 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
   dos::PassArgs a = c->base();
   // gap 0: the aperture field has the separable spectrum Arow[ky] Arow[kx]
   a.Hq = c->hq_slot(0);
+  a.mis = c->gap_mis(0);
   a.out_r0 = 0;
   a.out_r1 = c->n;
   DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, true, c->stream), "forward column pass (aperture)");
@@ -501,6 +530,7 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
     a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
     DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_fwd(a, save != 0, c->stream), "forward row pass");
     a.Hq = c->hq_slot(l);
+    a.mis = c->gap_mis(l);
     a.in_r0 = 0;
     a.in_r1 = c->n;
     a.out_r0 = l == c->K ? c->of : 0;
@@ -532,6 +562,14 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
     f.ckt = c->ckt;
     f.o = c->o;
     f.dLdI = d_dLdI;
+    f.sq = c->mis_on ? c->sq : nullptr;
+    f.df = (float)(1.0 / ((double)c->m * c->pitch));
+    for (int g = 0; g <= c->K; ++g) {
+      const dos::Misalign mg = c->gap_mis(g);
+      f.mis[g][0] = mg.ax;
+      f.mis[g][1] = mg.ay;
+      f.mis[g][2] = mg.dz;
+    }
     f.partial = c->partial;
     f.n = c->n;
     f.nw = c->nw;
@@ -555,6 +593,7 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
   ++c->launches;
   for (int l = c->K; l >= 1; --l) {
     a.Hq = c->hq_slot(l);
+    a.mis = c->gap_mis(l);
     a.in_r0 = l == c->K ? c->of : 0;
     a.in_r1 = l == c->K ? c->of + c->fov : c->n;
     a.out_r0 = 0;
@@ -813,6 +852,33 @@ DOS_API int dos_loss(dos_ctx* c, const float* d_T, double* h_loss, float* d_psnr
   return DOS_OK;
 }
 
+DOS_API int dos_set_misalignment(dos_ctx* c, const double* disp) {
+  int rc = check_ctx(c);
+  if (rc) return rc;
+  ++c->mis_gen;
+  if (!disp) {
+    c->mis_on = false;
+    return DOS_OK;
+  }
+  for (int i = 0; i < 3 * c->K; ++i)
+    if (!std::isfinite(disp[i])) return fail(DOS_ERR_ARG, "displacements must be finite");
+  if (!c->sq) {
+    if ((rc = c->alloc(&c->sq, (size_t)c->nw * c->hs * c->hs, "root table"))) return rc;
+    DOS_CUDA(dos::launch_sqtable(c->sq, c->d_lam, c->nw, c->n_med, c->pitch, c->m, c->hs, c->stream), "root table");
+  }
+  // layer l (1..K) displaced by D_l; planes 0 (aperture) and K+1 (detector) fixed:
+  // gap g carries the lateral shift D_g - D_{g+1} and the length change dz_{g+1} - dz_g
+  c->mis.assign(3 * (c->K + 1), 0.f);
+  auto D = [&](int l, int k) { return (l >= 1 && l <= c->K) ? disp[3 * (l - 1) + k] : 0.0; };
+  for (int g = 0; g <= c->K; ++g) {
+    c->mis[3 * g] = (float)(D(g, 0) - D(g + 1, 0));
+    c->mis[3 * g + 1] = (float)(D(g, 1) - D(g + 1, 1));
+    c->mis[3 * g + 2] = (float)(D(g + 1, 2) - D(g, 2));
+  }
+  c->mis_on = true;
+  return DOS_OK;
+}
+
 DOS_API int dos_efficiency(dos_ctx* c, float* d_eta) {
   int rc = check_ctx(c);
   if (rc) return rc;
@@ -863,9 +929,9 @@ DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dL
     DOS_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming), "step event");
     DOS_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming), "step event");
   }
-  const void* key[5] = {d_h, d_T, d_dLdh, d_I, d_psnr};
+  const void* key[6] = {d_h, d_T, d_dLdh, d_I, d_psnr, reinterpret_cast<const void*>(c->mis_gen)};
   bool same = c->gexec != nullptr;
-  for (int i = 0; i < 5; ++i) same = same && key[i] == c->gkey[i];
+  for (int i = 0; i < 6; ++i) same = same && key[i] == c->gkey[i];
   DOS_CUDA(cudaEventRecord(c->ev_in, c->stream), "step order");
   DOS_CUDA(cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "step order");
   if (!same) {
@@ -900,7 +966,7 @@ DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dL
     e = cudaGraphInstantiate(&c->gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(DOS_ERR_CUDA, std::string("step instantiate: ") + cudaGetErrorString(e));
-    for (int i = 0; i < 5; ++i) c->gkey[i] = key[i];
+    for (int i = 0; i < 6; ++i) c->gkey[i] = key[i];
   }
   DOS_CUDA(cudaGraphLaunch(c->gexec, c->gstream), "step graph launch");
   DOS_CUDA(cudaEventRecord(c->ev_out, c->gstream), "step order");
@@ -947,6 +1013,7 @@ DOS_API int dos_propagate(dos_ctx* c, int gap, const float* d_in, float* d_out, 
   a.fin = reinterpret_cast<const float2*>(d_in);
   a.fout = reinterpret_cast<float2*>(d_out);
   a.Hq = c->hq_slot(gap);
+  a.mis = c->gap_mis(gap);
   a.in_r0 = 0;
   a.in_r1 = c->n;
   a.out_r0 = 0;

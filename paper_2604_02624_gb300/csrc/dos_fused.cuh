@@ -50,6 +50,9 @@ struct FusedArgs {
   float* partial;            // [n_clusters][K][n][n]
   int n, nw, K, fov, of, hs;
   int save;
+  const float* sq;             // [nw][hs][hs] signed sqrt(|q|) when layers are misaligned, else null
+  float df;                    // DFT bin spacing [1/m]
+  float mis[kMaxGaps][3];      // per gap: lateral shift (x, y) and length change [m]
 };
 
 constexpr int ct_gcd(int a, int b) { return b == 0 ? a : ct_gcd(b, a % b); }
@@ -75,13 +78,22 @@ struct Fused {
   // H(|ky|, |kx|) for the thread's frequencies k = t + T*i of column cc:
   // |k| = k below M/2 and M - k above, both affine in i at compile time.
   __device__ static __forceinline__ void load_h(float2 (&hreg)[E], const float2* __restrict__ Hw, int hs, int t,
-                                                int cc) {
+                                                int cc, const float* __restrict__ Sw, const Misalign& mg) {
     const int bc = min(cc, M - cc);
     const float2* lo = Hw + (size_t)t * hs + bc;
     const float2* hi = Hw + (size_t)(M - t) * hs + bc;
 #pragma unroll
     for (int i = 0; i < E; ++i)
       hreg[i] = i < EH ? __ldg(lo + (size_t)T * i * hs) : __ldg(hi - (size_t)T * i * hs);
+    if (Sw) {
+      const float* slo = Sw + (size_t)t * hs + bc;
+      const float* shi = Sw + (size_t)(M - t) * hs + bc;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const float sv = i < EH ? __ldg(slo + (size_t)T * i * hs) : __ldg(shi - (size_t)T * i * hs);
+        hreg[i] = cmul(hreg[i], misalign_factor(mg, t + T * i, cc, M, sv));
+      }
+    }
   }
 
   static size_t smem_bytes(int n) {
@@ -114,7 +126,7 @@ struct Fused {
   template <bool ADJ, bool APERTURE>
   __device__ static void col_phase(const cg::cluster_group& cl, const Sm& s, const float2* __restrict__ Hw,
                                    const float2* __restrict__ arow, int n, int hs, int in_r0, int in_r1,
-                                   int out_r0, int out_r1) {
+                                   int out_r0, int out_r1, const float* __restrict__ Sw, const Misalign& mg) {
     const int l = threadIdx.x % LINES;
     const int t = threadIdx.x / LINES;
     const int rank = (int)cl.block_rank();
@@ -148,7 +160,7 @@ struct Fused {
       const int cc = ok ? c : c0;
       float2 r[E];
       float2 hreg[E];
-      if constexpr (kPrefetchH) load_h(hreg, Hw, hs, t, cc);
+      if constexpr (kPrefetchH) load_h(hreg, Hw, hs, t, cc, Sw, mg);
       if constexpr (APERTURE) {
         const float2 ac = arow[cc];
 #pragma unroll
@@ -159,7 +171,7 @@ struct Fused {
         if (cb + LINES < MC) fetch(cb + LINES, rnext);
         LF::template fft<false, PH>(r, t, z, s.tw);
       }
-      if constexpr (!kPrefetchH) load_h(hreg, Hw, hs, t, cc);
+      if constexpr (!kPrefetchH) load_h(hreg, Hw, hs, t, cc, Sw, mg);
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = ADJ ? cmulc(r[i], hreg[i]) : cmul(r[i], hreg[i]);
       LF::template fft<true, LF::P, QH>(r, t, z, s.tw);
@@ -362,6 +374,18 @@ struct Fused {
   __device__ static const float2* table(const FusedArgs& a, int gap, int w) {
     return a.Hq + (size_t)a.gap_slot[gap] * a.hq_slot_stride + (size_t)w * a.hs * a.hs;
   }
+  __device__ static const float* sqt(const FusedArgs& a, int w) {
+    return a.sq ? a.sq + (size_t)w * a.hs * a.hs : nullptr;
+  }
+  __device__ static Misalign mis(const FusedArgs& a, int gap) {
+    Misalign m;
+    m.sq = a.sq;
+    m.df = a.df;
+    m.ax = a.mis[gap][0];
+    m.ay = a.mis[gap][1];
+    m.dz = a.mis[gap][2];
+    return m;
+  }
 
   // --------------------------------------------------------------- sweeps
   __device__ static void forward(const FusedArgs& a) {
@@ -370,14 +394,14 @@ struct Fused {
     const int cid = blockIdx.x / C;
     const int ncl = gridDim.x / C;
     for (int w = cid; w < a.nw; w += ncl) {
-      col_phase<false, true>(cl, s, table(a, 0, w), a.arow, a.n, a.hs, 0, 0, 0, a.n);
+      col_phase<false, true>(cl, s, table(a, 0, w), a.arow, a.n, a.hs, 0, 0, 0, a.n, sqt(a, w), mis(a, 0));
       cl.sync();
       for (int layer = 0; layer < a.K; ++layer) {
         row_fwd_phase(cl, s, a, layer, w);
         cl.sync();
         const bool lastgap = layer == a.K - 1;
         col_phase<false, false>(cl, s, table(a, layer + 1, w), a.arow, a.n, a.hs, 0, a.n,
-                                lastgap ? a.of : 0, lastgap ? a.of + a.fov : a.n);
+                                lastgap ? a.of : 0, lastgap ? a.of + a.fov : a.n, sqt(a, w), mis(a, layer + 1));
         cl.sync();
       }
       out_phase(cl, s, a, w);
@@ -397,7 +421,7 @@ struct Fused {
       for (int layer = a.K - 1; layer >= 0; --layer) {
         const bool lastgap = layer == a.K - 1;
         col_phase<true, false>(cl, s, table(a, layer + 1, w), a.arow, a.n, a.hs,
-                               lastgap ? a.of : 0, lastgap ? a.of + a.fov : a.n, 0, a.n);
+                               lastgap ? a.of : 0, lastgap ? a.of + a.fov : a.n, 0, a.n, sqt(a, w), mis(a, layer + 1));
         cl.sync();
         row_adj_phase(cl, s, a, layer, w, part, w == cid);
         cl.sync();

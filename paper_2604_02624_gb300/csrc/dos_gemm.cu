@@ -263,7 +263,7 @@ __global__ void k_prep_rows(const float* __restrict__ D, size_t ldd, __nv_bfloat
 // -> X rows (w, kx): [Re over ky, Im over ky, 0 ...] (32 x 32 transpose in smem)
 __global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const float2* __restrict__ Hq, int hs,
                                 __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl, int m, int kp,
-                                int adj) {
+                                int adj, Misalign mis) {
   __shared__ float2 tile[32][33];
   const int w = blockIdx.z;
   const int ky0 = blockIdx.y * 32, kx0 = blockIdx.x * 32;
@@ -274,7 +274,9 @@ __global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const f
     if (ky < m && kx < m) {
       const size_t col = (size_t)w * m + kx;
       const float2 b = make_float2(D[(size_t)(2 * ky) * ldd + col], D[(size_t)(2 * ky + 1) * ldd + col]);
-      const float2 hv = Hw[(size_t)min(ky, m - ky) * hs + min(kx, m - kx)];
+      const size_t qi = (size_t)min(ky, m - ky) * hs + min(kx, m - kx);
+      float2 hv = Hw[qi];
+      if (mis.sq) hv = cmul(hv, misalign_factor(mis, ky, kx, m, mis.sq[(size_t)w * hs * hs + qi]));
       val = adj ? cmulc(b, hv) : cmul(b, hv);
     }
     tile[r][threadIdx.x] = val;
@@ -397,7 +399,7 @@ struct GemmProp {
 // X rows (w, y) of the chunk hold the field; computes the propagated field
 // (into fld) or, with o non-null, the output plane.
 cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool adj, float2* o, float* I, int of,
-                           int fov, cudaStream_t s) {
+                           int fov, const Misalign& mis, cudaStream_t s) {
   GemmProp g{&p, s};
   const int n = p.n, m = p.m;
   cudaError_t e;
@@ -406,7 +408,7 @@ cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool 
   k_prep_rows<<<nwc * m, 128, 0, s>>>(p.D, (size_t)c1, p.Xh, p.Xl, m, n, p.kp1);
   if ((e = g.gemm(p.Fh, p.Fl, p.rp1, p.kp1, c2)) != cudaSuccess) return e;        // column DFT
   k_prep_spectrum<<<dim3((m + 31) / 32, (m + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c2, Hq, hs, p.Xh,
-                                                                                  p.Xl, m, p.kp2, adj ? 1 : 0);
+                                                                                  p.Xl, m, p.kp2, adj ? 1 : 0, mis);
   if ((e = g.gemm(p.Gh, p.Gl, p.rp2, p.kp2, c2)) != cudaSuccess) return e;        // column IDFT
   k_prep_rows<<<nwc * n, 128, 0, s>>>(p.D, (size_t)c2, p.Xh, p.Xl, n, m, p.kp2);
   if ((e = g.gemm(p.Gh, p.Gl, p.rp2, p.kp2, c1)) != cudaSuccess) return e;        // row IDFT

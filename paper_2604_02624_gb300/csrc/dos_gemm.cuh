@@ -55,11 +55,12 @@ struct GemmPlan {
 cudaError_t launch_build_dft(GemmPlan& p, cudaStream_t s);
 
 struct ChanConst;
+struct Misalign;
 
 // One propagation (forward H or conj H) of the chunk's field held in X rows
 // (w, y); the result goes to p.fld, or to o / I on the FOV when o is given.
 cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool adj, float2* o, float* I, int of,
-                           int fov, cudaStream_t s);
+                           int fov, const Misalign& mis, cudaStream_t s);
 // field -> X rows: mode 0 copy, mode 1 checkpoint + Eq. 1 modulation, mode 2 aperture.
 cudaError_t gemm_prep_field(GemmPlan& p, int nwc, const float2* v, float2* ckpt, const float* h,
                             const ChanConst* chan, int mode, int a_off, int a_w, cudaStream_t s);

@@ -17,6 +17,29 @@ struct ChanConst {
   float pad;
 };
 
+// Misaligned layers (Section 3, "vaccination"): gap g carries the lateral
+// shift (ax, ay) and the length change dz; the transfer function becomes
+// H * exp(-2 pi j (fx ax + fy ay)) * H(dz), with H(dz) from the signed
+// root table sq = +sqrt(q) (propagating) or -sqrt(-q) (evanescent).
+struct Misalign {
+  const float* sq;   // [nw][hs][hs] signed sqrt(|q|) [1/m], or null when off
+  float df;          // DFT bin spacing 1 / (M pitch) [1/m]
+  float ax, ay, dz;  // this gap [m]
+};
+
+// exp(-2 pi j (fx ax + fy ay)) * H(dz) for bins (ky, kx) of an M-point grid
+__device__ __forceinline__ float2 misalign_factor(const Misalign& g, int ky, int kx, int m, float sq) {
+  const float fx = (float)(kx < m / 2 ? kx : kx - m) * g.df;
+  const float fy = (float)(ky < m / 2 ? ky : ky - m) * g.df;
+  float ph = -fmaf(fx, g.ax, fy * g.ay);  // cycles
+  float amp = 1.0f;
+  if (sq >= 0.0f) ph = fmaf(g.dz, sq, ph);
+  else amp = expf(6.283185307179586f * g.dz * sq);
+  float sn, cs;
+  sincospif(2.0f * ph, &sn, &cs);
+  return make_float2(amp * cs, amp * sn);
+}
+
 // Arguments of one propagation pass (all channels of the context).
 struct PassArgs {
   float2* S;              // [nw][n][m] spectra of the rows (row pass output / column pass in-out)
@@ -37,6 +60,7 @@ struct PassArgs {
   int out_r0, out_r1;     // column pass: rows stored on output
   int chunk;              // channels per block of the adjoint row pass
   int n_chunks;
+  Misalign mis;           // misaligned layers (mis.sq null: none)
 };
 
 // Kernel launchers of one padded size M (one translation unit per M).
@@ -62,6 +86,8 @@ int supported_m_list(int* out, int cap);
 cudaError_t launch_htable(float2* Hq, const double* d_lambda, int nw, double z, double n_medium,
                           double pitch, int m, int hs, int evanescent, cudaStream_t s);
 cudaError_t launch_arow(float2* arow, int m, int offset, int width, cudaStream_t s);
+cudaError_t launch_sqtable(float* sq, const double* d_lambda, int nw, double n_medium, double pitch, int m, int hs,
+                           cudaStream_t s);
 cudaError_t launch_twiddles(float2* tw, int P, int Q, int RP, int m, cudaStream_t s);
 cudaError_t launch_chan(ChanConst* chan, const double* d_lambda, const double* d_nidx,
                         const double* d_kappa, int nw, double n_medium, double h_base,

@@ -83,11 +83,14 @@ struct Pass {
       LF::template fft<false>(r, t, z, tw);
     }
     const float2* Hw = a.Hq + (size_t)w * a.hs * a.hs;
+    const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
     const int bc = min(cc, M - cc);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int k = t + T * i;
-      const float2 hv = Hw[min(k, M - k) * a.hs + bc];
+      const size_t qi = (size_t)min(k, M - k) * a.hs + bc;
+      float2 hv = Hw[qi];
+      if (Sw) hv = cmul(hv, misalign_factor(a.mis, k, cc, M, Sw[qi]));
       r[i] = ADJ ? cmulc(r[i], hv) : cmul(r[i], hv);
     }
     LF::template fft<true>(r, t, z, tw);

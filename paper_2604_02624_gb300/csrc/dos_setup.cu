@@ -51,6 +51,27 @@ cudaError_t launch_htable(float2* Hq, const double* d_lambda, int nw, double z, 
   return cudaGetLastError();
 }
 
+// signed root of q = (n/lambda)^2 - fx^2 - fy^2 on the quadrant (FP64, rounded once)
+__global__ void k_sqtable(float* __restrict__ sq, const double* __restrict__ lam, double n_medium, double pitch, int m,
+                          int hs) {
+  const int w = blockIdx.y;
+  const int a = blockIdx.x;
+  const double df = 1.0 / ((double)m * pitch);
+  const double k = n_medium / lam[w];
+  const double fa = a * df;
+  for (int b = threadIdx.x; b < hs; b += blockDim.x) {
+    const double fb = b * df;
+    const double q = k * k - fa * fa - fb * fb;
+    sq[((size_t)w * hs + a) * hs + b] = (float)(q >= 0.0 ? sqrt(q) : -sqrt(-q));
+  }
+}
+
+cudaError_t launch_sqtable(float* sq, const double* d_lambda, int nw, double n_medium, double pitch, int m, int hs,
+                           cudaStream_t s) {
+  k_sqtable<<<dim3(hs, nw), 256, 0, s>>>(sq, d_lambda, n_medium, pitch, m, hs);
+  return cudaGetLastError();
+}
+
 // Arow[k] = sum_{x = offset}^{offset + width - 1} exp(-2 pi j k x / m)
 __global__ void k_arow(float2* __restrict__ arow, int m, int offset, int width) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;

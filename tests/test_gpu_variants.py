@@ -94,3 +94,54 @@ def test_fine_tune_after_channel_swap_lowers_the_loss():
     _, losses = fine_tune(st, h, Ts, steps=30, lr=1e-2, h_max=664.5e-9)
     assert losses[-1] < 0.9 * losses[0], losses
     st.close()
+
+
+# ------------------------------------------------------------ misaligned layers (NEXT-4)
+DISP = np.array([[31e-9, -17e-9, 90e-9], [-12e-9, 44e-9, -150e-9]])
+
+
+@pytest.mark.parametrize("path", ["multipass", "fused", "dft_gemm"])
+def test_misaligned_layers_match_oracle(path):
+    from gpu_cases import TOL_FIELD, TOL_GRAD_ORACLE, split_bound, TOL_GRAD_FD
+    w = W.workload("small")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    st = DiffractiveStack.from_workload(w, device=DEV, path=path)
+    st.set_misalignment(DISP)
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    I = st.forward(hd)
+    o = st.output_field()
+    _, _, dl = st.loss(torch.tensor(T, dtype=torch.float32, device=DEV))
+    g = st.backward(hd, dl).cpu().numpy().astype(np.float64)
+    L_ref, _, g_ref, fwd = O.loss_and_grad(h, T, displacements=DISP, **oracle_model(w))
+    e_o = rel_l2(o.cpu().numpy().astype(np.complex128), fwd["o"])
+    if path == "dft_gemm":
+        assert e_o <= split_bound(4 * (w.n_layers + 1))
+        assert rel_l2(g, g_ref) <= TOL_GRAD_FD
+    else:
+        assert e_o <= TOL_FIELD
+        assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
+    # back to the aligned design
+    st.set_misalignment(None)
+    I0 = st.forward(hd).cpu().numpy().astype(np.float64)
+    ref0 = O.forward(h, keep_fields=False, **oracle_model(w))["I"]
+    assert rel_l2(I0, ref0) <= (split_bound(12, True) if path == "dft_gemm" else TOL_INTENSITY)
+    st.close()
+
+
+def test_graph_step_follows_misalignment_changes():
+    w = W.workload("small")
+    h = torch.tensor(W.thickness(w, 0), dtype=torch.float32, device=DEV)
+    T = torch.tensor(W.targets(w, 1), dtype=torch.float32, device=DEV)
+    st = DiffractiveStack.from_workload(w, device=DEV, path="fused")
+    g = torch.empty_like(h)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        disp = rng.uniform(-40e-9, 40e-9, (w.n_layers, 3))
+        st.set_misalignment(disp)
+        val, _ = st.step(h, T, grad_out=g, read=True)
+        st.forward(h)
+        L_ref, _, dl = st.loss(T)
+        assert val == L_ref
+        assert torch.equal(g, st.backward(h, dl))
+    st.close()
