@@ -79,6 +79,10 @@ enum {
  * Implementation of the propagation passes.
  *  DOS_PATH_MULTIPASS: a row pass and a column pass kernel per gap over all
  *    channels, row spectra staged in HBM (any supported M).
+ *  DOS_PATH_MULTIPASS_BULK: the same passes, but persistent blocks fetch their
+ *    next item (a column tile, or the next channel's rows) with bulk-async
+ *    copies into shared memory while computing the current one (needs the
+ *    column stage, 128 N bytes + exchange, within 227 KB of shared memory).
  *  DOS_PATH_FUSED: one persistent launch per sweep (forward or adjoint) in
  *    which a thread-block cluster carries one channel at a time through every
  *    gap with the field held in distributed shared memory (needs N <= M/2 and
@@ -88,17 +92,24 @@ enum {
  *    accumulation in tensor memory), channels processed in chunks; only on
  *    request (it trades accuracy, ~1e-5..1e-4, and speed for tensor cores).
  *  DOS_PATH_AUTO: dos_create times one forward+backward of every available
- *    multi-pass / cluster-resident configuration and keeps the fastest.
- * Environment: DOS_FORCE_CONFIG="multipass" or "fused:C<c>:L<lines>" (names as
- * printed by dos_describe) selects a configuration without timing, when it is
- * compatible with the requested path; DOS_TUNE_CACHE=<file> stores and reuses
+ *    multi-pass (plain and bulk) / cluster-resident configuration and keeps
+ *    the fastest.
+ * Environment: DOS_FORCE_CONFIG="multipass", "multipass:bulk" or
+ * "fused:C<c>:L<lines>" (names as printed by dos_describe) selects a
+ * configuration without timing, when it is among the requested path's; DOS_TUNE_CACHE=<file> stores and reuses
  * the autotuner's decision per (device, N, M, K, N_w, F).
+ * Fault injection (tests): DOS_INJECT_WAIT_TIMEOUT=1 at dos_create makes the
+ * first bulk-prefetch pass that the context launches announce its bytes
+ * without copying them, so that the bounded waits of its blocks expire (one
+ * second) and the next dos_read_loss reports DOS_ERR_TIMEOUT; later calls
+ * run normally.
  */
 enum {
   DOS_PATH_AUTO = 0,
   DOS_PATH_MULTIPASS = 1,
   DOS_PATH_FUSED = 2,
-  DOS_PATH_DFT_GEMM = 3
+  DOS_PATH_DFT_GEMM = 3,
+  DOS_PATH_MULTIPASS_BULK = 4
 };
 
 typedef struct dos_config {
@@ -119,6 +130,9 @@ typedef struct dos_config {
   int evanescent;     /* DOS_EVAN_DECAY or DOS_EVAN_ZERO                               */
   int loss;           /* DOS_LOSS_MSE or DOS_LOSS_MSE_SCALED                           */
   int path;           /* DOS_PATH_*                                                    */
+  int detector_bin;   /* b: one detector pixel integrates b x b simulation pixels of the
+                         F x F output (Section 4: the FOV is divided into output pixels);
+                         0 or 1 = score simulation pixels; b > 1 must divide F        */
 } dos_config;
 
 typedef struct dos_ctx dos_ctx;
@@ -157,14 +171,17 @@ DOS_API int dos_forward(dos_ctx *ctx, const float *d_h, float *d_I, int save_for
 
 /*
  * Objective of the last forward (Section 2: MSE between O_w = |o_w|^2 and its
- * target, over all channels), with the per-channel PSNR.
- *   d_T     [N_w][F][F] float32 targets (required).
+ * target, over all channels), with the per-channel PSNR.  The detector reads
+ * D_w = O_w summed over blocks of b x b simulation pixels (b = detector_bin,
+ * D = O for b <= 1); F_d = F / b detector pixels per side.
+ *   d_T     [N_w][F_d][F_d] float32 targets (required).
  *   h_loss  host double receiving L; when non-NULL the call waits for the
  *           stream.  When NULL, L stays on the device (dos_read_loss).
- *   d_psnr  [N_w] float32: 10 log10(1 / mean_p (sigma_w I - T)^2), sigma_w the
- *           least-squares scale sum I T / sum I^2; NULL to skip.
- *   d_dLdI  [N_w][F][F] float32 gradient dL/dI of the configured loss; NULL to skip.
- * L is normalised by n_lambda_total * F^2 so that shards of one design add up.
+ *   d_psnr  [N_w] float32: 10 log10(1 / mean_p (sigma_w D - T)^2), sigma_w the
+ *           least-squares scale sum D T / sum D^2; NULL to skip.
+ *   d_dLdI  [N_w][F][F] float32 gradient dL/dI of the configured loss with
+ *           respect to the simulation-pixel intensities; NULL to skip.
+ * L is normalised by n_lambda_total * F_d^2 so that shards of one design add up.
  * Errors: DOS_ERR_STATE (no forward yet), DOS_ERR_ARG, DOS_ERR_CUDA.
  */
 DOS_API int dos_loss(dos_ctx *ctx, const float *d_T, double *h_loss, float *d_psnr,
@@ -182,8 +199,9 @@ DOS_API int dos_loss(dos_ctx *ctx, const float *d_T, double *h_loss, float *d_ps
  * serves callers that cannot allocate device memory, e.g. code inside a
  * framework that owns all device memory through its own pool or runs under a
  * fixed budget, or a path where a cudaMalloc would stall the device).
- * Computes what dos_loss computes, from caller intensities instead of a
- * context, using only a fixed-size scratch array in the library itself.
+ * Computes what dos_loss computes with detector_bin = 1, from caller
+ * intensities instead of a context, using only a fixed-size scratch array in
+ * the library itself (a caller with detector pixels passes their sums).
  *   d_I, d_T  [n_lambda][fov][fov] float32 intensities and targets.
  *   n_lambda  1..DOS_NOALLOC_MAX_LAMBDA; larger values fail with DOS_ERR_ARG.
  *   n_lambda_total, loss: as in dos_config; h_loss, d_psnr, d_dLdI: as in
@@ -239,7 +257,12 @@ DOS_API int dos_efficiency(dos_ctx *ctx, float *d_eta);
 DOS_API int dos_quantize_thickness(const float *d_h, float *d_hq, size_t count, double h_max, int bits,
                                    void *cuda_stream);
 
-/* Copies the loss of the last dos_loss to *h_loss (waits for the stream). */
+/*
+ * Copies the loss of the last dos_loss to *h_loss (waits for the stream).
+ * Returns DOS_ERR_TIMEOUT when a kernel queued since the previous check gave
+ * up a bounded wait (bulk-copy or tensor-core completion); the loss and every
+ * result of that work are then invalid.  The flag is cleared by the report.
+ */
 DOS_API int dos_read_loss(dos_ctx *ctx, double *h_loss);
 
 /*
@@ -260,7 +283,7 @@ DOS_API int dos_backward(dos_ctx *ctx, const float *d_h, const float *d_dLdI, fl
  * on a stream private to the context (ordered after the context's stream by
  * an event, and the context's stream after it); later calls with the same
  * pointers replay the graph.
- *   d_h [K][N][N], d_T [N_w][F][F] inputs; d_dLdh [K][N][N] output (all required).
+ *   d_h [K][N][N], d_T [N_w][F_d][F_d] inputs; d_dLdh [K][N][N] output (all required).
  *   d_I [N_w][F][F] and d_psnr [N_w] optional outputs (NULL to skip).
  *   h_loss: when non-NULL receives L (waits for the stream).
  * Afterwards the context holds the same state as after the three calls.
@@ -326,7 +349,7 @@ DOS_API size_t dos_workspace_bytes(const dos_ctx *ctx);
 /* Number of kernel launches queued by the last dos_forward / dos_loss / dos_backward. */
 DOS_API int dos_last_launch_count(const dos_ctx *ctx);
 
-/* Implementation chosen for the context (DOS_PATH_MULTIPASS, _FUSED or _DFT_GEMM). */
+/* Implementation chosen for the context (DOS_PATH_MULTIPASS, _MULTIPASS_BULK, _FUSED or _DFT_GEMM). */
 DOS_API int dos_path(const dos_ctx *ctx);
 
 /*

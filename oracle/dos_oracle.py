@@ -199,16 +199,37 @@ def forward(h, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
 # --------------------------------------------------------------------------
 # Objective (Section 2) and quality metric
 # --------------------------------------------------------------------------
-def mse_loss(I, T, scaled=False):
-    """Loss over all channels and FOV pixels; returns (L, psnr[N_w], dL/dI).
-
-    plain:  L = mean_{w,p} (I - T)^2
-    scaled: L = mean_{w,p} (sigma_w I - T)^2, sigma_w = sum_p I T / sum_p I^2;
-            dL/dI holds sigma_w fixed, which is exact because sigma_w minimises
-            the per-channel error.
-    PSNR_w = 10 log10(1 / mean_p (sigma_w I - T)^2) (peak value 1).
-    """
+def detector_intensity(I, b):
+    """Output pixels of the detector (Section 4: the output FOV is divided into
+    25 x 25 pixels, each spanning several diffractive features): pixel (y, x)
+    integrates the b x b simulation pixels it covers,
+    D[w, y, x] = sum_{i, j < b} I[w, b y + i, b x + j].  b = 1 is the identity."""
     I = np.asarray(I, np.float64)
+    nw, f, _ = I.shape
+    if f % b:
+        raise ValueError("the FOV side must be a multiple of the detector bin")
+    fd = f // b
+    D = np.zeros((nw, fd, fd))
+    for i in range(b):
+        for j in range(b):
+            D += I[:, i::b, j::b]
+    return D
+
+
+def mse_loss(I, T, scaled=False, detector_bin=1):
+    """Loss over all channels and detector pixels; returns (L, psnr[N_w], dL/dI).
+
+    The detector reads D = detector_intensity(I, detector_bin) and T has its
+    shape; with detector_bin = 1, D = I.
+    plain:  L = mean_{w,p} (D - T)^2
+    scaled: L = mean_{w,p} (sigma_w D - T)^2, sigma_w = sum_p D T / sum_p D^2;
+            dL/dD holds sigma_w fixed, which is exact because sigma_w minimises
+            the per-channel error.
+    PSNR_w = 10 log10(1 / mean_p (sigma_w D - T)^2) (peak value 1).
+    dL/dI of a simulation pixel is dL/dD of the detector pixel that covers it.
+    """
+    b = int(detector_bin)
+    I = detector_intensity(I, b)
     T = np.asarray(T, np.float64)
     nw = I.shape[0]
     cnt = I[0].size
@@ -222,6 +243,7 @@ def mse_loss(I, T, scaled=False):
     else:
         L = np.sum((I - T) ** 2) / (nw * cnt)
         dLdI = 2.0 * (I - T)
+    dLdI = np.repeat(np.repeat(dLdI, b, axis=1), b, axis=2)
     return L, psnr, dLdI / (nw * cnt)
 
 
@@ -264,20 +286,22 @@ def backward(h, fwd, dLdI, lambdas, gaps, pitch, m, fov, n_index, kappa,
 
 
 def loss_and_grad(h, T, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
-                  n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False, displacements=None):
+                  n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False, displacements=None,
+                  detector_bin=1):
     fwd = forward(h, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
                   n_medium, h_base, evanescent, displacements=displacements)
-    L, psnr, dLdI = mse_loss(fwd["I"], T, scaled)
+    L, psnr, dLdI = mse_loss(fwd["I"], T, scaled, detector_bin)
     grad = backward(h, fwd, dLdI, lambdas, gaps, pitch, m, fov, n_index, kappa,
                     n_medium, h_base, evanescent, displacements=displacements)
     return L, psnr, grad, fwd
 
 
 def loss_only(h, T, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
-              n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False, displacements=None):
+              n_medium=1.0, h_base=0.0, evanescent="decay", scaled=False, displacements=None,
+              detector_bin=1):
     fwd = forward(h, lambdas, gaps, pitch, m, fov, aperture, n_index, kappa,
                   n_medium, h_base, evanescent, keep_fields=False, displacements=displacements)
-    return mse_loss(fwd["I"], T, scaled)[0]
+    return mse_loss(fwd["I"], T, scaled, detector_bin)[0]
 
 
 def finite_difference(h, T, pixels, delta, **model):

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libdos.so")
 DOS_OK, DOS_ERR_ARG, DOS_ERR_OOM, DOS_ERR_CUDA, DOS_ERR_STATE, DOS_ERR_TIMEOUT, DOS_ERR_UNSUPPORTED = range(7)
 DOS_EVAN_DECAY, DOS_EVAN_ZERO = 0, 1
 DOS_LOSS_MSE, DOS_LOSS_MSE_SCALED = 0, 1
-DOS_PATH_AUTO, DOS_PATH_MULTIPASS, DOS_PATH_FUSED, DOS_PATH_DFT_GEMM = 0, 1, 2, 3
+DOS_PATH_AUTO, DOS_PATH_MULTIPASS, DOS_PATH_FUSED, DOS_PATH_DFT_GEMM, DOS_PATH_MULTIPASS_BULK = 0, 1, 2, 3, 4
 
 ERROR_NAMES = {1: "DOS_ERR_ARG", 2: "DOS_ERR_OOM", 3: "DOS_ERR_CUDA", 4: "DOS_ERR_STATE",
                5: "DOS_ERR_TIMEOUT", 6: "DOS_ERR_UNSUPPORTED"}
@@ -51,6 +51,7 @@ class DosConfig(ctypes.Structure):
         ("n_index", POINTER(c_double)), ("kappa", POINTER(c_double)),
         ("n_medium", c_double), ("h_base", c_double),
         ("evanescent", c_int), ("loss", c_int), ("path", c_int),
+        ("detector_bin", c_int),
     ]
 
 

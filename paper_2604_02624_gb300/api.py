@@ -44,7 +44,7 @@ class DiffractiveStack:
                  gaps: Sequence[float], pitch: float, n_index, kappa=None, fov: int,
                  aperture: int = 0, n_medium: float = 1.0, h_base: float = 0.0,
                  evanescent: str = "decay", loss: str = "mse", n_lambda_total: int = 0,
-                 path: str = "auto", device=None):
+                 path: str = "auto", detector_bin: int = 1, device=None):
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         lam = np.ascontiguousarray(lambdas, dtype=np.float64)
         nw = lam.shape[0]
@@ -56,6 +56,8 @@ class DiffractiveStack:
         if self._gaps.shape[0] != n_layers + 1:
             raise ValueError("gaps must have n_layers + 1 entries")
         self.n, self.m, self.n_layers, self.n_lambda, self.fov = n, m, n_layers, nw, fov
+        self.detector_bin = max(1, int(detector_bin))
+        self.det = fov // self.detector_bin  # detector pixels per side (targets, PSNR)
         cfg = L.DosConfig()
         cfg.n, cfg.m, cfg.n_layers, cfg.n_lambda = n, m, n_layers, nw
         cfg.n_lambda_total = n_lambda_total
@@ -67,7 +69,9 @@ class DiffractiveStack:
         cfg.n_medium, cfg.h_base = n_medium, h_base
         cfg.evanescent = {"decay": L.DOS_EVAN_DECAY, "zero": L.DOS_EVAN_ZERO}[evanescent]
         cfg.loss = {"mse": L.DOS_LOSS_MSE, "mse_scaled": L.DOS_LOSS_MSE_SCALED}[loss]
+        cfg.detector_bin = int(detector_bin)
         cfg.path = {"auto": L.DOS_PATH_AUTO, "multipass": L.DOS_PATH_MULTIPASS,
+                    "multipass_bulk": L.DOS_PATH_MULTIPASS_BULK,
                     "fused": L.DOS_PATH_FUSED, "dft_gemm": L.DOS_PATH_DFT_GEMM}[path]
         self._ctx = None
         with torch.cuda.device(self.device):
@@ -108,7 +112,7 @@ class DiffractiveStack:
 
     @property
     def path(self) -> str:
-        return {1: "multipass", 2: "fused", 3: "dft_gemm"}[L.dos_path(self._ctx)]
+        return {1: "multipass", 2: "fused", 3: "dft_gemm", 4: "multipass_bulk"}[L.dos_path(self._ctx)]
 
     # ------------------------------------------------------------------ compute
     def forward(self, h: torch.Tensor, save_for_backward: bool = True,
@@ -125,11 +129,13 @@ class DiffractiveStack:
         return I
 
     def loss(self, T: torch.Tensor, read: bool = True, psnr: bool = True, grad: bool = True):
-        """Returns (loss or None, psnr[N_w] or None, dL/dI or None)."""
+        """Returns (loss or None, psnr[N_w] or None, dL/dI or None).  T holds the
+        targets of the detector pixels, [N_w][F/b][F/b]; dL/dI is [N_w][F][F]."""
         T = T.contiguous()
-        _need(T, torch.float32, (self.n_lambda, self.fov, self.fov), "T", self.device)
+        _need(T, torch.float32, (self.n_lambda, self.det, self.det), "T", self.device)
         p = torch.empty(self.n_lambda, dtype=torch.float32, device=self.device) if psnr else None
-        g = torch.empty_like(T) if grad else None
+        g = torch.empty((self.n_lambda, self.fov, self.fov), dtype=torch.float32,
+                        device=self.device) if grad else None
         self._bind()
         val = L.dos_loss(self._ctx, T.data_ptr(), read, p.data_ptr() if p is not None else 0,
                          g.data_ptr() if g is not None else 0)
@@ -156,7 +162,7 @@ class DiffractiveStack:
         """Forward + loss + backward in one call, replayed as a CUDA graph.
         Returns (loss or None, dL/dh).  Reusing the same tensors reuses the graph."""
         _need(h, torch.float32, (self.n_layers, self.n, self.n), "h", self.device)
-        _need(T, torch.float32, (self.n_lambda, self.fov, self.fov), "T", self.device)
+        _need(T, torch.float32, (self.n_lambda, self.det, self.det), "T", self.device)
         g = grad_out if grad_out is not None else torch.empty_like(h)
         _need(g, torch.float32, (self.n_layers, self.n, self.n), "grad_out", self.device)
         if intensity_out is not None:

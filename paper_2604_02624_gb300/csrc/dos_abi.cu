@@ -9,6 +9,9 @@
 //   backward: seed row pass (2 dL/dI o), K x (adjoint column pass with conj H
 //             + adjoint row pass [grad_u, dL/dh partials, conj(t) grad_u]),
 //             fixed-order reduction of the partials over channel chunks.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -111,6 +114,7 @@ struct dos_ctx {
   KernelTimer timer;
   int n = 0, m = 0, K = 0, nw = 0, nw_total = 0, fov = 0, ap = 0, of = 0, oa = 0, hs = 0;
   int evan = 0, loss = 0, path = DOS_PATH_MULTIPASS;
+  int bin = 1;  // detector pixel = bin x bin simulation pixels
   double pitch = 0, n_med = 1, h_base = 0;
   std::vector<double> gaps, lam, nidx, kap;
   std::vector<int> gap_slot;  // gap index -> transfer table slot
@@ -128,6 +132,17 @@ struct dos_ctx {
   double* d_loss = nullptr;
   double* h_loss = nullptr;  // pinned
   int chunk = 1, n_chunks = 1;
+  bool bulk = false;       // multi-pass with bulk-async prefetch (DOS_PATH_MULTIPASS_BULK)
+  int* d_err = nullptr;    // set by a kernel whose bounded wait expired
+  int* h_err = nullptr;    // pinned copy
+  bool inject_stall = false;  // DOS_INJECT_WAIT_TIMEOUT: the next bulk pass stalls (tests)
+  CUtensorMap tmap_S;        // S as [nw][n][m] 8-byte elements, box {col_lines, n, 1}
+  bool have_tmap = false;     // the bulk column pass runs the plain kernel without it
+  int take_stall() {
+    const int v = (bulk && inject_stall) ? 1 : 0;
+    if (v) inject_stall = false;
+    return v;
+  }
   bool have_fwd = false, have_ckpt = false, have_loss = false;
   int launches = 0;
   // cluster-resident path
@@ -160,7 +175,6 @@ struct dos_ctx {
   // split-BF16 DFT-GEMM path
   dos::GemmPlan gp = {};
   int gchunks = 0;
-  int* h_gerr = nullptr;  // pinned
 
   template <typename T>
   int alloc(T** p, size_t count, const char* what) {
@@ -193,8 +207,8 @@ struct dos_ctx {
     allocs.clear();
     if (h_loss) cudaFreeHost(h_loss);
     h_loss = nullptr;
-    if (h_gerr) cudaFreeHost(h_gerr);
-    h_gerr = nullptr;
+    if (h_err) cudaFreeHost(h_err);
+    h_err = nullptr;
   }
   float2* hq_slot(int gap) const { return Hq + (size_t)gap_slot[gap] * nw * hs * hs; }
   dos::PassArgs base() const {
@@ -213,6 +227,8 @@ struct dos_ctx {
     a.hs = hs;
     a.chunk = chunk;
     a.n_chunks = n_chunks;
+    a.err = d_err;
+    a.tmap = have_tmap ? &tmap_S : nullptr;
     return a;
   }
 };
@@ -241,6 +257,8 @@ int validate(const dos_config* c) {
   const int ap = c->aperture == 0 ? c->fov : c->aperture;
   if (ap < 1 || ap > c->n || (c->n - ap) % 2 != 0)
     return fail(DOS_ERR_ARG, "aperture must be 0 or in [1, n] with n - aperture even");
+  if (c->detector_bin < 0 || (c->detector_bin > 1 && c->fov % c->detector_bin != 0))
+    return fail(DOS_ERR_ARG, "detector_bin must be 0, 1 or a divisor of fov");
   if (!(c->pitch > 0) || !finite(c->pitch)) return fail(DOS_ERR_ARG, "pitch must be > 0");
   if (!c->gaps || !c->lambda || !c->n_index) return fail(DOS_ERR_ARG, "gaps, lambda and n_index are required");
   for (int i = 0; i <= c->n_layers; ++i)
@@ -256,11 +274,37 @@ int validate(const dos_config* c) {
     return fail(DOS_ERR_ARG, "evanescent must be DOS_EVAN_DECAY or DOS_EVAN_ZERO");
   if (c->loss != DOS_LOSS_MSE && c->loss != DOS_LOSS_MSE_SCALED)
     return fail(DOS_ERR_ARG, "loss must be DOS_LOSS_MSE or DOS_LOSS_MSE_SCALED");
-  if (c->path < DOS_PATH_AUTO || c->path > DOS_PATH_DFT_GEMM) return fail(DOS_ERR_ARG, "path must be a DOS_PATH_* value");
+  if (c->path < DOS_PATH_AUTO || c->path > DOS_PATH_MULTIPASS_BULK) return fail(DOS_ERR_ARG, "path must be a DOS_PATH_* value");
   return DOS_OK;
 }
 
 int choose_path(dos_ctx* x, int requested);
+
+// Tensor map of the row spectra S for the bulk column pass: [nw][n][m]
+// elements of 8 bytes (complex64 moved as opaque 64-bit words), box
+// {col_lines columns, n rows, 1 channel}, columns past m read as zeros.
+// A driver without the entry point leaves the plain column kernel in use.
+int make_spectra_map(dos_ctx* x) {
+  x->have_tmap = false;
+  if (x->n > 256) return DOS_OK;  // one box covers at most 256 rows
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    (void)cudaGetLastError();
+    return DOS_OK;
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)x->m, (cuuint64_t)x->n, (cuuint64_t)x->nw};
+  const cuuint64_t strides[2] = {(cuuint64_t)x->m * 8, (cuuint64_t)x->n * x->m * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)x->ops->col_lines, (cuuint32_t)x->n, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
+      &x->tmap_S, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, x->S, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(DOS_ERR_CUDA, "cuTensorMapEncodeTiled(row spectra) failed: " + std::to_string((int)r));
+  x->have_tmap = true;
+  return DOS_OK;
+}
 
 int build(dos_ctx* x, const dos_config* c) {
   x->n = c->n;
@@ -278,6 +322,7 @@ int build(dos_ctx* x, const dos_config* c) {
   x->h_base = c->h_base;
   x->evan = c->evanescent;
   x->loss = c->loss;
+  x->bin = c->detector_bin > 1 ? c->detector_bin : 1;
   x->path = DOS_PATH_MULTIPASS;
   x->gaps.assign(c->gaps, c->gaps + c->n_layers + 1);
   x->lam.assign(c->lambda, c->lambda + c->n_lambda);
@@ -349,12 +394,17 @@ int build(dos_ctx* x, const dos_config* c) {
     if ((rc = x->alloc(&g.Xl, xsz, "GEMM operand"))) return rc;
     if ((rc = x->alloc(&g.D, dsz, "GEMM output"))) return rc;
     if ((rc = x->alloc(&g.fld, nwc * n2, "GEMM field"))) return rc;
-    if ((rc = x->alloc(&g.err, 1, "GEMM error flag"))) return rc;
-    DOS_CUDA(cudaMemsetAsync(g.err, 0, sizeof(int), x->stream), "GEMM error flag");
-    DOS_CUDA(cudaMallocHost(&x->h_gerr, sizeof(int)), "cudaMallocHost(error flag)");
-    DOS_CUDA(dos::launch_build_dft(g, x->stream), "DFT matrices");
+  }
+  if ((rc = x->alloc(&x->d_err, 1, "error flag"))) return rc;
+  DOS_CUDA(cudaMemsetAsync(x->d_err, 0, sizeof(int), x->stream), "error flag");
+  DOS_CUDA(cudaMallocHost(&x->h_err, sizeof(int)), "cudaMallocHost(error flag)");
+  *x->h_err = 0;
+  if (c->path == DOS_PATH_DFT_GEMM) {
+    x->gp.err = x->d_err;
+    DOS_CUDA(dos::launch_build_dft(x->gp, x->stream), "DFT matrices");
   }
   if ((rc = x->alloc(&x->S, (size_t)x->nw * x->n * x->m, "row spectra"))) return rc;
+  if ((rc = make_spectra_map(x))) return rc;
   if ((rc = x->alloc(&x->ckpt, (size_t)x->K * x->nw * n2, "layer checkpoints"))) return rc;
   if (!x->fcands.empty() && (rc = x->alloc(&x->ckt, (size_t)x->K * x->nw * n2, "transmission checkpoints")))
     return rc;
@@ -390,22 +440,34 @@ int build(dos_ctx* x, const dos_config* c) {
   DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
   if ((rc = choose_path(x, c->path))) return rc;
   DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
+  const char* inj = std::getenv("DOS_INJECT_WAIT_TIMEOUT");
+  x->inject_stall = inj && *inj && std::string(inj) != "0";
   return DOS_OK;
 }
 
 // ------------------------------------------------------------ split-BF16 DFT-GEMM path
-int gemm_check(dos_ctx* c) {
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  DOS_CUDA(cudaStreamIsCapturing(c->stream, &cs), "capture status");
-  if (cs != cudaStreamCaptureStatusNone) return DOS_OK;  // checked by the next synchronising call
-  DOS_CUDA(cudaMemcpyAsync(c->h_gerr, c->gp.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "GEMM flag");
-  DOS_CUDA(cudaStreamSynchronize(c->stream), "GEMM flag");
-  if (*c->h_gerr) {
-    DOS_CUDA(cudaMemsetAsync(c->gp.err, 0, sizeof(int), c->stream), "GEMM flag");
-    return fail(DOS_ERR_TIMEOUT, "a tensor-core wait gave up (bounded mbarrier wait expired)");
+// The error flag set by a kernel whose bounded wait expired (tensor-core
+// commit or bulk-copy completion), read after the stream has drained.
+int flag_after_sync(dos_ctx* c) {
+  if (*c->h_err) {
+    *c->h_err = 0;
+    DOS_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "error flag");
+    return fail(DOS_ERR_TIMEOUT, "a bounded wait gave up (mbarrier wait for a tensor-core commit or a bulk copy "
+                                 "expired); results of the call are invalid");
   }
   return DOS_OK;
 }
+
+int err_check(dos_ctx* c) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DOS_CUDA(cudaStreamIsCapturing(c->stream, &cs), "capture status");
+  if (cs != cudaStreamCaptureStatusNone) return DOS_OK;  // checked by the next synchronising call
+  DOS_CUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "error flag");
+  DOS_CUDA(cudaStreamSynchronize(c->stream), "error flag");
+  return flag_after_sync(c);
+}
+
+int gemm_check(dos_ctx* c) { return err_check(c); }
 
 int gemm_forward(dos_ctx* c, const float* d_h, float* d_I) {
   dos::GemmPlan& g = c->gp;
@@ -528,14 +590,20 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
   for (int l = 1; l <= c->K; ++l) {
     a.h = d_h + (size_t)(l - 1) * n2;
     a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
-    DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_fwd(a, save != 0, c->stream), "forward row pass");
+    a.stall = c->take_stall();
+    DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,
+              c->bulk ? op->bulk_row_fwd(a, save != 0, c->stream) : op->row_fwd(a, save != 0, c->stream),
+              "forward row pass");
     a.Hq = c->hq_slot(l);
     a.mis = c->gap_mis(l);
     a.in_r0 = 0;
     a.in_r1 = c->n;
     a.out_r0 = l == c->K ? c->of : 0;
     a.out_r1 = l == c->K ? c->of + c->fov : c->n;
-    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, false, c->stream), "forward column pass");
+    a.stall = c->take_stall();
+    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD,
+              c->bulk ? op->bulk_col(a, false, c->stream) : op->col(a, false, false, c->stream),
+              "forward column pass");
     c->launches += 2;
   }
   a.I = d_I;
@@ -598,11 +666,17 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
     a.in_r1 = l == c->K ? c->of + c->fov : c->n;
     a.out_r0 = 0;
     a.out_r1 = c->n;
-    DOS_TIMED(c, DOS_KERNEL_COLUMN_ADJOINT, op->col(a, true, false, c->stream), "adjoint column pass");
+    a.stall = c->take_stall();
+    DOS_TIMED(c, DOS_KERNEL_COLUMN_ADJOINT,
+              c->bulk ? op->bulk_col(a, true, c->stream) : op->col(a, true, false, c->stream),
+              "adjoint column pass");
     a.h = d_h + (size_t)(l - 1) * n2;
     a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
     a.partial = c->partial + (size_t)(l - 1) * c->n_chunks * n2;
-    DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT, op->row_adj(a, l == 1, c->stream), "adjoint row pass");
+    a.stall = c->take_stall();
+    DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT,
+              c->bulk ? op->bulk_row_adj(a, l == 1, c->stream) : op->row_adj(a, l == 1, c->stream),
+              "adjoint row pass");
     c->launches += 2;
   }
   DOS_TIMED(c, DOS_KERNEL_GRAD_REDUCE,
@@ -613,8 +687,14 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
 }
 
 // ------------------------------------------------------------ autotuner
-std::string choice_name(const dos::FusedOps* f) {
-  if (!f) return "multipass";
+// Choices of the autotuner: kPlain / kBulk (multi-pass without / with
+// bulk-async prefetch) or an index into the cluster-resident candidates.
+constexpr int kPlain = -2, kBulk = -1;
+
+std::string choice_name(const dos_ctx* x, int idx) {
+  if (idx == kPlain) return "multipass";
+  if (idx == kBulk) return "multipass:bulk";
+  const dos::FusedOps* f = x->fcands[idx];
   return "fused:C" + std::to_string(f->C) + ":L" + std::to_string(f->lines);
 }
 
@@ -629,9 +709,11 @@ std::string tune_key(const dos_ctx* x) {
   return k.str();
 }
 
+
 void set_choice(dos_ctx* x, int idx) {
+  x->bulk = idx == kBulk;
   if (idx < 0) {
-    x->path = DOS_PATH_MULTIPASS;
+    x->path = idx == kBulk ? DOS_PATH_MULTIPASS_BULK : DOS_PATH_MULTIPASS;
     x->fops = nullptr;
     x->n_clusters = 0;
   } else {
@@ -639,6 +721,14 @@ void set_choice(dos_ctx* x, int idx) {
     x->fops = x->fcands[idx];
     x->n_clusters = x->fcand_clusters[idx];
   }
+}
+
+std::string choice_detail(const dos_ctx* x, int idx) {
+  std::ostringstream d;
+  d << "path=" << choice_name(x, idx);
+  if (idx >= 0)
+    d << " threads=" << x->fops->threads << " clusters=" << x->n_clusters << " smem=" << x->fops->smem(x->n);
+  return d.str();
 }
 
 // time forward(save) + backward of the current choice on zero thickness / zero seed
@@ -664,43 +754,53 @@ int time_choice(dos_ctx* x, const float* h0, const float* g0, float* d0, float* 
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (!rc) rc = err_check(x);
   *ms_out = best;
   return rc;
 }
 
 int choose_path(dos_ctx* x, int requested) {
-  std::ostringstream d;
   if (requested == DOS_PATH_DFT_GEMM) {
     x->path = DOS_PATH_DFT_GEMM;
     x->fops = nullptr;
+    x->bulk = false;
     x->describe = "path=dft_gemm chunk=" + std::to_string(x->gp.nwc) + " kp=" + std::to_string(x->gp.kp1) + "/" +
                   std::to_string(x->gp.kp2) + " rows=" + std::to_string(x->gp.rp1) + "/" + std::to_string(x->gp.rp2) +
                   " (split-BF16, 3 terms, tcgen05)";
     return DOS_OK;
   }
-  if (requested == DOS_PATH_MULTIPASS || x->fcands.empty()) {
-    if (requested == DOS_PATH_FUSED)
-      return fail(DOS_ERR_UNSUPPORTED, "no cluster-resident configuration fits this design (needs n <= m/2 and a "
-                                       "compiled configuration for m)");
-    set_choice(x, -1);
-    x->describe = "path=multipass (" + std::string(requested == DOS_PATH_MULTIPASS ? "requested" : "no fused configuration") + ")";
+  if (requested == DOS_PATH_MULTIPASS) {
+    set_choice(x, kPlain);
+    x->describe = "path=multipass (requested)";
     return DOS_OK;
   }
-  // explicit override (profiling, reproducible benchmarks): "multipass" or "fused:C<c>:L<lines>"
+  if (requested == DOS_PATH_MULTIPASS_BULK) {
+    set_choice(x, kBulk);
+    x->describe = "path=multipass:bulk (requested)";
+    return DOS_OK;
+  }
+  if (requested == DOS_PATH_FUSED && x->fcands.empty())
+    return fail(DOS_ERR_UNSUPPORTED, "no cluster-resident configuration fits this design (needs n <= m/2 and a "
+                                     "compiled configuration for m)");
+  // the candidates of the request
+  std::vector<int> cands;
+  if (requested == DOS_PATH_AUTO) {
+    cands.push_back(kPlain);
+    cands.push_back(kBulk);
+  }
+  for (int i = 0; i < (int)x->fcands.size(); ++i) cands.push_back(i);
+  if (cands.size() == 1) {
+    set_choice(x, cands[0]);
+    x->describe = choice_detail(x, cands[0]) + " (only candidate)";
+    return DOS_OK;
+  }
+  // explicit override (profiling, reproducible benchmarks): a name as printed by dos_describe
   const char* force = std::getenv("DOS_FORCE_CONFIG");
   if (force && *force) {
-    const std::string v(force);
-    if (v == "multipass" && requested != DOS_PATH_FUSED) {
-      set_choice(x, -1);
-      x->describe = "path=multipass (DOS_FORCE_CONFIG)";
-      return DOS_OK;
-    }
-    for (size_t i = 0; i < x->fcands.size(); ++i)
-      if (choice_name(x->fcands[i]) == v && requested != DOS_PATH_MULTIPASS) {
-        set_choice(x, (int)i);
-        x->describe = "path=" + v + " threads=" + std::to_string(x->fops->threads) + " clusters=" +
-                      std::to_string(x->n_clusters) + " smem=" + std::to_string(x->fops->smem(x->n)) +
-                      " (DOS_FORCE_CONFIG)";
+    for (int idx : cands)
+      if (choice_name(x, idx) == force) {
+        set_choice(x, idx);
+        x->describe = choice_detail(x, idx) + " (DOS_FORCE_CONFIG)";
         return DOS_OK;
       }
   }
@@ -713,15 +813,10 @@ int choose_path(dos_ctx* x, int requested) {
     while (std::getline(in, line)) {
       if (line.compare(0, key.size() + 1, key + "\t") != 0) continue;
       const std::string v = line.substr(key.size() + 1);
-      if (v == "multipass" && requested == DOS_PATH_AUTO) {
-        set_choice(x, -1);
-        x->describe = "path=multipass (tuning cache)";
-        return DOS_OK;
-      }
-      for (size_t i = 0; i < x->fcands.size(); ++i)
-        if (choice_name(x->fcands[i]) == v) {
-          set_choice(x, (int)i);
-          x->describe = "path=" + v + " clusters=" + std::to_string(x->n_clusters) + " (tuning cache)";
+      for (int idx : cands)
+        if (choice_name(x, idx) == v) {
+          set_choice(x, idx);
+          x->describe = choice_detail(x, idx) + " (tuning cache)";
           return DOS_OK;
         }
     }
@@ -735,20 +830,22 @@ int choose_path(dos_ctx* x, int requested) {
   if (e == cudaSuccess) e = cudaMemsetAsync(g0, 0, sizeof(float) * (size_t)x->nw * x->fov * x->fov, x->stream);
   int rc = DOS_OK;
   if (e != cudaSuccess) rc = fail(DOS_ERR_CUDA, std::string("autotune buffers: ") + cudaGetErrorString(e));
-  int best = -2;
+  int best = cands[0];
   float best_ms = 1e30f;
+  std::ostringstream d;
   d << "tuned (fwd+bwd ms):";
-  for (int i = (requested == DOS_PATH_AUTO ? -1 : 0); rc == DOS_OK && i < (int)x->fcands.size(); ++i) {
-    set_choice(x, i);
+  for (size_t k = 0; rc == DOS_OK && k < cands.size(); ++k) {
+    const int idx = cands[k];
+    set_choice(x, idx);
     float ms = 0.f;
     rc = time_choice(x, h0, g0, d0, &ms);
     if (rc) break;
-    d << " " << choice_name(i < 0 ? nullptr : x->fcands[i]);
-    if (i >= 0) d << "x" << x->fcand_clusters[i];
+    d << " " << choice_name(x, idx);
+    if (idx >= 0) d << "x" << x->fcand_clusters[idx];
     d << "=" << ms;
     if (ms < best_ms) {
       best_ms = ms;
-      best = i;
+      best = idx;
     }
   }
   cudaFree(h0);
@@ -756,15 +853,10 @@ int choose_path(dos_ctx* x, int requested) {
   cudaFree(d0);
   if (rc) return rc;
   set_choice(x, best);
-  std::ostringstream head;
-  head << "path=" << choice_name(x->fops);
-  if (x->fops)
-    head << " threads=" << x->fops->threads << " clusters=" << x->n_clusters
-         << " smem=" << x->fops->smem(x->n);
-  x->describe = head.str() + " | " + d.str();
+  x->describe = choice_detail(x, best) + " | " + d.str();
   if (cache && *cache) {
     std::ofstream out(cache, std::ios::app);
-    out << key << "\t" << choice_name(x->fops) << "\n";
+    out << key << "\t" << choice_name(x, best) << "\n";
   }
   return DOS_OK;
 }
@@ -835,15 +927,16 @@ DOS_API int dos_loss(dos_ctx* c, const float* d_T, double* h_loss, float* d_psnr
   if (rc) return rc;
   if (!c->have_fwd) return fail(DOS_ERR_STATE, "dos_loss needs a dos_forward first");
   if (!d_T) return fail(DOS_ERR_ARG, "d_T is NULL");
-  const int fov2 = c->fov * c->fov;
-  const double norm = (double)c->nw_total * fov2;
+  const int det2 = (c->fov / c->bin) * (c->fov / c->bin);
+  const double norm = (double)c->nw_total * det2;
   c->launches = 0;
-  DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, fov2, c->stream), "loss statistics");
-  DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_final(c->stats, c->nw, fov2, norm, c->loss, c->d_loss, d_psnr, c->stream),
+  DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, c->fov, c->bin, c->stream),
+            "loss statistics");
+  DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_final(c->stats, c->nw, det2, norm, c->loss, c->d_loss, d_psnr, c->stream),
             "loss total");
   c->launches += 2;
   if (d_dLdI) {
-    DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_dldi(c->o, d_T, c->stats, d_dLdI, c->nw, fov2, norm, c->loss, c->stream),
+    DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_dldi(c->o, d_T, c->stats, d_dLdI, c->nw, c->fov, c->bin, norm, c->loss, c->stream),
               "dL/dI");
     ++c->launches;
   }
@@ -906,9 +999,10 @@ DOS_API int dos_read_loss(dos_ctx* c, double* h_loss) {
   if (!h_loss) return fail(DOS_ERR_ARG, "h_loss is NULL");
   DOS_CUDA(cudaMemcpyAsync(c->h_loss, c->d_loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
            "read loss");
+  DOS_CUDA(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "error flag");
   DOS_CUDA(cudaStreamSynchronize(c->stream), "read loss");
   *h_loss = *c->h_loss;
-  return DOS_OK;
+  return flag_after_sync(c);
 }
 
 DOS_API int dos_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
@@ -936,26 +1030,29 @@ DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dL
   DOS_CUDA(cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "step order");
   if (!same) {
     const bool timing = c->timer.on;
+    const bool inject = c->inject_stall;  // an injected stall never enters the graph
     c->timer.on = false;
+    c->inject_stall = false;
     cudaStream_t user = c->stream;
     c->stream = c->gstream;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-      const int fov2 = c->fov * c->fov;
-      const double norm = (double)c->nw_total * fov2;
+      const int det2 = (c->fov / c->bin) * (c->fov / c->bin);
+      const double norm = (double)c->nw_total * det2;
       rc = run_forward(c, d_h, d_I, 1);
-      if (!rc) e = dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, fov2, c->gstream);
+      if (!rc) e = dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, c->fov, c->bin, c->gstream);
       if (!rc && e == cudaSuccess)
-        e = dos::launch_loss_final(c->stats, c->nw, fov2, norm, c->loss, c->d_loss, d_psnr, c->gstream);
+        e = dos::launch_loss_final(c->stats, c->nw, det2, norm, c->loss, c->d_loss, d_psnr, c->gstream);
       if (!rc && e == cudaSuccess)
-        e = dos::launch_dldi(c->o, d_T, c->stats, c->dLdI_step, c->nw, fov2, norm, c->loss, c->gstream);
+        e = dos::launch_dldi(c->o, d_T, c->stats, c->dLdI_step, c->nw, c->fov, c->bin, norm, c->loss, c->gstream);
       if (!rc && e == cudaSuccess) rc = run_backward(c, d_h, c->dLdI_step, d_dLdh);
       cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
       if (e == cudaSuccess) e = e2;
     }
     c->stream = user;
     c->timer.on = timing;
+    c->inject_stall = inject;
     if (rc || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       if (rc) return rc;

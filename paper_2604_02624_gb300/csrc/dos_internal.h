@@ -61,6 +61,9 @@ struct PassArgs {
   int chunk;              // channels per block of the adjoint row pass
   int n_chunks;
   Misalign mis;           // misaligned layers (mis.sq null: none)
+  int* err;               // set to 1 by a bulk-copy pass whose bounded wait expired
+  int stall;              // fault injection: bulk passes expect bytes that are never copied
+  const void* tmap;       // host CUtensorMap of S as [nw][n][m] 8-byte elements (bulk column pass), or null
 };
 
 // Kernel launchers of one padded size M (one translation unit per M).
@@ -74,6 +77,13 @@ struct PassOps {
   cudaError_t (*row_adj)(const PassArgs&, bool first, cudaStream_t);
   cudaError_t (*row_in)(const PassArgs&, cudaStream_t);    // caller field -> row spectra
   cudaError_t (*row_back)(const PassArgs&, cudaStream_t);  // row spectra -> caller field
+  // the same column / forward row / adjoint row passes with bulk-async prefetch
+  // (dos_pass_bulk.cuh); bulk_row_lines rows per row block
+  int bulk_row_lines;
+  size_t (*bulk_col_smem)(int n);
+  cudaError_t (*bulk_col)(const PassArgs&, bool adjoint, cudaStream_t);
+  cudaError_t (*bulk_row_fwd)(const PassArgs&, bool save, cudaStream_t);
+  cudaError_t (*bulk_row_adj)(const PassArgs&, bool first, cudaStream_t);
 };
 
 const PassOps* pass_ops_for_m(int m);
@@ -100,12 +110,15 @@ struct LossStats {
   double sse_sc;   // sum_p (sigma I - T)^2
   double pad;
 };
-cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov2,
+// o: [nw][fov][fov] output field; T: [nw][fov/bin][fov/bin] targets of the
+// detector pixels (bin x bin simulation pixels each); dLdI: [nw][fov][fov]
+cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov, int bin,
                               cudaStream_t s);
-cudaError_t launch_loss_final(const LossStats* st, int nw, int fov2, double norm, int mode,
+// det2: detector pixels per channel (PSNR mean)
+cudaError_t launch_loss_final(const LossStats* st, int nw, int det2, double norm, int mode,
                               double* d_loss, float* d_psnr, cudaStream_t s);
 cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, float* dLdI, int nw,
-                        int fov2, double norm, int mode, cudaStream_t s);
+                        int fov, int bin, double norm, int mode, cudaStream_t s);
 cudaError_t launch_grad_reduce(const float* partial, float* grad, int n_chunks, size_t count,
                                size_t chunk_stride, cudaStream_t s);
 cudaError_t launch_grad_reduce_flat(const float* partial, float* grad, int n_parts, size_t count,

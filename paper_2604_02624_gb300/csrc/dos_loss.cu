@@ -1,9 +1,11 @@
 // dos_loss.cu - objective, quality metric and the gradient reduction.
 //
 // Section 2: the design minimises an MSE between the output intensity O_w of
-// every channel and its target; reconstruction quality is a PSNR.  All sums
-// run in FP64 in a fixed order (per-thread strided partial sums, then a
-// shared-memory tree), so results are reproducible bit for bit.
+// every channel and its target; reconstruction quality is a PSNR.  The
+// detector (Section 4: the FOV divided into output pixels) reads pixel (y, x)
+// as the sum of the b x b simulation intensities it covers (b = 1: I itself).
+// All sums run in FP64 in a fixed order (per-thread strided partial sums, then
+// a shared-memory tree), so results are reproducible bit for bit.
 #include "dos_internal.h"
 
 #include "../../include/dos.h"
@@ -26,17 +28,28 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 __device__ __forceinline__ float intensity(float2 o) { return fmaf(o.x, o.x, o.y * o.y); }
 
-// per channel: sum (I-T)^2, sigma = sum I T / sum I^2, sum (sigma I - T)^2
+// detector pixel p = (y, x) of a channel's F x F output field: sum over its b x b block
+__device__ __forceinline__ double detector(const float2* ow, int fov, int b, int p) {
+  if (b == 1) return intensity(ow[p]);
+  const int fd = fov / b, y = (p / fd) * b, x = (p % fd) * b;
+  double s = 0.0;
+  for (int i = 0; i < b; ++i)
+    for (int j = 0; j < b; ++j) s += (double)intensity(ow[(size_t)(y + i) * fov + x + j]);
+  return s;
+}
+
+// per channel: sum (D-T)^2, sigma = sum D T / sum D^2, sum (sigma D - T)^2
 __global__ void __launch_bounds__(kRedThreads) k_loss_stats(const float2* __restrict__ o,
                                                             const float* __restrict__ T,
-                                                            LossStats* __restrict__ st, int fov2) {
+                                                            LossStats* __restrict__ st, int fov, int b) {
   __shared__ double sh[kRedThreads];
   const int w = blockIdx.x;
-  const float2* ow = o + (size_t)w * fov2;
-  const float* tw = T + (size_t)w * fov2;
+  const int fd = fov / b, det2 = fd * fd;
+  const float2* ow = o + (size_t)w * fov * fov;
+  const float* tw = T + (size_t)w * det2;
   double sse = 0, sit = 0, sii = 0;
-  for (int p = threadIdx.x; p < fov2; p += kRedThreads) {
-    const double I = intensity(ow[p]);
+  for (int p = threadIdx.x; p < det2; p += kRedThreads) {
+    const double I = detector(ow, fov, b, p);
     const double t = tw[p];
     sse += (I - t) * (I - t);
     sit += I * t;
@@ -47,8 +60,8 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_stats(const float2* __rest
   sii = block_sum(sii, sh);
   const double sigma = sii > 0.0 ? sit / sii : 0.0;
   double ssc = 0;
-  for (int p = threadIdx.x; p < fov2; p += kRedThreads) {
-    const double d = sigma * (double)intensity(ow[p]) - (double)tw[p];
+  for (int p = threadIdx.x; p < det2; p += kRedThreads) {
+    const double d = sigma * detector(ow, fov, b, p) - (double)tw[p];
     ssc += d * d;
   }
   ssc = block_sum(ssc, sh);
@@ -62,9 +75,9 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_stats(const float2* __rest
   }
 }
 
-cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov2,
+cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov, int bin,
                               cudaStream_t s) {
-  k_loss_stats<<<nw, kRedThreads, 0, s>>>(o, T, st, fov2);
+  k_loss_stats<<<nw, kRedThreads, 0, s>>>(o, T, st, fov, bin);
   return cudaGetLastError();
 }
 
@@ -89,27 +102,33 @@ cudaError_t launch_loss_final(const LossStats* st, int nw, int fov2, double norm
   return cudaGetLastError();
 }
 
-// dL/dI: 2 (I - T) / norm, or 2 sigma (sigma I - T) / norm for the scaled loss
+// dL/dI of a simulation pixel = dL/dD of its detector pixel:
+// 2 (D - T) / norm, or 2 sigma (sigma D - T) / norm for the scaled loss
 __global__ void k_dldi(const float2* __restrict__ o, const float* __restrict__ T,
                        const LossStats* __restrict__ st, float* __restrict__ dLdI, size_t total,
-                       int fov2, double norm, int mode) {
+                       int fov, int b, double norm, int mode) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
-  const double I = intensity(o[i]);
+  const int fov2 = fov * fov, fd = fov / b;
+  const size_t w = i / fov2;
+  const int q = (int)(i % fov2);
+  const int p = ((q / fov) / b) * fd + (q % fov) / b;  // detector pixel covering q
+  const double I = detector(o + w * fov2, fov, b, p);
+  const double t = T[w * fd * fd + p];
   double g;
   if (mode == DOS_LOSS_MSE_SCALED) {
-    const double sg = st[i / fov2].sigma;
-    g = 2.0 * sg * (sg * I - (double)T[i]) / norm;
+    const double sg = st[w].sigma;
+    g = 2.0 * sg * (sg * I - t) / norm;
   } else {
-    g = 2.0 * (I - (double)T[i]) / norm;
+    g = 2.0 * (I - t) / norm;
   }
   dLdI[i] = (float)g;
 }
 
 cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, float* dLdI, int nw,
-                        int fov2, double norm, int mode, cudaStream_t s) {
-  const size_t total = (size_t)nw * fov2;
-  k_dldi<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(o, T, st, dLdI, total, fov2, norm, mode);
+                        int fov, int bin, double norm, int mode, cudaStream_t s) {
+  const size_t total = (size_t)nw * fov * fov;
+  k_dldi<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(o, T, st, dLdI, total, fov, bin, norm, mode);
   return cudaGetLastError();
 }
 

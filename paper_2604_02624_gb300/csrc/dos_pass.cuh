@@ -387,17 +387,6 @@ struct PassLaunch {
   static cudaError_t row_back(const PassArgs& a, cudaStream_t s) {
     return launch_k(k_row_back<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
   }
-  static const PassOps* ops() {
-    static const PassOps o = {LF::M, LF::P, LF::Q, LF::T, PS::ROWL, PS::COLL,
-                              &col, &row_fwd, &row_out, &row_seed, &row_adj, &row_in, &row_back};
-    return &o;
-  }
 };
 
 }  // namespace dos
-
-// One translation unit per padded size: defines dos::pass_ops_<M>().
-#define DOS_DEFINE_PASS_OPS(M_, P_, Q_, T_)                                          \
-  namespace dos {                                                                    \
-  const PassOps* pass_ops_##M_() { return PassLaunch<Line<P_, Q_, T_>>::ops(); }     \
-  }

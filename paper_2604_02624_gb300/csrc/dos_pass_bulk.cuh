@@ -1,0 +1,379 @@
+// dos_pass_bulk.cuh - the multi-pass row and column passes with bulk-async prefetch.
+//
+// Same arithmetic as dos_pass.cuh; what changes is how the input reaches the
+// block.  Blocks are persistent over several work items and the bulk-copy
+// engine (cp.async.bulk global -> shared, completion counted in bytes on an
+// mbarrier) fetches the next item while the block computes the current one:
+//   column pass : item = a tile of COLL columns of one channel; one tensor
+//                 copy (TMA) of the box {COLL columns, N rows} of the spectra;
+//   row passes  : item = the block's RL rows of the next channel of its chunk;
+//                 one contiguous bulk copy of RL * M * 8 bytes.
+// One staging buffer per block suffices: the item is moved from the stage to
+// registers and the block synchronises before the next copy is issued, so
+// the copy overlaps the whole DFT / modulation / DFT / store of the item.
+// Every wait is bounded (one second of global time): when it expires the
+// block sets *err, issues no further copy and leaves its loop (the copy it
+// waited for is its only one in flight).  PassArgs::stall (fault injection
+// for tests) makes the blocks announce their bytes without copying them, so
+// that the first wait of every block expires.
+#pragma once
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "dos_pass.cuh"
+
+namespace dos {
+
+constexpr unsigned long long kBulkWaitNs = 1000000000ull;  // bounded wait: one second
+constexpr long kBulkSpin = 1L << 30;                        // and an iteration cap behind it
+
+__device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bulk_bar_init(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(b)));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sh_addr(b)), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   sh_addr(dst)),
+               "l"(src), "r"(bytes), "r"(sh_addr(b))
+               : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// true once the phase with this parity has completed; false after kBulkWaitNs
+__device__ __forceinline__ bool bulk_wait(uint64_t* b, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (long it = 0; it < kBulkSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(sh_addr(b)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 15) == 15 && global_ns() - t0 > kBulkWaitNs) return false;
+  }
+  return false;
+}
+
+template <class LF, int RL>
+struct PassBulk {
+  static constexpr int T = LF::T, E = LF::E, M = LF::M;
+  static constexpr int COLL = Pass<LF>::COLL, ZL = Pass<LF>::ZL;
+  static constexpr int CT = T * COLL, RT = T * RL;
+  static constexpr bool EARLY_H = E <= 20;  // registers allow the H values in flight
+
+  // ------------------------------------------------------------ column pass
+  // dynamic shared memory (from a 128-byte aligned base):
+  //   stage[n][COLL] | exchange[COLL][ZL] | tw[ZS] | barrier
+  static size_t col_smem(int n) {
+    return 128 + sizeof(float2) * ((size_t)n * COLL + (size_t)COLL * ZL + LF::ZS) + sizeof(uint64_t);
+  }
+
+  // All N rows of every column tile are fetched by one tensor copy of the box
+  // {COLL columns, N rows, 1 channel} (columns past M read as zeros).
+  template <bool ADJ>
+  __device__ static void col(const PassArgs& a, const CUtensorMap* map) {
+    extern __shared__ __align__(16) unsigned char col_raw[];
+    float2* stage = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(col_raw) + 127) & ~uintptr_t(127));
+    float2* zb = stage + (size_t)a.n * COLL;
+    float2* tw = zb + (size_t)COLL * ZL;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    const int l = threadIdx.x % COLL, t = threadIdx.x / COLL;
+    float2* z = zb + l * ZL;
+    constexpr int ntiles = (M + COLL - 1) / COLL;
+    const int items = a.nw * ntiles;
+    const uint32_t bytes = (uint32_t)(COLL * 8) * (uint32_t)a.n;
+    if (threadIdx.x == 0) {
+      bulk_bar_init(bar);
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+    }
+    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    __syncthreads();
+    auto fetch = [&](int it) {
+      if (threadIdx.x != 0) return;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(bar, bytes);
+      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      const int w = it / ntiles, c0 = (it % ntiles) * COLL;
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+          "[%5];" ::"r"(sh_addr(stage)),
+          "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(0), "r"(w), "r"(sh_addr(bar))
+          : "memory");
+    };
+    bool ok = true;
+    int k = 0;
+    if ((int)blockIdx.x < items) fetch(blockIdx.x);
+    for (int it = blockIdx.x; it < items; it += gridDim.x, ++k) {
+      const int w = it / ntiles, c0 = (it % ntiles) * COLL;
+      const int c = c0 + l;
+      const bool cok = c < M;
+      const int cc = cok ? c : c0;
+      if (!bulk_wait(bar, (uint32_t)(k & 1))) ok = false;
+      if (!__syncthreads_and(ok)) break;
+      float2 r[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int row = t + T * i;
+        r[i] = row < a.n ? stage[(size_t)row * COLL + l] : czero();
+      }
+      __syncthreads();  // stage consumed: the next item may land in it
+      if (it + (int)gridDim.x < items) fetch(it + gridDim.x);
+      // transfer function of this column; with few elements per thread it is
+      // loaded before the forward DFT so that the loads overlap it
+      const float2* Hw = a.Hq + (size_t)w * a.hs * a.hs;
+      const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
+      const int bc = min(cc, M - cc);
+      float2 hv[EARLY_H ? E : 1];
+      if constexpr (EARLY_H) {
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int kk = t + T * i;
+          hv[i] = __ldg(Hw + (size_t)min(kk, M - kk) * a.hs + bc);
+        }
+      }
+      LF::template fft<false>(r, t, z, tw);
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        float2 h;
+        if constexpr (EARLY_H) {
+          h = hv[i];
+        } else {
+          const int kk = t + T * i;
+          h = __ldg(Hw + (size_t)min(kk, M - kk) * a.hs + bc);
+        }
+        if (Sw) {
+          const int kk = t + T * i;
+          h = cmul(h, misalign_factor(a.mis, kk, cc, M, Sw[(size_t)min(kk, M - kk) * a.hs + bc]));
+        }
+        r[i] = ADJ ? cmulc(r[i], h) : cmul(r[i], h);
+      }
+      LF::template fft<true>(r, t, z, tw);
+      float2* dst = a.S + (size_t)w * a.n * M + cc;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int row = t + T * i;
+        if (cok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
+      }
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
+  }
+
+  // ------------------------------------------------------------- row passes
+  // dynamic shared memory: stage[RL][M] | exchange[RL][ZL] | tw[ZS] | barrier
+  static size_t row_smem() {
+    return sizeof(float2) * ((size_t)RL * M + (size_t)RL * ZL + LF::ZS) + sizeof(uint64_t);
+  }
+
+  // Rows [blockIdx.x * RL, +RL) of the channels of chunk blockIdx.y.
+  //   ADJ false : forward layer pass (as Pass::row_fwd), FLAG = save the checkpoint
+  //   ADJ true  : adjoint layer pass (as Pass::row_adj), FLAG = first layer
+  template <bool ADJ, bool FLAG>
+  __device__ static void row(const PassArgs& a) {
+    extern __shared__ __align__(16) float2 smem[];
+    float2* stage = smem;
+    float2* zb = stage + (size_t)RL * M;
+    float2* tw = zb + (size_t)RL * ZL;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    const int l = threadIdx.x / T, t = threadIdx.x % T;
+    float2* z = zb + l * ZL;
+    const int r0 = blockIdx.x * RL;
+    const int nrows = min(RL, a.n - r0);
+    const int row = r0 + l;
+    const bool ok = l < nrows;
+    const int rr = ok ? row : r0;
+    const int w0 = blockIdx.y * a.chunk;
+    const int w1 = min(a.nw, w0 + a.chunk);
+    const uint32_t bytes = (uint32_t)nrows * M * 8u;
+    if (threadIdx.x == 0) bulk_bar_init(bar);
+    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    __syncthreads();
+    auto fetch = [&](int w) {
+      if (threadIdx.x != 0) return;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(bar, bytes);
+      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      bulk_g2s(stage, a.S + ((size_t)w * a.n + r0) * M, bytes, bar);
+    };
+    // the thickness row is held in registers by the forward pass; the adjoint
+    // pass (which also carries its gradient and the checkpoint) re-reads it
+    // from L1 per channel
+    const float* hrow = a.h + (size_t)rr * a.n;
+    float hv[ADJ ? 1 : E];
+    if constexpr (!ADJ) {
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i;
+        hv[i] = (x < a.n) ? __ldg(hrow + x) : 0.f;
+      }
+    }
+    float g[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) g[i] = 0.f;
+    bool okw = true;
+    if (w0 < w1) fetch(w0);
+    int k = 0;
+    for (int w = w0; w < w1; ++w, ++k) {
+      const ChanConst cc = a.chan[w];
+      if (!bulk_wait(bar, (uint32_t)(k & 1))) okw = false;
+      if (!__syncthreads_and(okw)) break;
+      float2 r[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) r[i] = stage[(size_t)(ok ? l : 0) * M + t + T * i];
+      __syncthreads();  // stage consumed: the next channel may land in it
+      if (w + 1 < w1) fetch(w + 1);
+      LF::template fft<true>(r, t, z, tw);
+      float2* srow = a.S + ((size_t)w * a.n + rr) * M;
+      if constexpr (!ADJ) {
+        float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int x = t + T * i;
+          if (x < a.n) {
+            const float2 v = r[i];
+            if (FLAG && ok) ck[x] = v;
+            r[i] = cmul(transmission(hv[i], cc), v);
+          } else {
+            r[i] = czero();
+          }
+        }
+        LF::template fft<false>(r, t, z, tw);
+        if (ok) {
+#pragma unroll
+          for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+        }
+      } else {
+        const float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int x = t + T * i;
+          if (x < a.n) {
+            const float2 au = r[i];
+            const float2 tt = transmission(__ldg(hrow + x), cc);
+            const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
+            g[i] = fmaf(au.x, cu.x, fmaf(au.y, cu.y, g[i]));
+            r[i] = cmulc(au, tt);
+          } else {
+            r[i] = czero();
+          }
+        }
+        if constexpr (!FLAG) {
+          LF::template fft<false>(r, t, z, tw);
+          if (ok) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+          }
+        }
+      }
+    }
+    if (!okw) {
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      return;
+    }
+    if constexpr (ADJ) {
+      if (ok) {
+        float* prow = a.partial + ((size_t)blockIdx.y * a.n + row) * a.n;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int x = t + T * i;
+          if (x < a.n) prow[x] = g[i];
+        }
+      }
+    }
+  }
+};
+
+// two resident blocks per SM where the line's registers allow it
+template <class LF>
+constexpr int bulk_min_blocks() { return LF::E <= 20 ? 2 : 1; }
+
+template <class LF, int RL, bool ADJ>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, bulk_min_blocks<LF>())
+    k_col_bulk(PassArgs a, const __grid_constant__ CUtensorMap map) {
+  PassBulk<LF, RL>::template col<ADJ>(a, &map);
+}
+template <class LF, int RL, bool ADJ, bool FLAG>
+__global__ void __launch_bounds__(LF::T * RL, bulk_min_blocks<LF>()) k_row_bulk(PassArgs a) {
+  PassBulk<LF, RL>::template row<ADJ, FLAG>(a);
+}
+
+// Launchers.  The column pass runs one persistent block per resident slot
+// (blocks per SM from the occupancy calculator x SMs); the row passes run
+// (row blocks) x (channel chunks) blocks, each looping over its chunk.
+template <class LF, int RL>
+struct PassBulkLaunch {
+  using PB = PassBulk<LF, RL>;
+  template <typename K>
+  static cudaError_t slots(K kernel, int threads, size_t smem, int* out) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem)) != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    *out = std::max(1, per_sm) * sms;
+    return cudaSuccess;
+  }
+  // The tensor copy needs every row [0, N) as input and N <= 256 (one box);
+  // other column passes (the adjoint's first, FOV-rows-only gap) run the
+  // plain kernel.
+  static cudaError_t col(const PassArgs& a, bool adj, cudaStream_t s) {
+    const size_t sm = PB::col_smem(a.n);
+    if (!a.tmap || a.in_r0 != 0 || a.in_r1 != a.n || a.n > 256 || sm > 227 * 1024)
+      return PassLaunch<LF>::col(a, adj, false, s);
+    const int items = a.nw * ((LF::M + PB::COLL - 1) / PB::COLL);
+    if (items == 0) return cudaSuccess;
+    int n_slots = 0;
+    auto kern = adj ? k_col_bulk<LF, RL, true> : k_col_bulk<LF, RL, false>;
+    cudaError_t e = slots(kern, PB::CT, sm, &n_slots);
+    if (e != cudaSuccess) return e;
+    kern<<<std::min(items, n_slots), PB::CT, sm, s>>>(a, *static_cast<const CUtensorMap*>(a.tmap));
+    return cudaGetLastError();
+  }
+  static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
+    const dim3 g((a.n + RL - 1) / RL, a.n_chunks);
+    const size_t sm = PB::row_smem();
+    return save ? launch_k(k_row_bulk<LF, RL, false, true>, g, PB::RT, sm, a, s)
+                : launch_k(k_row_bulk<LF, RL, false, false>, g, PB::RT, sm, a, s);
+  }
+  static cudaError_t row_adj(const PassArgs& a, bool first, cudaStream_t s) {
+    const dim3 g((a.n + RL - 1) / RL, a.n_chunks);
+    const size_t sm = PB::row_smem();
+    return first ? launch_k(k_row_bulk<LF, RL, true, true>, g, PB::RT, sm, a, s)
+                 : launch_k(k_row_bulk<LF, RL, true, false>, g, PB::RT, sm, a, s);
+  }
+};
+
+// The launchers of one padded size, plain and bulk-prefetching.
+template <class LF, int RL>
+const PassOps* pass_ops_table() {
+  using PL = PassLaunch<LF>;
+  using PBL = PassBulkLaunch<LF, RL>;
+  static const PassOps o = {LF::M,       LF::P,          LF::Q,          LF::T,
+                            Pass<LF>::ROWL, Pass<LF>::COLL, &PL::col,    &PL::row_fwd,
+                            &PL::row_out, &PL::row_seed,  &PL::row_adj,  &PL::row_in,
+                            &PL::row_back, RL,            &PassBulk<LF, RL>::col_smem,
+                            &PBL::col,    &PBL::row_fwd,  &PBL::row_adj};
+  return &o;
+}
+
+}  // namespace dos
+
+// One translation unit per padded size: defines dos::pass_ops_<M>() (RL_ rows
+// per block in the bulk-prefetching row passes).
+#define DOS_DEFINE_PASS_OPS(M_, P_, Q_, T_, RL_)                                              \
+  namespace dos {                                                                             \
+  const PassOps* pass_ops_##M_() { return pass_ops_table<Line<P_, Q_, T_>, RL_>(); }          \
+  }

@@ -41,6 +41,24 @@ def test_library_hides_internal_symbols(lib):
         getattr(lib, "launch_htable")
 
 
+def test_config_struct_matches_the_header():
+    """The ctypes mirror of dos_config has the header's fields, in order and
+    with the header's C types (int / double / pointer)."""
+
+    text = open(os.path.join(ROOT, "include", "dos.h")).read()
+    body = text[text.index("typedef struct dos_config {"):text.index("} dos_config;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(int|double|const double \*)\s*([a-z_]+);", body)
+    names = [n if n != "lambda" else "lambda_" for _, n in fields]
+    assert names == [f[0] for f in L.DosConfig._fields_]
+    kinds = {"int": ctypes.c_int, "double": ctypes.c_double}
+    for (ty, _), (_, ct) in zip(fields, L.DosConfig._fields_):
+        if ty.endswith("*"):
+            assert issubclass(ct, ctypes._Pointer)
+        else:
+            assert ct is kinds[ty]
+
+
 def test_supported_sizes_are_reported(lib):
     ms = L.dos_supported_m()
     for m in (128, 400, 512):
@@ -81,6 +99,10 @@ def _cfg(**over):
     ({"evanescent": 7}, "evanescent"),
     ({"loss": 9}, "loss"),
     ({"n_lambda_total": 1}, "n_lambda_total"),
+    ({"path": 5}, "path"),
+    ({"detector_bin": 3}, "detector_bin"),
+    ({"detector_bin": -2}, "detector_bin"),
+    ({"path": -1}, "path"),
 ])
 def test_invalid_designs_are_rejected_on_the_host(lib, over, msg):
     cfg, keep = _cfg(**over)
@@ -89,6 +111,19 @@ def test_invalid_designs_are_rejected_on_the_host(lib, over, msg):
     assert rc == L.DOS_ERR_ARG
     assert h.value is None
     assert msg in L.dos_last_error()
+
+
+@pytest.mark.parametrize("path", [L.DOS_PATH_AUTO, L.DOS_PATH_MULTIPASS, L.DOS_PATH_FUSED,
+                                  L.DOS_PATH_DFT_GEMM, L.DOS_PATH_MULTIPASS_BULK])
+def test_every_declared_path_passes_host_validation(lib, path):
+    """Host validation accepts every DOS_PATH_* value (without a GPU the call
+    then stops at the first CUDA call, not at argument checking)."""
+    cfg, keep = _cfg(path=path)
+    h = ctypes.c_void_p()
+    rc = lib.dos_create(ctypes.byref(h), ctypes.byref(cfg), None)
+    assert rc != L.DOS_ERR_ARG, L.dos_last_error()
+    if rc == L.DOS_OK:
+        lib.dos_destroy(h)
 
 
 def test_null_arguments_are_rejected(lib):

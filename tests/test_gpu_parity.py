@@ -31,7 +31,8 @@ def _built():
     torch.cuda.set_device(DEV)
 
 
-PATHS = ["multipass", "fused"]
+PATHS = ["multipass", "multipass_bulk", "fused"]
+MULTIPASS = ["multipass", "multipass_bulk"]
 
 
 def _stack(w, **kw):
@@ -93,11 +94,12 @@ def test_forward_fields_and_intensity(name, path):
     for l in range(1, w.n_layers + 1):
         v = _np(st.layer_field(l)).astype(np.complex128)
         assert rel_l2(v, ref["v"][:, l - 1]) <= TOL_FIELD, l
-    assert st.last_launch_count == (2 * w.n_layers + 2 if path == "multipass" else 1)
+    assert st.last_launch_count == (2 * w.n_layers + 2 if path in MULTIPASS else 1)
     st.close()
 
 
-def test_forward_ragged_and_options():
+@pytest.mark.parametrize("path", MULTIPASS)
+def test_forward_ragged_and_options(path):
     """N = 100 in M = 200 (ragged row blocks and column tiles), three layers with
     unequal gaps, a medium of index 1.33, base thickness, per-channel
     dispersion and loss, zeroed evanescent bins, full-window aperture."""
@@ -105,15 +107,16 @@ def test_forward_ragged_and_options():
     w = custom(100, 200, 3, lam, [30, 55, 30, 80], 40, aperture=100,
                n_index=[1.52, 1.51, 1.50, 1.495, 1.49], kappa=[0.02, 0.0, 0.01, 0.03, 0.0],
                n_medium=1.33, h_base=120e-9, name="ragged")
-    st, h, T, hd, I, o, ref = _forward_case(w, evan="zero")
+    st, h, T, hd, I, o, ref = _forward_case(w, evan="zero", path=path)
     assert rel_l2(_np(o).astype(np.complex128), ref["o"]) <= TOL_FIELD
     assert rel_l2(_np(I).astype(np.float64), ref["I"]) <= TOL_INTENSITY
     st.close()
 
 
-def test_forward_single_pixel_layer():
+@pytest.mark.parametrize("path", MULTIPASS)
+def test_forward_single_pixel_layer(path):
     w = custom(1, 16, 2, [500, 700], 3, 1, name="one-pixel")
-    st, h, T, hd, I, o, ref = _forward_case(w)
+    st, h, T, hd, I, o, ref = _forward_case(w, path=path)
     assert rel_l2(_np(o).astype(np.complex128), ref["o"]) <= TOL_FIELD
     st.close()
 
@@ -271,7 +274,9 @@ def test_full_size_gradient_is_the_sum_of_channel_shards(path):
 
 def test_paths_agree_at_full_size():
     """The cluster-resident and the multi-pass implementations of the massive
-    step give the same intensities and gradient (both FP32, different orders)."""
+    step give the same intensities and gradient (both FP32, different orders);
+    the bulk-prefetch multi-pass passes do the plain passes' arithmetic in the
+    same order."""
     w = W.workload("massive")
     h = _t(W.thickness(w, 0))
     T = _t(W.targets(w, 1))
@@ -282,8 +287,11 @@ def test_paths_agree_at_full_size():
         _, _, g = st.loss(T)
         out[path] = (I, st.backward(h, g).clone())
         st.close()
-    assert rel_l2(_np(out["fused"][0]).astype(np.float64), _np(out["multipass"][0]).astype(np.float64)) <= 1e-5
-    assert rel_l2(_np(out["fused"][1]).astype(np.float64), _np(out["multipass"][1]).astype(np.float64)) <= 1e-4
+    ref = [_np(x).astype(np.float64) for x in out["multipass"]]
+    assert rel_l2(_np(out["fused"][0]).astype(np.float64), ref[0]) <= 1e-5
+    assert rel_l2(_np(out["fused"][1]).astype(np.float64), ref[1]) <= 1e-4
+    assert rel_l2(_np(out["multipass_bulk"][0]).astype(np.float64), ref[0]) <= 1e-6
+    assert rel_l2(_np(out["multipass_bulk"][1]).astype(np.float64), ref[1]) <= 1e-6
 
 
 def test_auto_path_is_tuned_and_described():

@@ -100,7 +100,7 @@ def test_fine_tune_after_channel_swap_lowers_the_loss():
 DISP = np.array([[31e-9, -17e-9, 90e-9], [-12e-9, 44e-9, -150e-9]])
 
 
-@pytest.mark.parametrize("path", ["multipass", "fused", "dft_gemm"])
+@pytest.mark.parametrize("path", ["multipass", "multipass_bulk", "fused", "dft_gemm"])
 def test_misaligned_layers_match_oracle(path):
     from gpu_cases import TOL_FIELD, TOL_GRAD_ORACLE, split_bound, TOL_GRAD_FD
     w = W.workload("small")
@@ -144,4 +144,38 @@ def test_graph_step_follows_misalignment_changes():
         L_ref, _, dl = st.loss(T)
         assert val == L_ref
         assert torch.equal(g, st.backward(h, dl))
+    st.close()
+
+
+# ------------------------------------------------------------ detector pixels (Section 4)
+@pytest.mark.parametrize("path", ["multipass", "fused"])
+@pytest.mark.parametrize("b,loss", [(2, "mse"), (5, "mse_scaled")])
+def test_detector_pixels_loss_psnr_and_gradient(path, b, loss):
+    """Detector pixels of b x b simulation pixels (b = 2: the 25 x 25 output
+    pixels of a 50-pixel FOV): loss, PSNR, dL/dI and the thickness gradient
+    against the FP64 oracle; the graph step gives the same values."""
+    from gpu_cases import TOL_GRAD_ORACLE, TOL_LOSS
+    w = W.workload("small")
+    h = W.thickness(w, 0)
+    fd = w.fov // b
+    rng = np.random.default_rng(40 + b)
+    T = (rng.uniform(0, 1, (w.n_lambda, fd, fd)) * 1e-4 * b * b).astype(np.float32)
+    st = DiffractiveStack.from_workload(w, device=DEV, path=path, loss=loss, detector_bin=b)
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    Td = torch.tensor(T, device=DEV)
+    st.forward(hd)
+    val, psnr, dl = st.loss(Td)
+    g = st.backward(hd, dl).clone()
+    scaled = loss == "mse_scaled"
+    L_ref, psnr_ref, g_ref, fwd = O.loss_and_grad(h, T, scaled=scaled, detector_bin=b, **oracle_model(w))
+    _, _, dl_ref = O.mse_loss(fwd["I"], T, scaled, b)
+    assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref)
+    assert np.max(np.abs(psnr.cpu().numpy() - psnr_ref)) <= 1e-3
+    assert rel_l2(dl.cpu().numpy().astype(np.float64), dl_ref) <= TOL_INTENSITY
+    assert rel_l2(g.cpu().numpy().astype(np.float64), g_ref) <= TOL_GRAD_ORACLE
+    gs = torch.empty_like(g)
+    val2, _ = st.step(hd, Td, grad_out=gs, read=True)
+    assert val2 == val and torch.equal(gs, g)
+    with pytest.raises(ValueError):
+        st.loss(torch.zeros((w.n_lambda, w.fov, w.fov), device=DEV))
     st.close()
