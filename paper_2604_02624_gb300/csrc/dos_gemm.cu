@@ -4,10 +4,14 @@
 // 128 x 256 FP32 tile in tensor memory; K is consumed in chunks of 64 bf16
 // staged in shared memory in the canonical K-major, non-swizzled core-matrix
 // layout (8 rows x 16 bytes per core matrix; 128 B between core matrices
-// along K, 1024 B between 8-row groups).  Two stages alternate: while the
-// tensor core works on one chunk (issued by one thread, completion signalled
-// to an mbarrier by tcgen05.commit) the block stages the next.  Every wait is
-// bounded: on expiry the kernel records an error flag and finishes cleanly.
+// along K, 1024 B between 8-row groups).  Operands arrive by cp.async
+// (16-byte asynchronous global -> shared copies, many in flight per thread)
+// through a GSTAGES-deep ring: while the tensor core works on chunk i (issued
+// by one thread, completion signalled to the stage's mbarrier by
+// tcgen05.commit), the copies of chunks i+1 .. i+GSTAGES-1 are in flight.  The
+// grid runs the CTAs of one column tile (which share its B operand) next to
+// each other.  Every wait is bounded: on expiry the kernel records an error
+// flag and finishes cleanly.
 #include <cuda_bf16.h>
 
 #include "dos_gemm.cuh"
@@ -17,6 +21,7 @@
 namespace dos {
 
 constexpr int GTM = 128, GTN = 256, GTK = 64;
+constexpr int GSTAGES = 4;
 constexpr int kGemmThreads = 128;
 constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier wait (a fraction of a second)
 
@@ -44,10 +49,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
+// 16-byte global -> shared copy; src_bytes 0 writes zeros (ragged column tiles)
+__device__ __forceinline__ void cp16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 struct __align__(1024) GemmSmem {
-  uint8_t a[2][GTM * GTK * 2];  // 2 x 16 KB
-  uint8_t b[2][GTN * GTK * 2];  // 2 x 32 KB
-  uint64_t bar[2];
+  uint8_t a[GSTAGES][GTM * GTK * 2];  // 16 KB per stage
+  uint8_t b[GSTAGES][GTN * GTK * 2];  // 32 KB per stage
+  uint64_t bar[GSTAGES];
   uint32_t tmem;
 };
 
@@ -55,15 +71,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gsm_raw);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int n0 = blockIdx.x * GTN, m0 = blockIdx.y * GTM;
+  const int m0 = blockIdx.x * GTM, n0 = blockIdx.y * GTN;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
                  "r"(GTN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar[1])));
+    for (int s = 0; s < GSTAGES; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar[s])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -72,37 +87,44 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   const uint32_t tmem = sm.tmem;
   const int kchunks = g.K / GTK;
   const int total = g.nseg * kchunks;
-  bool ok = true;
-  int issued = 0;  // iterations whose MMAs were committed
-  for (int it = 0; it < total; ++it) {
-    const int buf = it & 1;
-    if (it >= 2) {
-      if (!mbar_wait(smem_addr(&sm.bar[buf]), (uint32_t)(((it - 2) >> 1) & 1))) ok = false;
-    }
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
+  // copies of chunk `it` into its stage (every thread: 8 A and 16 B pieces of 16 bytes)
+  auto load = [&](int it) {
+    const int st = it % GSTAGES;
     const int seg = it / kchunks;
     const int k0 = (it % kchunks) * GTK;
     const __nv_bfloat16* A = g.a[seg];
     const __nv_bfloat16* B = g.b[seg];
-    for (int c = tid; c < GTM * (GTK / 8); c += kGemmThreads) {
+#pragma unroll
+    for (int q = 0; q < GTM * (GTK / 8) / kGemmThreads; ++q) {
+      const int c = tid + q * kGemmThreads;
       const int r = c / (GTK / 8), kc = c % (GTK / 8);
-      const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + r) * g.K + k0 + kc * 8);
-      *reinterpret_cast<uint4*>(sm.a[buf] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16) = v;
+      cp16(sm.a[st] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16, A + (size_t)(m0 + r) * g.K + k0 + kc * 8, 16);
     }
-    for (int c = tid; c < GTN * (GTK / 8); c += kGemmThreads) {
+#pragma unroll
+    for (int q = 0; q < GTN * (GTK / 8) / kGemmThreads; ++q) {
+      const int c = tid + q * kGemmThreads;
       const int r = c / (GTK / 8), kc = c % (GTK / 8);
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (n0 + r < g.cols) v = *reinterpret_cast<const uint4*>(B + (size_t)(n0 + r) * g.K + k0 + kc * 8);
-      *reinterpret_cast<uint4*>(sm.b[buf] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16) = v;
+      const bool in = n0 + r < g.cols;
+      cp16(sm.b[st] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16,
+           B + (size_t)(in ? n0 + r : 0) * g.K + k0 + kc * 8, in ? 16u : 0u);
     }
+  };
+  // prologue: chunks 0 .. GSTAGES-2 in flight (one commit group per chunk slot)
+#pragma unroll
+  for (int s = 0; s < GSTAGES - 1; ++s) {
+    if (s < total) load(s);
+    cp_commit();
+  }
+  bool ok = true;
+  int issued = 0;  // chunks whose MMAs were committed
+  for (int it = 0; it < total; ++it) {
+    const int st = it % GSTAGES;
+    cp_wait<GSTAGES - 2>();  // this thread's copies of chunk `it` have landed
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    __syncthreads();         // ... and everyone else's
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sa = smem_addr(sm.a[buf]), sb = smem_addr(sm.b[buf]);
+      const uint32_t sa = smem_addr(sm.a[st]), sb = smem_addr(sm.b[st]);
 #pragma unroll
       for (int kk = 0; kk < GTK / 16; ++kk) {
         const uint64_t da = kmajor_desc(sa + kk * 256), db = kmajor_desc(sb + kk * 256);
@@ -113,14 +135,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
             "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(&sm.bar[buf])));
+          smem_addr(&sm.bar[st])));
     }
     issued = it + 1;
+    // refill the stage of chunk it-1 with chunk it+GSTAGES-1 once its MMAs are done
+    const int nx = it + GSTAGES - 1;
+    if (nx < total) {
+      if (it >= 1 && !mbar_wait(smem_addr(&sm.bar[(it - 1) % GSTAGES]), (uint32_t)(((it - 1) / GSTAGES) & 1)))
+        ok = false;
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      load(nx);
+    }
+    cp_commit();
   }
+  cp_wait<0>();  // no copy may still target shared memory when the CTA ends
   // the last commit covers every MMA issued before it
   if (ok && total > 0) {
     const int last = total - 1;
-    if (!mbar_wait(smem_addr(&sm.bar[last & 1]), (uint32_t)((last >> 1) & 1))) ok = false;
+    if (!mbar_wait(smem_addr(&sm.bar[last % GSTAGES]), (uint32_t)((last / GSTAGES) & 1))) ok = false;
   }
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -154,7 +189,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   } else {
     // give the MMAs still in flight a bounded chance to finish before the
     // tensor memory they write is released
-    if (issued > 0) (void)mbar_wait(smem_addr(&sm.bar[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
+    if (issued > 0)
+      (void)mbar_wait(smem_addr(&sm.bar[(issued - 1) % GSTAGES]), (uint32_t)(((issued - 1) / GSTAGES) & 1));
     if (tid == 0) atomicExch(g.err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -170,7 +206,8 @@ cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const dim3 grid((g.cols + GTN - 1) / GTN, g.rows / GTM);
+  // row tiles fastest: the CTAs of one column tile (same B operand) run together
+  const dim3 grid(g.rows / GTM, (g.cols + GTN - 1) / GTN);
   k_tc_gemm<<<grid, kGemmThreads, sm, s>>>(g);
   return cudaGetLastError();
 }

@@ -41,13 +41,25 @@ __device__ __forceinline__ float2 transmission(float h, const ChanConst& cc) {
   return make_float2(amp * c, -amp * s);
 }
 
+// Stride between the lines' exchange buffers in the row passes.  There the
+// T threads of a line are consecutive (line = tid / T), so a warp straddles
+// two or more lines; these strides make the 8-byte exchange accesses of such
+// warps free of bank conflicts (least-conflict for M = 200), found by
+// enumerating the bank pattern of every access of the compiled line shapes.
+constexpr int row_line_stride(int m, int zs) {
+  return m == 400 ? 420 : m == 200 ? 222 : m == 128 ? 148 : m == 32 ? 42 : zs;
+}
+
 template <class LF>
 struct Pass {
   static constexpr int T = LF::T, E = LF::E, M = LF::M;
   static constexpr int ROWL = 16;  // rows per block in the row passes
   static constexpr int COLL = 16;  // columns per block in the column pass
-  static constexpr int ZL = LF::ZS + 1;  // odd stride between the lines' exchange buffers
+  // column pass: line = tid % COLL, an odd stride keeps the lines apart
+  static constexpr int ZL = LF::ZS + 1;
+  static constexpr int RZL = row_line_stride(M, LF::ZS);
   static constexpr size_t smem_bytes(int lines) { return sizeof(float2) * (LF::ZS + (size_t)lines * ZL); }
+  static constexpr size_t row_smem_bytes(int lines) { return sizeof(float2) * (LF::ZS + (size_t)lines * RZL); }
 
   __device__ static __forceinline__ void load_tw(float2* tw, const float2* g) {
     for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = g[i];
@@ -114,7 +126,7 @@ struct Pass {
     rc.l = threadIdx.x / T;
     rc.t = threadIdx.x % T;
     rc.tw = smem;
-    rc.z = smem + LF::ZS + rc.l * ZL;
+    rc.z = smem + LF::ZS + rc.l * RZL;
     load_tw(rc.tw, a.tw);
     return rc;
   }
@@ -309,12 +321,17 @@ struct Pass {
 };
 
 // ------------------------------------------------------------------ kernels
+// Lines of up to 20 elements per thread fit three blocks per SM in registers
+// (64 per thread; the column and forward row passes then need no or few spills).
+template <class LF>
+constexpr int pass_min_blocks() { return LF::E <= 20 ? 3 : 1; }
+
 template <class LF, bool ADJ, bool APERTURE>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL) k_col(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, pass_min_blocks<LF>()) k_col(PassArgs a) {
   Pass<LF>::template col<ADJ, APERTURE>(a);
 }
 template <class LF, bool SAVE>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_fwd(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>()) k_row_fwd(PassArgs a) {
   Pass<LF>::template row_fwd<SAVE>(a);
 }
 template <class LF>
@@ -365,27 +382,27 @@ struct PassLaunch {
   }
   static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
     const dim3 g(row_blocks(a.n), a.nw);
-    const size_t sm = PS::smem_bytes(PS::ROWL);
+    const size_t sm = PS::row_smem_bytes(PS::ROWL);
     return save ? launch_k(k_row_fwd<LF, true>, g, RT, sm, a, s)
                 : launch_k(k_row_fwd<LF, false>, g, RT, sm, a, s);
   }
   static cudaError_t row_out(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_out<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+    return launch_k(k_row_out<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
   }
   static cudaError_t row_seed(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_seed<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+    return launch_k(k_row_seed<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
   }
   static cudaError_t row_adj(const PassArgs& a, bool first, cudaStream_t s) {
     const dim3 g(row_blocks(a.n), a.n_chunks);
-    const size_t sm = PS::smem_bytes(PS::ROWL);
+    const size_t sm = PS::row_smem_bytes(PS::ROWL);
     return first ? launch_k(k_row_adj<LF, true>, g, RT, sm, a, s)
                  : launch_k(k_row_adj<LF, false>, g, RT, sm, a, s);
   }
   static cudaError_t row_in(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_in<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+    return launch_k(k_row_in<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
   }
   static cudaError_t row_back(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_back<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::smem_bytes(PS::ROWL), a, s);
+    return launch_k(k_row_back<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
   }
 };
 

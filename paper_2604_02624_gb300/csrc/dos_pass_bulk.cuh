@@ -7,7 +7,8 @@
 //   column pass : item = a tile of COLL columns of one channel; one tensor
 //                 copy (TMA) of the box {COLL columns, N rows} of the spectra;
 //   row passes  : item = the block's RL rows of the next channel of its chunk;
-//                 one contiguous bulk copy of RL * M * 8 bytes.
+//                 one cp.async.bulk of M * 8 bytes per row (rows padded in
+//                 shared memory against bank conflicts).
 // One staging buffer per block suffices: the item is moved from the stage to
 // registers and the block synchronises before the next copy is issued, so
 // the copy overlaps the whole DFT / modulation / DFT / store of the item.
@@ -67,10 +68,20 @@ __device__ __forceinline__ bool bulk_wait(uint64_t* b, uint32_t parity) {
   return false;
 }
 
+// Row stride of the row passes' staging buffer: a warp reads the rows of two
+// or more lines at once, and these strides make those 8-byte reads free of
+// bank conflicts (enumerated on the host for the compiled line shapes).
+constexpr int row_stage_stride(int m) {
+  return m == 400 ? 404 : m == 200 ? 202 : m == 128 ? 132 : m == 64 ? 68 : m == 32 ? 34 : m == 16 ? 18 : m;
+}
+
 template <class LF, int RL>
 struct PassBulk {
   static constexpr int T = LF::T, E = LF::E, M = LF::M;
-  static constexpr int COLL = Pass<LF>::COLL, ZL = Pass<LF>::ZL;
+  static constexpr int COLL = Pass<LF>::COLL, ZL = Pass<LF>::ZL, RZL = Pass<LF>::RZL;
+  static constexpr int SR = row_stage_stride(M);  // even: every staged row starts 16-byte aligned
+  static_assert(SR % 2 == 0 && SR >= M, "staged rows must be 16-byte aligned and hold M values");
+  static_assert(Pass<LF>::RZL >= LF::ZS, "exchange buffers must not overlap");
   static constexpr int CT = T * COLL, RT = T * RL;
   static constexpr bool EARLY_H = E <= 20;  // registers allow the H values in flight
 
@@ -172,9 +183,9 @@ struct PassBulk {
   }
 
   // ------------------------------------------------------------- row passes
-  // dynamic shared memory: stage[RL][M] | exchange[RL][ZL] | tw[ZS] | barrier
+  // dynamic shared memory: stage[RL][SR] | exchange[RL][RZL] | tw[ZS] | barrier
   static size_t row_smem() {
-    return sizeof(float2) * ((size_t)RL * M + (size_t)RL * ZL + LF::ZS) + sizeof(uint64_t);
+    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * RZL + LF::ZS) + sizeof(uint64_t);
   }
 
   // Rows [blockIdx.x * RL, +RL) of the channels of chunk blockIdx.y.
@@ -184,11 +195,11 @@ struct PassBulk {
   __device__ static void row(const PassArgs& a) {
     extern __shared__ __align__(16) float2 smem[];
     float2* stage = smem;
-    float2* zb = stage + (size_t)RL * M;
-    float2* tw = zb + (size_t)RL * ZL;
+    float2* zb = stage + (size_t)RL * SR;
+    float2* tw = zb + (size_t)RL * RZL;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
     const int l = threadIdx.x / T, t = threadIdx.x % T;
-    float2* z = zb + l * ZL;
+    float2* z = zb + l * RZL;
     const int r0 = blockIdx.x * RL;
     const int nrows = min(RL, a.n - r0);
     const int row = r0 + l;
@@ -200,12 +211,14 @@ struct PassBulk {
     if (threadIdx.x == 0) bulk_bar_init(bar);
     for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
     __syncthreads();
+    // thread 0 copies the block's rows of channel w, one bulk copy (M * 8 bytes) per row
     auto fetch = [&](int w) {
       if (threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_expect(bar, bytes);
       if (a.stall) return;  // injected fault: the expected bytes never arrive
-      bulk_g2s(stage, a.S + ((size_t)w * a.n + r0) * M, bytes, bar);
+      const float2* src = a.S + ((size_t)w * a.n + r0) * M;
+      for (int q = 0; q < nrows; ++q) bulk_g2s(stage + (size_t)q * SR, src + (size_t)q * M, M * 8u, bar);
     };
     // the thickness row is held in registers by the forward pass; the adjoint
     // pass (which also carries its gradient and the checkpoint) re-reads it
@@ -231,7 +244,7 @@ struct PassBulk {
       if (!__syncthreads_and(okw)) break;
       float2 r[E];
 #pragma unroll
-      for (int i = 0; i < E; ++i) r[i] = stage[(size_t)(ok ? l : 0) * M + t + T * i];
+      for (int i = 0; i < E; ++i) r[i] = stage[(size_t)(ok ? l : 0) * SR + t + T * i];
       __syncthreads();  // stage consumed: the next channel may land in it
       if (w + 1 < w1) fetch(w + 1);
       LF::template fft<true>(r, t, z, tw);
