@@ -424,10 +424,29 @@ def _split_compare(dev, L, DiffractiveStack, W):
         st.close()
     dI = float(torch.linalg.vector_norm(outs["dft_gemm"][0] - outs["auto"][0]) / torch.linalg.vector_norm(outs["auto"][0]))
     dg = float(torch.linalg.vector_norm(outs["dft_gemm"][1] - outs["auto"][1]) / torch.linalg.vector_norm(outs["auto"][1]))
+    # tensor-core work of the step: per propagation four real GEMMs of the padded
+    # DFT matrices (rows x K) against the channels' data, three bf16 terms each
+    pad = lambda v, q: (v + q - 1) // q * q
+    n, m = w.n, w.m
+    rp1, kp1, rp2, kp2 = pad(2 * m, 128), pad(2 * n, 64), pad(2 * n, 128), pad(2 * m, 64)
+    per_channel = rp1 * n * kp1 + rp1 * m * kp1 + rp2 * m * kp2 + rp2 * n * kp2
+    flops = 2.0 * 3 * (2 * w.n_layers + 1) * w.n_lambda * per_channel
+    tf = flops / (res["dft_gemm"]["ms_per_step"] * 1e-3) / 1e12
+    peaks = {}
+    try:
+        import json as _json
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
     return {"workload": "precision: 4096 lambda x 8 layers, 256x256 padded to 512x512",
             "fp32_path": res["auto"], "split_bf16_dft_gemm": res["dft_gemm"],
             "speedup_vs_fp32": res["auto"]["ms_per_step"] / res["dft_gemm"]["ms_per_step"],
-            "rel_l2_intensity_vs_fp32": dI, "rel_l2_gradient_vs_fp32": dg}
+            "rel_l2_intensity_vs_fp32": dI, "rel_l2_gradient_vs_fp32": dg,
+            "tensor": {"gemm_flops_per_step": flops, "achieved_tflops_whole_path": tf,
+                       "peak_tflops": peak, "peak_source": "measured sustained bf16" if peaks else "fallback",
+                       "frac_whole_path": tf / peak,
+                       "note": "whole-path time (GEMMs and the conversion kernels between them) in the denominator"}}
 
 
 def main():

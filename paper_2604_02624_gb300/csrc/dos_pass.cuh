@@ -321,13 +321,14 @@ struct Pass {
 };
 
 // ------------------------------------------------------------------ kernels
-// Lines of up to 20 elements per thread fit three blocks per SM in registers
-// (64 per thread; the column and forward row passes then need no or few spills).
+// The forward row pass of lines with up to 20 elements per thread fits three
+// blocks per SM in 64 registers per thread without spills (measured faster than
+// two; the column pass is faster with its own register allocation).
 template <class LF>
 constexpr int pass_min_blocks() { return LF::E <= 20 ? 3 : 1; }
 
 template <class LF, bool ADJ, bool APERTURE>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, pass_min_blocks<LF>()) k_col(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL) k_col(PassArgs a) {
   Pass<LF>::template col<ADJ, APERTURE>(a);
 }
 template <class LF, bool SAVE>
