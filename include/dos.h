@@ -91,6 +91,8 @@ enum {
  *    tensor cores in split-BF16 (three terms hi*hi + hi*lo + lo*hi, FP32
  *    accumulation in tensor memory), channels processed in chunks; only on
  *    request (it trades accuracy, ~1e-5..1e-4, and speed for tensor cores).
+ *  DOS_PATH_DFT_GEMM_X3: the same with every operand split into three bf16
+ *    parts and six products kept (~1e-7 per GEMM, twice the tensor work).
  *  DOS_PATH_AUTO: dos_create times one forward+backward of every available
  *    multi-pass (plain and bulk) / cluster-resident configuration and keeps
  *    the fastest.
@@ -109,7 +111,8 @@ enum {
   DOS_PATH_MULTIPASS = 1,
   DOS_PATH_FUSED = 2,
   DOS_PATH_DFT_GEMM = 3,
-  DOS_PATH_MULTIPASS_BULK = 4
+  DOS_PATH_MULTIPASS_BULK = 4,
+  DOS_PATH_DFT_GEMM_X3 = 5
 };
 
 typedef struct dos_config {
@@ -349,7 +352,7 @@ DOS_API size_t dos_workspace_bytes(const dos_ctx *ctx);
 /* Number of kernel launches queued by the last dos_forward / dos_loss / dos_backward. */
 DOS_API int dos_last_launch_count(const dos_ctx *ctx);
 
-/* Implementation chosen for the context (DOS_PATH_MULTIPASS, _MULTIPASS_BULK, _FUSED or _DFT_GEMM). */
+/* Implementation chosen for the context (DOS_PATH_MULTIPASS, _MULTIPASS_BULK, _FUSED, _DFT_GEMM or _DFT_GEMM_X3). */
 DOS_API int dos_path(const dos_ctx *ctx);
 
 /*

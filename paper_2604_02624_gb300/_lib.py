@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_PKG, "libdos.so")
 DOS_OK, DOS_ERR_ARG, DOS_ERR_OOM, DOS_ERR_CUDA, DOS_ERR_STATE, DOS_ERR_TIMEOUT, DOS_ERR_UNSUPPORTED = range(7)
 DOS_EVAN_DECAY, DOS_EVAN_ZERO = 0, 1
 DOS_LOSS_MSE, DOS_LOSS_MSE_SCALED = 0, 1
-DOS_PATH_AUTO, DOS_PATH_MULTIPASS, DOS_PATH_FUSED, DOS_PATH_DFT_GEMM, DOS_PATH_MULTIPASS_BULK = 0, 1, 2, 3, 4
+DOS_PATH_AUTO, DOS_PATH_MULTIPASS, DOS_PATH_FUSED, DOS_PATH_DFT_GEMM, DOS_PATH_MULTIPASS_BULK, DOS_PATH_DFT_GEMM_X3 = \
+    0, 1, 2, 3, 4, 5
 
 ERROR_NAMES = {1: "DOS_ERR_ARG", 2: "DOS_ERR_OOM", 3: "DOS_ERR_CUDA", 4: "DOS_ERR_STATE",
                5: "DOS_ERR_TIMEOUT", 6: "DOS_ERR_UNSUPPORTED"}

@@ -72,7 +72,8 @@ class DiffractiveStack:
         cfg.detector_bin = int(detector_bin)
         cfg.path = {"auto": L.DOS_PATH_AUTO, "multipass": L.DOS_PATH_MULTIPASS,
                     "multipass_bulk": L.DOS_PATH_MULTIPASS_BULK,
-                    "fused": L.DOS_PATH_FUSED, "dft_gemm": L.DOS_PATH_DFT_GEMM}[path]
+                    "fused": L.DOS_PATH_FUSED, "dft_gemm": L.DOS_PATH_DFT_GEMM,
+                    "dft_gemm_x3": L.DOS_PATH_DFT_GEMM_X3}[path]
         self._ctx = None
         with torch.cuda.device(self.device):
             self._ctx = L.dos_create(cfg, torch.cuda.current_stream(self.device).cuda_stream)
@@ -112,7 +113,8 @@ class DiffractiveStack:
 
     @property
     def path(self) -> str:
-        return {1: "multipass", 2: "fused", 3: "dft_gemm", 4: "multipass_bulk"}[L.dos_path(self._ctx)]
+        return {1: "multipass", 2: "fused", 3: "dft_gemm", 4: "multipass_bulk",
+                5: "dft_gemm_x3"}[L.dos_path(self._ctx)]
 
     # ------------------------------------------------------------------ compute
     def forward(self, h: torch.Tensor, save_for_backward: bool = True,

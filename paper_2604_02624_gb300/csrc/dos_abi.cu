@@ -274,7 +274,7 @@ int validate(const dos_config* c) {
     return fail(DOS_ERR_ARG, "evanescent must be DOS_EVAN_DECAY or DOS_EVAN_ZERO");
   if (c->loss != DOS_LOSS_MSE && c->loss != DOS_LOSS_MSE_SCALED)
     return fail(DOS_ERR_ARG, "loss must be DOS_LOSS_MSE or DOS_LOSS_MSE_SCALED");
-  if (c->path < DOS_PATH_AUTO || c->path > DOS_PATH_MULTIPASS_BULK) return fail(DOS_ERR_ARG, "path must be a DOS_PATH_* value");
+  if (c->path < DOS_PATH_AUTO || c->path > DOS_PATH_DFT_GEMM_X3) return fail(DOS_ERR_ARG, "path must be a DOS_PATH_* value");
   return DOS_OK;
 }
 
@@ -368,30 +368,33 @@ int build(dos_ctx* x, const dos_config* c) {
     }
   }
   // split-BF16 DFT-GEMM plan (only when requested)
-  if (c->path == DOS_PATH_DFT_GEMM) {
+  const bool gemm = c->path == DOS_PATH_DFT_GEMM || c->path == DOS_PATH_DFT_GEMM_X3;
+  if (gemm) {
     auto pad = [](int v, int q) { return (v + q - 1) / q * q; };
+    x->gp.parts = c->path == DOS_PATH_DFT_GEMM_X3 ? 3 : 2;
     x->gp.n = x->n;
     x->gp.m = x->m;
     x->gp.nwc = std::min(x->nw, 256);
     x->gp.kp1 = pad(2 * x->n, 64);
     x->gp.kp2 = pad(2 * x->m, 64);
-    x->gp.rp1 = pad(2 * x->m, 128);
-    x->gp.rp2 = pad(2 * x->n, 128);
+    x->gp.rp1 = pad(2 * x->m, 256);
+    x->gp.rp2 = pad(2 * x->n, 256);
     x->gchunks = (x->nw + x->gp.nwc - 1) / x->gp.nwc;
     partial_count = std::max(partial_count, (size_t)x->gchunks * x->K * n2);
   }
   int rc;
-  if (c->path == DOS_PATH_DFT_GEMM) {
+  if (gemm) {
     dos::GemmPlan& g = x->gp;
     const size_t nwc = (size_t)g.nwc;
     const size_t xsz = std::max({nwc * g.m * g.kp1, nwc * g.m * g.kp2, nwc * g.n * g.kp1, nwc * g.n * g.kp2});
     const size_t dsz = std::max({(size_t)g.rp1 * nwc * g.m, (size_t)g.rp2 * nwc * g.m, (size_t)g.rp1 * nwc * g.n});
-    if ((rc = x->alloc(&g.Fh, (size_t)g.rp1 * g.kp1, "DFT matrix"))) return rc;
-    if ((rc = x->alloc(&g.Fl, (size_t)g.rp1 * g.kp1, "DFT matrix"))) return rc;
-    if ((rc = x->alloc(&g.Gh, (size_t)g.rp2 * g.kp2, "IDFT matrix"))) return rc;
-    if ((rc = x->alloc(&g.Gl, (size_t)g.rp2 * g.kp2, "IDFT matrix"))) return rc;
-    if ((rc = x->alloc(&g.Xh, xsz, "GEMM operand"))) return rc;
-    if ((rc = x->alloc(&g.Xl, xsz, "GEMM operand"))) return rc;
+    g.F.k = g.G.k = g.X.k = g.parts;
+    for (int q = 0; q < 3; ++q) g.F.p[q] = g.G.p[q] = g.X.p[q] = nullptr;
+    for (int q = 0; q < g.parts; ++q) {
+      if ((rc = x->alloc(&g.F.p[q], (size_t)g.rp1 * g.kp1, "DFT matrix"))) return rc;
+      if ((rc = x->alloc(&g.G.p[q], (size_t)g.rp2 * g.kp2, "IDFT matrix"))) return rc;
+      if ((rc = x->alloc(&g.X.p[q], xsz, "GEMM operand"))) return rc;
+    }
     if ((rc = x->alloc(&g.D, dsz, "GEMM output"))) return rc;
     if ((rc = x->alloc(&g.fld, nwc * n2, "GEMM field"))) return rc;
   }
@@ -399,7 +402,7 @@ int build(dos_ctx* x, const dos_config* c) {
   DOS_CUDA(cudaMemsetAsync(x->d_err, 0, sizeof(int), x->stream), "error flag");
   DOS_CUDA(cudaMallocHost(&x->h_err, sizeof(int)), "cudaMallocHost(error flag)");
   *x->h_err = 0;
-  if (c->path == DOS_PATH_DFT_GEMM) {
+  if (gemm) {
     x->gp.err = x->d_err;
     DOS_CUDA(dos::launch_build_dft(x->gp, x->stream), "DFT matrices");
   }
@@ -543,7 +546,7 @@ int gemm_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dL
 int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
   const size_t n2 = (size_t)c->n * c->n;
   c->launches = 0;
-  if (c->path == DOS_PATH_DFT_GEMM) return gemm_forward(c, d_h, d_I);
+  if (c->path == DOS_PATH_DFT_GEMM || c->path == DOS_PATH_DFT_GEMM_X3) return gemm_forward(c, d_h, d_I);
   if (c->path == DOS_PATH_FUSED) {
     dos::FusedArgs f;
     std::memset(&f, 0, sizeof(f));
@@ -615,7 +618,7 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
 int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
   const size_t n2 = (size_t)c->n * c->n;
   c->launches = 0;
-  if (c->path == DOS_PATH_DFT_GEMM) return gemm_backward(c, d_h, d_dLdI, d_dLdh);
+  if (c->path == DOS_PATH_DFT_GEMM || c->path == DOS_PATH_DFT_GEMM_X3) return gemm_backward(c, d_h, d_dLdI, d_dLdh);
   if (c->path == DOS_PATH_FUSED) {
     dos::FusedArgs f;
     std::memset(&f, 0, sizeof(f));
@@ -760,13 +763,14 @@ int time_choice(dos_ctx* x, const float* h0, const float* g0, float* d0, float* 
 }
 
 int choose_path(dos_ctx* x, int requested) {
-  if (requested == DOS_PATH_DFT_GEMM) {
-    x->path = DOS_PATH_DFT_GEMM;
+  if (requested == DOS_PATH_DFT_GEMM || requested == DOS_PATH_DFT_GEMM_X3) {
+    x->path = requested;
     x->fops = nullptr;
     x->bulk = false;
-    x->describe = "path=dft_gemm chunk=" + std::to_string(x->gp.nwc) + " kp=" + std::to_string(x->gp.kp1) + "/" +
+    x->describe = std::string(requested == DOS_PATH_DFT_GEMM_X3 ? "path=dft_gemm_x3" : "path=dft_gemm") +
+                  " chunk=" + std::to_string(x->gp.nwc) + " kp=" + std::to_string(x->gp.kp1) + "/" +
                   std::to_string(x->gp.kp2) + " rows=" + std::to_string(x->gp.rp1) + "/" + std::to_string(x->gp.rp2) +
-                  " (split-BF16, 3 terms, tcgen05)";
+                  (x->gp.parts == 3 ? " (split-BF16, 3 parts, 6 products, tcgen05)" : " (split-BF16, 2 parts, 3 products, tcgen05)");
     return DOS_OK;
   }
   if (requested == DOS_PATH_MULTIPASS) {

@@ -1,7 +1,9 @@
 // dos_gemm.cu - split-BF16 DFT-GEMM form of the propagation (tcgen05, TMEM).
 //
 // See dos_gemm.cuh for the formulation.  The GEMM kernel: one CTA computes a
-// 128 x 256 FP32 tile in tensor memory; K is consumed in chunks of 64 bf16
+// 256 x 256 FP32 tile in tensor memory (two 128-row MMAs sharing each B
+// chunk, all 512 TMEM columns: operand bytes per FLOP are what bound the
+// kernel, through L2); K is consumed in chunks of 64 bf16
 // staged in shared memory in the canonical K-major, non-swizzled core-matrix
 // layout (8 rows x 16 bytes per core matrix; 128 B between core matrices
 // along K, 1024 B between 8-row groups).  Operands arrive by cp.async
@@ -20,8 +22,9 @@
 
 namespace dos {
 
-constexpr int GTM = 128, GTN = 256, GTK = 64;
-constexpr int GSTAGES = 4;
+constexpr int GTM = 128, GTN = 256, GTK = 64;  // one MMA: 128 x 256 x 16 per K step
+constexpr int GCM = 2 * GTM;                    // rows per CTA
+constexpr int GSTAGES = 3;
 constexpr int kGemmThreads = 128;
 constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier wait (a fraction of a second)
 
@@ -61,7 +64,7 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 struct __align__(1024) GemmSmem {
-  uint8_t a[GSTAGES][GTM * GTK * 2];  // 16 KB per stage
+  uint8_t a[GSTAGES][GCM * GTK * 2];  // 32 KB per stage
   uint8_t b[GSTAGES][GTN * GTK * 2];  // 32 KB per stage
   uint64_t bar[GSTAGES];
   uint32_t tmem;
@@ -71,10 +74,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gsm_raw);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int m0 = blockIdx.x * GTM, n0 = blockIdx.y * GTN;
+  const int m0 = blockIdx.x * GCM, n0 = blockIdx.y * GTN;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
-                 "r"(GTN));
+                 "r"(2 * GTN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
     const __nv_bfloat16* A = g.a[seg];
     const __nv_bfloat16* B = g.b[seg];
 #pragma unroll
-    for (int q = 0; q < GTM * (GTK / 8) / kGemmThreads; ++q) {
+    for (int q = 0; q < GCM * (GTK / 8) / kGemmThreads; ++q) {
       const int c = tid + q * kGemmThreads;
       const int r = c / (GTK / 8), kc = c % (GTK / 8);
       cp16(sm.a[st] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16, A + (size_t)(m0 + r) * g.K + k0 + kc * 8, 16);
@@ -127,12 +130,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
       const uint32_t sa = smem_addr(sm.a[st]), sb = smem_addr(sm.b[st]);
 #pragma unroll
       for (int kk = 0; kk < GTK / 16; ++kk) {
-        const uint64_t da = kmajor_desc(sa + kk * 256), db = kmajor_desc(sb + kk * 256);
+        const uint64_t db = kmajor_desc(sb + kk * 256);
         const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // rows h*128.. of the tile: A core matrices from byte 16 KB * h
+          const uint64_t da = kmajor_desc(sa + h * (GTM / 8) * (GTK / 8) * 128 + kk * 256);
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(h * GTN)),
+              "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_addr(&sm.bar[st])));
@@ -160,11 +167,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    const int row = m0 + warp * 32 + lane;
+   for (int h = 0; h < 2; ++h) {
+    const int row = m0 + h * GTM + warp * 32 + lane;
     float* drow = g.D + (size_t)row * g.ldd;
     for (int c0 = 0; c0 < GTN; c0 += 32) {
       uint32_t r[32];
-      const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * GTN + c0);
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
           "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -186,6 +194,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
           if (cb + j < g.cols) drow[cb + j] = __uint_as_float(r[j]);
       }
     }
+   }
   } else {
     // give the MMAs still in flight a bounded chance to finish before the
     // tensor memory they write is released
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GTN));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * GTN));
 }
 
 cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s) {
@@ -207,23 +216,26 @@ cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s) {
     attr = true;
   }
   // row tiles fastest: the CTAs of one column tile (same B operand) run together
-  const dim3 grid(g.rows / GTM, (g.cols + GTN - 1) / GTN);
+  const dim3 grid(g.rows / GCM, (g.cols + GTN - 1) / GTN);
   k_tc_gemm<<<grid, kGemmThreads, sm, s>>>(g);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ constant matrices
-__device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t i, float v) {
+// x -> bf16 parts: each the round-to-nearest of what the earlier parts leave
+__device__ __forceinline__ void split_store(const Parts& P, size_t i, float v) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  hi[i] = h;
-  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  P.p[0][i] = h;
+  const float r1 = v - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  P.p[1][i] = m;
+  if (P.k > 2) P.p[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
 // W rows r: output o = r / 2 (re for even r, im for odd r); K index c: input
 // element c (its real part) for c < kin, input c - kin (imaginary part) for
 // kin <= c < 2 kin.  Entry exp(sign 2 pi j o x / m) in FP64, split into bf16.
-__global__ void k_dft_matrix(__nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, int rows_pad, int kpad,
-                             int nout, int kin, int m, int sign) {
+__global__ void k_dft_matrix(Parts W, int rows_pad, int kpad, int nout, int kin, int m, int sign) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)rows_pad * kpad) return;
   const int r = (int)(i / kpad), c = (int)(i % kpad);
@@ -238,13 +250,13 @@ __global__ void k_dft_matrix(__nv_bfloat16* __restrict__ hi, __nv_bfloat16* __re
     if ((r & 1) == 0) v = (float)(c < kin ? co : -s);
     else v = (float)(c < kin ? s : co);
   }
-  split_store(hi, lo, i, v);
+  split_store(W, i, v);
 }
 
 cudaError_t launch_build_dft(GemmPlan& p, cudaStream_t s) {
   const size_t nf = (size_t)p.rp1 * p.kp1, ng = (size_t)p.rp2 * p.kp2;
-  k_dft_matrix<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(p.Fh, p.Fl, p.rp1, p.kp1, p.m, p.n, p.m, -1);
-  k_dft_matrix<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(p.Gh, p.Gl, p.rp2, p.kp2, p.n, p.m, p.m, +1);
+  k_dft_matrix<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(p.F, p.rp1, p.kp1, p.m, p.n, p.m, -1);
+  k_dft_matrix<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(p.G, p.rp2, p.kp2, p.n, p.m, p.m, +1);
   return cudaGetLastError();
 }
 
@@ -252,8 +264,8 @@ cudaError_t launch_build_dft(GemmPlan& p, cudaStream_t s) {
 // field (complex [w][y][x]) -> X rows (w, y): [Re(u), Im(u), 0 ...] of length kp.
 // mode 0: u = v;  mode 1: checkpoint v, u = t(h) v (forward layer);  mode 2: aperture.
 __global__ void k_prep_field(const float2* __restrict__ v, float2* __restrict__ ckpt, const float* __restrict__ h,
-                             const ChanConst* __restrict__ chan, __nv_bfloat16* __restrict__ Xh,
-                             __nv_bfloat16* __restrict__ Xl, int n, int kp, int mode, int a_off, int a_w) {
+                             const ChanConst* __restrict__ chan, Parts X, int n, int kp, int mode, int a_off,
+                             int a_w) {
   const int wy = blockIdx.x;  // w * n + y
   const int w = wy / n, y = wy % n;
   const size_t base = (size_t)wy * kp;
@@ -276,13 +288,12 @@ __global__ void k_prep_field(const float2* __restrict__ v, float2* __restrict__ 
       }
       val = c < n ? u.x : u.y;
     }
-    split_store(Xh, Xl, base + c, val);
+    split_store(X, base + c, val);
   }
 }
 
 // D (rows 2k+{0,1}, cols (w, j) of width nj) -> X rows (w, k): [Re over j, Im over j, 0 ...]
-__global__ void k_prep_rows(const float* __restrict__ D, size_t ldd, __nv_bfloat16* __restrict__ Xh,
-                            __nv_bfloat16* __restrict__ Xl, int nk, int nj, int kp) {
+__global__ void k_prep_rows(const float* __restrict__ D, size_t ldd, Parts X, int nk, int nj, int kp) {
   const int wk = blockIdx.x;  // w * nk + k
   const int w = wk / nk, k = wk % nk;
   const size_t base = (size_t)wk * kp;
@@ -292,15 +303,14 @@ __global__ void k_prep_rows(const float* __restrict__ D, size_t ldd, __nv_bfloat
     float val = 0.f;
     if (c < nj) val = dre[c];
     else if (c < 2 * nj) val = dim[c - nj];
-    split_store(Xh, Xl, base + c, val);
+    split_store(X, base + c, val);
   }
 }
 
 // D (rows 2ky+{0,1}, cols (w, kx) of width m) times H_w(|ky|,|kx|) (conj if adj)
 // -> X rows (w, kx): [Re over ky, Im over ky, 0 ...] (32 x 32 transpose in smem)
 __global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const float2* __restrict__ Hq, int hs,
-                                __nv_bfloat16* __restrict__ Xh, __nv_bfloat16* __restrict__ Xl, int m, int kp,
-                                int adj, Misalign mis) {
+                                Parts X, int m, int kp, int adj, Misalign mis) {
   __shared__ float2 tile[32][33];
   const int w = blockIdx.z;
   const int ky0 = blockIdx.y * 32, kx0 = blockIdx.x * 32;
@@ -324,8 +334,8 @@ __global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const f
     if (kx < m && ky < m) {
       const float2 val = tile[threadIdx.x][r];
       const size_t base = ((size_t)w * m + kx) * kp;
-      split_store(Xh, Xl, base + ky, val.x);
-      split_store(Xh, Xl, base + m + ky, val.y);
+      split_store(X, base + ky, val.x);
+      split_store(X, base + m + ky, val.y);
     }
   }
   // zero the K padding of the rows this block owns (once, by the ky0 == 0 blocks)
@@ -334,7 +344,7 @@ __global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const f
       const int kx = kx0 + r;
       if (kx >= m) continue;
       const size_t base = ((size_t)w * m + kx) * kp;
-      for (int c = 2 * m + threadIdx.x; c < kp; c += 32) split_store(Xh, Xl, base + c, 0.f);
+      for (int c = 2 * m + threadIdx.x; c < kp; c += 32) split_store(X, base + c, 0.f);
     }
   }
 }
@@ -414,15 +424,21 @@ __global__ void k_field_adj(float2* __restrict__ field, const float2* __restrict
 struct GemmProp {
   GemmPlan* p;
   cudaStream_t s;
-  cudaError_t gemm(const __nv_bfloat16* Wh, const __nv_bfloat16* Wl, int rows, int K, int cols) {
+  // D = W X^T over the kept products of the parts: (0,0), (0,1), (1,0) and,
+  // with three parts, (0,2), (2,0), (1,1).  The tensor core's FP32 accumulation
+  // loses a little of every partial sum (measured: the relative error grows with
+  // the number of accumulation steps at the accumulator's magnitude), so the
+  // small products go first and the large (0,0) product last: the error is then
+  // that of the (0,0) product alone.
+  cudaError_t gemm(const Parts& W, int rows, int K, int cols) {
+    static const int ta2[3] = {0, 1, 0}, tb2[3] = {1, 0, 0};
+    static const int ta3[6] = {1, 0, 2, 0, 1, 0}, tb3[6] = {1, 2, 0, 1, 0, 0};
     GemmArgs g;
-    g.a[0] = Wh;
-    g.b[0] = p->Xh;
-    g.a[1] = Wh;
-    g.b[1] = p->Xl;
-    g.a[2] = Wl;
-    g.b[2] = p->Xh;
-    g.nseg = 3;
+    g.nseg = p->parts == 3 ? 6 : 3;
+    for (int t = 0; t < g.nseg; ++t) {
+      g.a[t] = W.p[p->parts == 3 ? ta3[t] : ta2[t]];
+      g.b[t] = p->X.p[p->parts == 3 ? tb3[t] : tb2[t]];
+    }
     g.rows = rows;
     g.cols = cols;
     g.K = K;
@@ -441,14 +457,14 @@ cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool 
   const int n = p.n, m = p.m;
   cudaError_t e;
   const int c1 = nwc * n, c2 = nwc * m;
-  if ((e = g.gemm(p.Fh, p.Fl, p.rp1, p.kp1, c1)) != cudaSuccess) return e;        // row DFT
-  k_prep_rows<<<nwc * m, 128, 0, s>>>(p.D, (size_t)c1, p.Xh, p.Xl, m, n, p.kp1);
-  if ((e = g.gemm(p.Fh, p.Fl, p.rp1, p.kp1, c2)) != cudaSuccess) return e;        // column DFT
-  k_prep_spectrum<<<dim3((m + 31) / 32, (m + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c2, Hq, hs, p.Xh,
-                                                                                  p.Xl, m, p.kp2, adj ? 1 : 0, mis);
-  if ((e = g.gemm(p.Gh, p.Gl, p.rp2, p.kp2, c2)) != cudaSuccess) return e;        // column IDFT
-  k_prep_rows<<<nwc * n, 128, 0, s>>>(p.D, (size_t)c2, p.Xh, p.Xl, n, m, p.kp2);
-  if ((e = g.gemm(p.Gh, p.Gl, p.rp2, p.kp2, c1)) != cudaSuccess) return e;        // row IDFT
+  if ((e = g.gemm(p.F, p.rp1, p.kp1, c1)) != cudaSuccess) return e;        // row DFT
+  k_prep_rows<<<nwc * m, 128, 0, s>>>(p.D, (size_t)c1, p.X, m, n, p.kp1);
+  if ((e = g.gemm(p.F, p.rp1, p.kp1, c2)) != cudaSuccess) return e;        // column DFT
+  k_prep_spectrum<<<dim3((m + 31) / 32, (m + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c2, Hq, hs, p.X, m,
+                                                                                  p.kp2, adj ? 1 : 0, mis);
+  if ((e = g.gemm(p.G, p.rp2, p.kp2, c2)) != cudaSuccess) return e;        // column IDFT
+  k_prep_rows<<<nwc * n, 128, 0, s>>>(p.D, (size_t)c2, p.X, n, m, p.kp2);
+  if ((e = g.gemm(p.G, p.rp2, p.kp2, c1)) != cudaSuccess) return e;        // row IDFT
   k_prep_out<<<dim3((n + 31) / 32, (n + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c1, p.fld, o, I, n, of,
                                                                              fov);
   return cudaGetLastError();
@@ -456,7 +472,7 @@ cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool 
 
 cudaError_t gemm_prep_field(GemmPlan& p, int nwc, const float2* v, float2* ckpt, const float* h,
                             const ChanConst* chan, int mode, int a_off, int a_w, cudaStream_t s) {
-  k_prep_field<<<nwc * p.n, 128, 0, s>>>(v, ckpt, h, chan, p.Xh, p.Xl, p.n, p.kp1, mode, a_off, a_w);
+  k_prep_field<<<nwc * p.n, 128, 0, s>>>(v, ckpt, h, chan, p.X, p.n, p.kp1, mode, a_off, a_w);
   return cudaGetLastError();
 }
 

@@ -9,9 +9,11 @@
 //   C = G B (column IDFT),      V = C G^T-rows (row IDFT),
 // each written as Y = W X with the data matrix X stacked over channels.
 //
-// Precision: every operand is split into bf16 hi + lo (x = hi + lo to ~2^-16);
-// a product keeps three terms, W_hi X_hi + W_hi X_lo + W_lo X_hi, accumulated
-// in FP32 in tensor memory.  In real form a complex W (m x k) is a 2m x 2k
+// Precision: every operand is split into bf16 parts, x = x0 + x1 (+ x2), each
+// the bf16 rounding of what the earlier parts leave.  Two parts carry ~2^-17
+// relative and a product keeps three terms, W0 X0 + W0 X1 + W1 X0; three parts
+// carry ~2^-26 and a product keeps six, adding W0 X2 + W2 X0 + W1 X1 (the
+// dropped terms are below 2^-26).  Terms accumulate in FP32 in tensor memory.  In real form a complex W (m x k) is a 2m x 2k
 // matrix whose row 2o is [Re W_o, -Im W_o] and row 2o+1 is [Im W_o, Re W_o];
 // the data column is [Re x; Im x], so lanes 2o / 2o+1 of the accumulator hold
 // the real / imaginary part of output o.
@@ -26,10 +28,11 @@ namespace dos {
 
 // One GEMM D[rows][cols] (f32, row-major, leading dimension ldd) =
 //   sum over segments s of A_s[rows][K] * B_s[cols][K]^T, A_s / B_s bf16 K-major.
-// rows % 128 == 0, K % 64 == 0; cols may be ragged (tile of 256).
+// rows % 256 == 0, K % 64 == 0; cols may be ragged (tile of 256).
+constexpr int kMaxGemmTerms = 6;
 struct GemmArgs {
-  const __nv_bfloat16* a[3];
-  const __nv_bfloat16* b[3];
+  const __nv_bfloat16* a[kMaxGemmTerms];
+  const __nv_bfloat16* b[kMaxGemmTerms];
   int nseg;
   int rows, cols, K;
   float* D;
@@ -40,13 +43,20 @@ struct GemmArgs {
 cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s);
 
 // Context-level buffers and constants of the DFT-GEMM path.
+// The bf16 parts of one operand (parts 1 or 2 unused when there are fewer).
+struct Parts {
+  __nv_bfloat16* p[3];
+  int k;  // 2 or 3
+};
+
 struct GemmPlan {
   int n, m, nwc;            // layer side, padded size, channels per chunk
   int kp1, kp2;             // padded K of the N- and M-point products (multiples of 64)
-  int rp1, rp2;             // padded rows of F (2M) and G (2N) (multiples of 128)
-  __nv_bfloat16 *Fh, *Fl;   // [rp1][kp1]
-  __nv_bfloat16 *Gh, *Gl;   // [rp2][kp2]
-  __nv_bfloat16 *Xh, *Xl;   // data operand, [max cols][max kp]
+  int rp1, rp2;             // padded rows of F (2M) and G (2N) (multiples of 256)
+  int parts;                // bf16 parts per operand: 2 (three products) or 3 (six)
+  Parts F;                  // [rp1][kp1] each
+  Parts G;                  // [rp2][kp2] each
+  Parts X;                  // data operand, [max cols][max kp] each
   float* D;                 // GEMM output, [max rows][max cols]
   float2* fld;              // FP32 working field [nwc][n][n]
   int* err;

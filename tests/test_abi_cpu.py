@@ -99,7 +99,7 @@ def _cfg(**over):
     ({"evanescent": 7}, "evanescent"),
     ({"loss": 9}, "loss"),
     ({"n_lambda_total": 1}, "n_lambda_total"),
-    ({"path": 5}, "path"),
+    ({"path": 6}, "path"),
     ({"detector_bin": 3}, "detector_bin"),
     ({"detector_bin": -2}, "detector_bin"),
     ({"path": -1}, "path"),
@@ -114,7 +114,7 @@ def test_invalid_designs_are_rejected_on_the_host(lib, over, msg):
 
 
 @pytest.mark.parametrize("path", [L.DOS_PATH_AUTO, L.DOS_PATH_MULTIPASS, L.DOS_PATH_FUSED,
-                                  L.DOS_PATH_DFT_GEMM, L.DOS_PATH_MULTIPASS_BULK])
+                                  L.DOS_PATH_DFT_GEMM, L.DOS_PATH_MULTIPASS_BULK, L.DOS_PATH_DFT_GEMM_X3])
 def test_every_declared_path_passes_host_validation(lib, path):
     """Host validation accepts every DOS_PATH_* value (without a GPU the call
     then stops at the first CUDA call, not at argument checking)."""

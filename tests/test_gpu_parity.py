@@ -13,7 +13,7 @@ from paper_2604_02624_gb300 import workloads as W
 from paper_2604_02624_gb300 import _lib as L
 from paper_2604_02624_gb300.api import DiffractiveStack, DosFunction
 
-from gpu_cases import (TOL_FIELD, TOL_GRAD_FD, TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS,
+from gpu_cases import (SPLIT_TARGET, TOL_FIELD, TOL_GRAD_FD, TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS,
                        custom, oracle_model, rel_l2, replace, split_bound)
 
 pytestmark = pytest.mark.gpu
@@ -364,6 +364,36 @@ def test_split_bf16_dft_gemm_against_oracle(name, sub):
     assert e_field <= split_bound(n_gemms), e_field
     assert e_int <= split_bound(n_gemms, intensity=True), e_int
     assert rel_l2(g, g_ref) <= TOL_GRAD_FD
+    assert e_int <= SPLIT_TARGET  # with the small products accumulated first, on every geometry
+    st.close()
+
+
+@pytest.mark.parametrize("name,sub", [("tiny", None), ("small", None), ("massive", 16), ("precision", 16)])
+def test_split_bf16_three_parts_meets_the_split_target(name, sub):
+    """Three bf16 parts per operand and six products per GEMM: field,
+    intensity and gradient within 1e-4 of the FP64 oracle (the split-BF16
+    target) on every geometry, including the 8-layer precision design (36
+    chained GEMMs, where two parts miss it); the short cascades meet the FP32
+    paths' field tolerance.  What remains is the tensor core's FP32
+    accumulation of the (0,0) product, ~1e-6 per GEMM at K = 1024."""
+    w = W.workload(name)
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    if sub:
+        idx = W.subset_indices(w.n_lambda, sub)
+        w, T = w.subset(idx), T[idx]
+    st = _stack(w, path="dft_gemm_x3")
+    assert st.path == "dft_gemm_x3"
+    hd = _t(h)
+    I = st.forward(hd)
+    o = st.output_field()
+    _, _, dl = st.loss(_t(T))
+    g = _np(st.backward(hd, dl)).astype(np.float64)
+    L_ref, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    e_field = rel_l2(_np(o).astype(np.complex128), fwd["o"])
+    assert e_field <= SPLIT_TARGET
+    assert rel_l2(_np(I).astype(np.float64), fwd["I"]) <= SPLIT_TARGET
+    assert rel_l2(g, g_ref) <= SPLIT_TARGET
     if name in ("tiny", "small"):
-        assert e_int <= 1e-4  # spec split-BF16 target holds for the short cascades
+        assert e_field <= TOL_FIELD
     st.close()
