@@ -126,6 +126,11 @@ struct dos_ctx {
   size_t bytes = 0;
   float2 *S = nullptr, *ckpt = nullptr, *o = nullptr, *Hq = nullptr, *arow = nullptr, *tw = nullptr;
   float2* ckt = nullptr;  // transmission checkpoints of the cluster-resident path
+  // create-time input field v1 = P_z0(aperture), [nw][n][n] (Section 2's uniform
+  // input field after the first gap; independent of the thickness)
+  float2* v1 = nullptr;
+  bool ckpt1_is_v1 = false;  // the last multi-pass forward started from v1
+  int step_launches = 0;     // kernels in the captured step graph
   dos::ChanConst* chan = nullptr;
   float* partial = nullptr;
   dos::LossStats* stats = nullptr;
@@ -440,6 +445,17 @@ int build(dos_ctx* x, const dos_config* c) {
   DOS_CUDA(dos::launch_arow(x->arow, x->m, x->oa, x->ap, x->stream), "aperture spectrum");
   const int RP = x->ops->P % 2 == 0 ? x->ops->P + 1 : x->ops->P;
   DOS_CUDA(dos::launch_twiddles(x->tw, x->ops->P, x->ops->Q, RP, x->m, x->stream), "twiddles");
+  if (!gemm) {
+    // v1: the aperture's separable spectrum through gap 0, inverse row DFT, crop
+    if ((rc = x->alloc(&x->v1, (size_t)x->nw * n2, "input field"))) return rc;
+    dos::PassArgs a = x->base();
+    a.Hq = x->hq_slot(0);
+    a.out_r0 = 0;
+    a.out_r1 = x->n;
+    a.fout = x->v1;
+    DOS_CUDA(x->ops->col(a, false, true, x->stream), "input field");
+    DOS_CUDA(x->ops->row_back(a, x->stream), "input field");
+  }
   DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
   if ((rc = choose_path(x, c->path))) return rc;
   DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
@@ -583,20 +599,30 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
   }
   const dos::PassOps* op = c->ops;
   dos::PassArgs a = c->base();
-  // gap 0: the aperture field has the separable spectrum Arow[ky] Arow[kx]
-  a.Hq = c->hq_slot(0);
-  a.mis = c->gap_mis(0);
-  a.out_r0 = 0;
-  a.out_r1 = c->n;
-  DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, true, c->stream), "forward column pass (aperture)");
-  ++c->launches;
+  // gap 0 is the create-time table v1 unless the layers are displaced (then the
+  // first gap depends on layer 1's displacement): the aperture field has the
+  // separable spectrum Arow[ky] Arow[kx]
+  c->ckpt1_is_v1 = c->v1 && !c->mis_on;
+  if (!c->ckpt1_is_v1) {
+    a.Hq = c->hq_slot(0);
+    a.mis = c->gap_mis(0);
+    a.out_r0 = 0;
+    a.out_r1 = c->n;
+    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, true, c->stream), "forward column pass (aperture)");
+    ++c->launches;
+  }
   for (int l = 1; l <= c->K; ++l) {
     a.h = d_h + (size_t)(l - 1) * n2;
     a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
-    a.stall = c->take_stall();
-    DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,
-              c->bulk ? op->bulk_row_fwd(a, save != 0, c->stream) : op->row_fwd(a, save != 0, c->stream),
-              "forward row pass");
+    if (l == 1 && c->ckpt1_is_v1) {
+      a.fin = c->v1;
+      DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_first(a, c->stream), "first row pass");
+    } else {
+      a.stall = c->take_stall();
+      DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,
+                c->bulk ? op->bulk_row_fwd(a, save != 0, c->stream) : op->row_fwd(a, save != 0, c->stream),
+                "forward row pass");
+    }
     a.Hq = c->hq_slot(l);
     a.mis = c->gap_mis(l);
     a.in_r0 = 0;
@@ -674,7 +700,7 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
               c->bulk ? op->bulk_col(a, true, c->stream) : op->col(a, true, false, c->stream),
               "adjoint column pass");
     a.h = d_h + (size_t)(l - 1) * n2;
-    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
+    a.ckpt = (l == 1 && c->ckpt1_is_v1) ? c->v1 : c->ckpt + (size_t)(l - 1) * c->nw * n2;
     a.partial = c->partial + (size_t)(l - 1) * c->n_chunks * n2;
     a.stall = c->take_stall();
     DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT,
@@ -1045,12 +1071,14 @@ DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dL
       const int det2 = (c->fov / c->bin) * (c->fov / c->bin);
       const double norm = (double)c->nw_total * det2;
       rc = run_forward(c, d_h, d_I, 1);
+      const int fwd_launches = c->launches;
       if (!rc) e = dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, c->fov, c->bin, c->gstream);
       if (!rc && e == cudaSuccess)
         e = dos::launch_loss_final(c->stats, c->nw, det2, norm, c->loss, c->d_loss, d_psnr, c->gstream);
       if (!rc && e == cudaSuccess)
         e = dos::launch_dldi(c->o, d_T, c->stats, c->dLdI_step, c->nw, c->fov, c->bin, norm, c->loss, c->gstream);
       if (!rc && e == cudaSuccess) rc = run_backward(c, d_h, c->dLdI_step, d_dLdh);
+      if (!rc) c->step_launches = fwd_launches + 3 + c->launches;
       cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
       if (e == cudaSuccess) e = e2;
     }
@@ -1072,7 +1100,7 @@ DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dL
   DOS_CUDA(cudaGraphLaunch(c->gexec, c->gstream), "step graph launch");
   DOS_CUDA(cudaEventRecord(c->ev_out, c->gstream), "step order");
   DOS_CUDA(cudaStreamWaitEvent(c->stream, c->ev_out, 0), "step order");
-  c->launches = (c->path == DOS_PATH_FUSED ? 1 : 2 * c->K + 2) + 3 + (c->path == DOS_PATH_FUSED ? 2 : 2 * c->K + 2);
+  c->launches = c->step_launches;
   c->have_fwd = c->have_ckpt = c->have_loss = true;
   if (h_loss) return dos_read_loss(c, h_loss);
   return DOS_OK;
@@ -1096,8 +1124,9 @@ DOS_API int dos_layer_field(dos_ctx* c, int layer, float* d_v) {
   if (layer < 1 || layer > c->K) return fail(DOS_ERR_ARG, "layer must be in [1, n_layers]");
   if (!d_v) return fail(DOS_ERR_ARG, "d_v is NULL");
   const size_t n2 = (size_t)c->n * c->n;
-  DOS_CUDA(cudaMemcpyAsync(d_v, c->ckpt + (size_t)(layer - 1) * c->nw * n2, sizeof(float2) * c->nw * n2,
-                           cudaMemcpyDeviceToDevice, c->stream),
+  const bool table = layer == 1 && c->ckpt1_is_v1 && (c->path == DOS_PATH_MULTIPASS || c->path == DOS_PATH_MULTIPASS_BULK);
+  DOS_CUDA(cudaMemcpyAsync(d_v, table ? c->v1 : c->ckpt + (size_t)(layer - 1) * c->nw * n2,
+                           sizeof(float2) * c->nw * n2, cudaMemcpyDeviceToDevice, c->stream),
            "copy layer field");
   return DOS_OK;
 }

@@ -166,6 +166,33 @@ struct Pass {
     }
   }
 
+  // first layer from the create-time input field v1 = P_z0(aperture) (a.fin):
+  // u = t(h) v1 -> pad -> forward row DFT.  No inverse DFT, and no checkpoint:
+  // the table itself is the first layer's incoming field.
+  __device__ static void row_first(const PassArgs& a) {
+    const RowCtx rc = row_ctx(a);
+    const int t = rc.t;
+    const int w = blockIdx.y;
+    const int row = blockIdx.x * ROWL + rc.l;
+    const bool ok = row < a.n;
+    const int rr = ok ? row : 0;
+    const float2* vrow = a.fin + ((size_t)w * a.n + rr) * a.n;
+    const float* hrow = a.h + (size_t)rr * a.n;
+    const ChanConst cc = a.chan[w];
+    float2 r[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = t + T * i;
+      r[i] = x < a.n ? cmul(transmission(hrow[x], cc), vrow[x]) : czero();
+    }
+    LF::template fft<false>(r, t, rc.z, rc.tw);
+    if (ok) {
+      float2* srow = a.S + ((size_t)w * a.n + row) * M;
+#pragma unroll
+      for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+    }
+  }
+
   // output plane: IDFT of the FOV rows -> o (complex) and I = |o|^2
   __device__ static void row_out(const PassArgs& a) {
     const RowCtx rc = row_ctx(a);
@@ -336,6 +363,10 @@ __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>())
   Pass<LF>::template row_fwd<SAVE>(a);
 }
 template <class LF>
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>()) k_row_first(PassArgs a) {
+  Pass<LF>::row_first(a);
+}
+template <class LF>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_out(PassArgs a) {
   Pass<LF>::row_out(a);
 }
@@ -386,6 +417,9 @@ struct PassLaunch {
     const size_t sm = PS::row_smem_bytes(PS::ROWL);
     return save ? launch_k(k_row_fwd<LF, true>, g, RT, sm, a, s)
                 : launch_k(k_row_fwd<LF, false>, g, RT, sm, a, s);
+  }
+  static cudaError_t row_first(const PassArgs& a, cudaStream_t s) {
+    return launch_k(k_row_first<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
   }
   static cudaError_t row_out(const PassArgs& a, cudaStream_t s) {
     return launch_k(k_row_out<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);

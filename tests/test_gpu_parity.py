@@ -94,7 +94,8 @@ def test_forward_fields_and_intensity(name, path):
     for l in range(1, w.n_layers + 1):
         v = _np(st.layer_field(l)).astype(np.complex128)
         assert rel_l2(v, ref["v"][:, l - 1]) <= TOL_FIELD, l
-    assert st.last_launch_count == (2 * w.n_layers + 2 if path in MULTIPASS else 1)
+    # multi-pass: K row + K column passes and the output pass (gap 0 is the create-time input field)
+    assert st.last_launch_count == (2 * w.n_layers + 1 if path in MULTIPASS else 1)
     st.close()
 
 
@@ -396,4 +397,48 @@ def test_split_bf16_three_parts_meets_the_split_target(name, sub):
     assert rel_l2(g, g_ref) <= SPLIT_TARGET
     if name in ("tiny", "small"):
         assert e_field <= TOL_FIELD
+    st.close()
+
+
+@pytest.mark.parametrize("n,m,k", [(51, 128, 2), (300, 512, 1), (7, 16, 3)])
+def test_bulk_path_fallbacks_match_oracle(n, m, k):
+    """Shapes where the bulk-prefetch passes fall back: odd N (checkpoint rows
+    are not 16-byte multiples, the adjoint stages spectra instead), N > 256
+    (one TMA box holds at most 256 rows, the column pass runs the plain
+    kernel), and a single-tile M = 16."""
+    fov = n if n < 16 else (n // 2 if (n - n // 2) % 2 == 0 else n // 2 + 1)  # N - F even
+    w = custom(n, m, k, [480, 610, 720], 30, fov, name="bulk-fallback")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    st = _stack(w, path="multipass_bulk")
+    assert st.path == "multipass_bulk"
+    hd = _t(h)
+    st.forward(hd)
+    o = st.output_field()
+    _, _, dl = st.loss(_t(T))
+    g = _np(st.backward(hd, dl)).astype(np.float64)
+    L_ref, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    assert rel_l2(_np(o).astype(np.complex128), fwd["o"]) <= TOL_FIELD
+    assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
+    st.close()
+
+
+def test_forced_configuration_and_tuning_cache(tmp_path, monkeypatch):
+    """DOS_FORCE_CONFIG selects a named configuration without timing;
+    DOS_TUNE_CACHE stores the tuned choice and a second context reuses it."""
+    w = W.workload("batched")
+    monkeypatch.setenv("DOS_FORCE_CONFIG", "multipass:bulk")
+    st = _stack(w, path="auto")
+    assert st.path == "multipass_bulk" and "DOS_FORCE_CONFIG" in L.dos_describe(st.handle)
+    st.close()
+    monkeypatch.delenv("DOS_FORCE_CONFIG")
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("DOS_TUNE_CACHE", str(cache))
+    st = _stack(w, path="auto")
+    first = st.path
+    assert "tuned" in L.dos_describe(st.handle)
+    st.close()
+    assert cache.read_text().strip()
+    st = _stack(w, path="auto")
+    assert st.path == first and "tuning cache" in L.dos_describe(st.handle)
     st.close()
