@@ -391,7 +391,9 @@ int build(dos_ctx* x, const dos_config* c) {
   if (gemm) {
     dos::GemmPlan& g = x->gp;
     const size_t nwc = (size_t)g.nwc;
-    const size_t xsz = std::max({nwc * g.m * g.kp1, nwc * g.m * g.kp2, nwc * g.n * g.kp1, nwc * g.n * g.kp2});
+    // the data operand holds whole 256-row tiles (the GEMM reads them whole)
+    const size_t cm = (nwc * g.m + 255) / 256 * 256, cn = (nwc * g.n + 255) / 256 * 256;
+    const size_t xsz = std::max({cm * g.kp1, cm * g.kp2, cn * g.kp1, cn * g.kp2});
     const size_t dsz = std::max({(size_t)g.rp1 * nwc * g.m, (size_t)g.rp2 * nwc * g.m, (size_t)g.rp1 * nwc * g.n});
     g.F.k = g.G.k = g.X.k = g.parts;
     for (int q = 0; q < 3; ++q) g.F.p[q] = g.G.p[q] = g.X.p[q] = nullptr;

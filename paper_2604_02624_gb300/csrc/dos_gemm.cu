@@ -6,14 +6,16 @@
 // kernel, through L2); K is consumed in chunks of 64 bf16
 // staged in shared memory in the canonical K-major, non-swizzled core-matrix
 // layout (8 rows x 16 bytes per core matrix; 128 B between core matrices
-// along K, 1024 B between 8-row groups).  Operands arrive by cp.async
-// (16-byte asynchronous global -> shared copies, many in flight per thread)
-// through a GSTAGES-deep ring: while the tensor core works on chunk i (issued
-// by one thread, completion signalled to the stage's mbarrier by
-// tcgen05.commit), the copies of chunks i+1 .. i+GSTAGES-1 are in flight.  The
-// grid runs the CTAs of one column tile (which share its B operand) next to
-// each other.  Every wait is bounded: on expiry the kernel records an error
-// flag and finishes cleanly.
+// along K, 1024 B between 8-row groups).  Both operands are kept in global
+// memory in that order, tile by tile (gemm_tiled), so each stage arrives by
+// two 32 KB bulk copies (cp.async.bulk, completion counted in bytes on the
+// stage's "full" mbarrier) through a GSTAGES-deep ring: while the tensor core
+// works on chunk i (issued by one thread, completion signalled to the stage's
+// "empty" mbarrier by tcgen05.commit), the copies of chunks i+1 .. i+GSTAGES-1
+// are in flight.  The grid runs the CTAs of one column tile (which share its B
+// operand) next to each other.  Every wait is bounded: on expiry the kernel
+// records an error flag, lets its copies and MMAs in flight finish (bounded)
+// and ends cleanly.
 #include <cuda_bf16.h>
 
 #include "dos_gemm.cuh"
@@ -52,36 +54,46 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// 16-byte global -> shared copy; src_bytes 0 writes zeros (ragged column tiles)
-__device__ __forceinline__ void cp16(void* dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
-               : "memory");
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+// one contiguous global -> shared bulk copy, completion counted on `bar`
+__device__ __forceinline__ void bulk_tile(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 struct __align__(1024) GemmSmem {
-  uint8_t a[GSTAGES][GCM * GTK * 2];  // 32 KB per stage
+  uint8_t a[GSTAGES][GCM * GTK * 2];  // 32 KB per stage (one operand tile)
   uint8_t b[GSTAGES][GTN * GTK * 2];  // 32 KB per stage
-  uint64_t bar[GSTAGES];
+  uint64_t full[GSTAGES];             // copies of the stage landed
+  uint64_t empty[GSTAGES];            // MMAs reading the stage done
   uint32_t tmem;
 };
 
+// Operands are stored tile by tile (gemm_tiled): one 256-row x 64-K tile is
+// 32 KB, contiguous, already in the shared-memory order the MMAs read, so a
+// stage is two bulk copies issued by one thread.  Thread 0 also issues the
+// MMAs; the other warps wait at the block barrier and then drain the
+// accumulators.
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gsm_raw);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int m0 = blockIdx.x * GCM, n0 = blockIdx.y * GTN;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+  const int m0 = mt * GCM, n0 = nt * GTN;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
                  "r"(2 * GTN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < GSTAGES; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.bar[s])));
+    for (int s = 0; s < GSTAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.empty[s])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -90,42 +102,29 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   const uint32_t tmem = sm.tmem;
   const int kchunks = g.K / GTK;
   const int total = g.nseg * kchunks;
-  // copies of chunk `it` into its stage (every thread: 8 A and 16 B pieces of 16 bytes)
-  auto load = [&](int it) {
-    const int st = it % GSTAGES;
-    const int seg = it / kchunks;
-    const int k0 = (it % kchunks) * GTK;
-    const __nv_bfloat16* A = g.a[seg];
-    const __nv_bfloat16* B = g.b[seg];
-#pragma unroll
-    for (int q = 0; q < GCM * (GTK / 8) / kGemmThreads; ++q) {
-      const int c = tid + q * kGemmThreads;
-      const int r = c / (GTK / 8), kc = c % (GTK / 8);
-      cp16(sm.a[st] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16, A + (size_t)(m0 + r) * g.K + k0 + kc * 8, 16);
-    }
-#pragma unroll
-    for (int q = 0; q < GTN * (GTK / 8) / kGemmThreads; ++q) {
-      const int c = tid + q * kGemmThreads;
-      const int r = c / (GTK / 8), kc = c % (GTK / 8);
-      const bool in = n0 + r < g.cols;
-      cp16(sm.b[st] + ((r / 8) * (GTK / 8) + kc) * 128 + (r % 8) * 16,
-           B + (size_t)(in ? n0 + r : 0) * g.K + k0 + kc * 8, in ? 16u : 0u);
-    }
-  };
-  // prologue: chunks 0 .. GSTAGES-2 in flight (one commit group per chunk slot)
-#pragma unroll
-  for (int s = 0; s < GSTAGES - 1; ++s) {
-    if (s < total) load(s);
-    cp_commit();
-  }
+  constexpr uint32_t kTile = GCM * GTK * 2;  // bytes of one operand tile (A and B alike)
+  static_assert(GCM == GTN, "A and B tiles have the same shape");
   bool ok = true;
-  int issued = 0;  // chunks whose MMAs were committed
-  for (int it = 0; it < total; ++it) {
-    const int st = it % GSTAGES;
-    cp_wait<GSTAGES - 2>();  // this thread's copies of chunk `it` have landed
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();         // ... and everyone else's
-    if (tid == 0) {
+  if (tid == 0) {
+    int copied = 0;    // chunks whose copies were issued
+    int landed = 0;    // chunks whose copies were waited for
+    int committed = 0; // chunks whose MMAs were committed
+    auto issue = [&](int c) {
+      const int st = c % GSTAGES, seg = c / kchunks, kc = c % kchunks;
+      const uint32_t fb = smem_addr(&sm.full[st]);
+      bar_expect_tx(fb, 2 * kTile);
+      bulk_tile(sm.a[st], g.a[seg] + ((size_t)mt * kchunks + kc) * (kTile / 2), kTile, fb);
+      bulk_tile(sm.b[st], g.b[seg] + ((size_t)nt * kchunks + kc) * (kTile / 2), kTile, fb);
+      copied = c + 1;
+    };
+    for (int c = 0; c < GSTAGES - 1 && c < total; ++c) issue(c);
+    for (int it = 0; it < total && ok; ++it) {
+      const int st = it % GSTAGES;
+      if (!mbar_wait(smem_addr(&sm.full[st]), (uint32_t)((it / GSTAGES) & 1))) {
+        ok = false;
+        break;
+      }
+      landed = it + 1;
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t sa = smem_addr(sm.a[st]), sb = smem_addr(sm.b[st]);
 #pragma unroll
@@ -142,65 +141,63 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(&sm.bar[st])));
-    }
-    issued = it + 1;
-    // refill the stage of chunk it-1 with chunk it+GSTAGES-1 once its MMAs are done
-    const int nx = it + GSTAGES - 1;
-    if (nx < total) {
-      if (it >= 1 && !mbar_wait(smem_addr(&sm.bar[(it - 1) % GSTAGES]), (uint32_t)(((it - 1) / GSTAGES) & 1)))
-        ok = false;
-      if (!__syncthreads_and(ok)) {
-        ok = false;
-        break;
+          smem_addr(&sm.empty[st])));
+      committed = it + 1;
+      // refill the stage of chunk it-1 with chunk it+GSTAGES-1 once its MMAs are done
+      const int nx = it + GSTAGES - 1;
+      if (nx < total) {
+        if (it >= 1 && !mbar_wait(smem_addr(&sm.empty[(it - 1) % GSTAGES]), (uint32_t)(((it - 1) / GSTAGES) & 1))) {
+          ok = false;
+          break;
+        }
+        issue(nx);
       }
-      load(nx);
     }
-    cp_commit();
-  }
-  cp_wait<0>();  // no copy may still target shared memory when the CTA ends
-  // the last commit covers every MMA issued before it
-  if (ok && total > 0) {
-    const int last = total - 1;
-    if (!mbar_wait(smem_addr(&sm.bar[last % GSTAGES]), (uint32_t)((last / GSTAGES) & 1))) ok = false;
+    // the last commit covers every MMA issued before it
+    if (ok && committed > 0 &&
+        !mbar_wait(smem_addr(&sm.empty[(committed - 1) % GSTAGES]), (uint32_t)(((committed - 1) / GSTAGES) & 1)))
+      ok = false;
+    if (!ok) {
+      // a wait gave up: give the copies and MMAs in flight a bounded chance to
+      // finish before the shared and tensor memory they use is released
+      for (int c = landed; c < copied; ++c)
+        (void)mbar_wait(smem_addr(&sm.full[c % GSTAGES]), (uint32_t)((c / GSTAGES) & 1));
+      if (committed > 0)
+        (void)mbar_wait(smem_addr(&sm.empty[(committed - 1) % GSTAGES]), (uint32_t)(((committed - 1) / GSTAGES) & 1));
+      atomicExch(g.err, 1);
+    }
   }
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-   for (int h = 0; h < 2; ++h) {
-    const int row = m0 + h * GTM + warp * 32 + lane;
-    float* drow = g.D + (size_t)row * g.ldd;
-    for (int c0 = 0; c0 < GTN; c0 += 32) {
-      uint32_t r[32];
-      const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * GTN + c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(addr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      const int cb = n0 + c0;
-      if (cb + 32 <= g.cols && (g.ldd & 3) == 0) {
+    for (int h = 0; h < 2; ++h) {
+      const int row = m0 + h * GTM + warp * 32 + lane;
+      float* drow = g.D + (size_t)row * g.ldd;
+      for (int c0 = 0; c0 < GTN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * GTN + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        const int cb = n0 + c0;
+        if (cb + 32 <= g.cols && (g.ldd & 3) == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          *reinterpret_cast<float4*>(drow + cb + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                                  __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-      } else {
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<float4*>(drow + cb + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                                    __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+        } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (cb + j < g.cols) drow[cb + j] = __uint_as_float(r[j]);
+          for (int j = 0; j < 32; ++j)
+            if (cb + j < g.cols) drow[cb + j] = __uint_as_float(r[j]);
+        }
       }
     }
-   }
-  } else {
-    // give the MMAs still in flight a bounded chance to finish before the
-    // tensor memory they write is released
-    if (issued > 0)
-      (void)mbar_wait(smem_addr(&sm.bar[(issued - 1) % GSTAGES]), (uint32_t)(((issued - 1) / GSTAGES) & 1));
-    if (tid == 0) atomicExch(g.err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -240,6 +237,7 @@ __global__ void k_dft_matrix(Parts W, int rows_pad, int kpad, int nout, int kin,
   if (i >= (size_t)rows_pad * kpad) return;
   const int r = (int)(i / kpad), c = (int)(i % kpad);
   const int o = r / 2;
+  const size_t at = gemm_tiled((size_t)r, c, kpad);
   float v = 0.f;
   if (o < nout && c < 2 * kin) {
     const int x = c < kin ? c : c - kin;
@@ -250,7 +248,7 @@ __global__ void k_dft_matrix(Parts W, int rows_pad, int kpad, int nout, int kin,
     if ((r & 1) == 0) v = (float)(c < kin ? co : -s);
     else v = (float)(c < kin ? s : co);
   }
-  split_store(W, i, v);
+  split_store(W, at, v);
 }
 
 cudaError_t launch_build_dft(GemmPlan& p, cudaStream_t s) {
@@ -268,7 +266,6 @@ __global__ void k_prep_field(const float2* __restrict__ v, float2* __restrict__ 
                              int a_w) {
   const int wy = blockIdx.x;  // w * n + y
   const int w = wy / n, y = wy % n;
-  const size_t base = (size_t)wy * kp;
   for (int c = threadIdx.x; c < kp; c += blockDim.x) {
     float val = 0.f;
     if (c < 2 * n) {
@@ -288,7 +285,7 @@ __global__ void k_prep_field(const float2* __restrict__ v, float2* __restrict__ 
       }
       val = c < n ? u.x : u.y;
     }
-    split_store(X, base + c, val);
+    split_store(X, gemm_tiled((size_t)wy, c, kp), val);
   }
 }
 
@@ -296,14 +293,13 @@ __global__ void k_prep_field(const float2* __restrict__ v, float2* __restrict__ 
 __global__ void k_prep_rows(const float* __restrict__ D, size_t ldd, Parts X, int nk, int nj, int kp) {
   const int wk = blockIdx.x;  // w * nk + k
   const int w = wk / nk, k = wk % nk;
-  const size_t base = (size_t)wk * kp;
   const float* dre = D + (size_t)(2 * k) * ldd + (size_t)w * nj;
   const float* dim = dre + ldd;
   for (int c = threadIdx.x; c < kp; c += blockDim.x) {
     float val = 0.f;
     if (c < nj) val = dre[c];
     else if (c < 2 * nj) val = dim[c - nj];
-    split_store(X, base + c, val);
+    split_store(X, gemm_tiled((size_t)wk, c, kp), val);
   }
 }
 
@@ -333,9 +329,9 @@ __global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const f
     const int kx = kx0 + r, ky = ky0 + threadIdx.x;
     if (kx < m && ky < m) {
       const float2 val = tile[threadIdx.x][r];
-      const size_t base = ((size_t)w * m + kx) * kp;
-      split_store(X, base + ky, val.x);
-      split_store(X, base + m + ky, val.y);
+      const size_t row = (size_t)w * m + kx;
+      split_store(X, gemm_tiled(row, ky, kp), val.x);
+      split_store(X, gemm_tiled(row, m + ky, kp), val.y);
     }
   }
   // zero the K padding of the rows this block owns (once, by the ky0 == 0 blocks)
@@ -343,8 +339,8 @@ __global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const f
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
       const int kx = kx0 + r;
       if (kx >= m) continue;
-      const size_t base = ((size_t)w * m + kx) * kp;
-      for (int c = 2 * m + threadIdx.x; c < kp; c += 32) split_store(X, base + c, 0.f);
+      const size_t row = (size_t)w * m + kx;
+      for (int c = 2 * m + threadIdx.x; c < kp; c += 32) split_store(X, gemm_tiled(row, c, kp), 0.f);
     }
   }
 }

@@ -26,9 +26,20 @@
 
 namespace dos {
 
+// Element (row, k) of an operand with kp (a multiple of 64) columns of K in
+// the tiled order the GEMM reads: tiles of 256 rows x 64 K, 32 KB each,
+// row-tile major; inside a tile the tensor core's K-major core-matrix order
+// (8 rows x 8 K = 128 bytes per core matrix, 8 core matrices along K, then
+// the next 8 rows).
+__host__ __device__ inline size_t gemm_tiled(size_t row, int k, int kp) {
+  return ((((row >> 8) * (size_t)(kp >> 6)) + (size_t)(k >> 6)) << 14) +
+         ((size_t)((((int)(row & 255) >> 3) << 3) + ((k & 63) >> 3)) << 6) + ((row & 7) << 3) + (size_t)(k & 7);
+}
+
 // One GEMM D[rows][cols] (f32, row-major, leading dimension ldd) =
-//   sum over segments s of A_s[rows][K] * B_s[cols][K]^T, A_s / B_s bf16 K-major.
-// rows % 256 == 0, K % 64 == 0; cols may be ragged (tile of 256).
+//   sum over segments s of A_s[rows][K] * B_s[cols][K]^T, A_s / B_s bf16 in
+//   the tiled order above.  rows % 256 == 0, K % 64 == 0; cols may be ragged
+//   (B must then hold whole 256-row tiles; rows past cols are never stored).
 constexpr int kMaxGemmTerms = 6;
 struct GemmArgs {
   const __nv_bfloat16* a[kMaxGemmTerms];
