@@ -394,15 +394,14 @@ int build(dos_ctx* x, const dos_config* c) {
     // the data operand holds whole 256-row tiles (the GEMM reads them whole)
     const size_t cm = (nwc * g.m + 255) / 256 * 256, cn = (nwc * g.n + 255) / 256 * 256;
     const size_t xsz = std::max({cm * g.kp1, cm * g.kp2, cn * g.kp1, cn * g.kp2});
-    const size_t dsz = std::max({(size_t)g.rp1 * nwc * g.m, (size_t)g.rp2 * nwc * g.m, (size_t)g.rp1 * nwc * g.n});
-    g.F.k = g.G.k = g.X.k = g.parts;
-    for (int q = 0; q < 3; ++q) g.F.p[q] = g.G.p[q] = g.X.p[q] = nullptr;
+    g.F.k = g.G.k = g.X.k = g.Y.k = g.parts;
+    for (int q = 0; q < 3; ++q) g.F.p[q] = g.G.p[q] = g.X.p[q] = g.Y.p[q] = nullptr;
     for (int q = 0; q < g.parts; ++q) {
       if ((rc = x->alloc(&g.F.p[q], (size_t)g.rp1 * g.kp1, "DFT matrix"))) return rc;
       if ((rc = x->alloc(&g.G.p[q], (size_t)g.rp2 * g.kp2, "IDFT matrix"))) return rc;
       if ((rc = x->alloc(&g.X.p[q], xsz, "GEMM operand"))) return rc;
+      if ((rc = x->alloc(&g.Y.p[q], xsz, "GEMM operand"))) return rc;
     }
-    if ((rc = x->alloc(&g.D, dsz, "GEMM output"))) return rc;
     if ((rc = x->alloc(&g.fld, nwc * n2, "GEMM field"))) return rc;
   }
   if ((rc = x->alloc(&x->d_err, 1, "error flag"))) return rc;
@@ -506,14 +505,16 @@ int gemm_forward(dos_ctx* c, const float* d_h, float* d_I) {
       DOS_TIMED(c, DOS_KERNEL_GEMM_PROPAGATION,
                 dos::gemm_propagate(g, nc, c->hq_slot(gap) + (size_t)w0 * hs2, c->hs, false,
                                     last ? c->o + (size_t)w0 * f2 : nullptr,
-                                    (last && d_I) ? d_I + (size_t)w0 * f2 : nullptr, c->of, c->fov, mg, c->stream),
+                                    (last && d_I) ? d_I + (size_t)w0 * f2 : nullptr, c->of, c->fov, mg, &c->launches,
+                                    c->stream),
                 "GEMM propagation");
-      if (!last)
+      if (!last) {
         DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
                   dos::gemm_prep_field(g, nc, g.fld, c->ckpt + ((size_t)gap * c->nw + w0) * n2, d_h + (size_t)gap * n2,
                                        c->chan + w0, 1, 0, 0, c->stream),
                   "GEMM layer modulation");
-      c->launches += last ? 9 : 10;
+        ++c->launches;
+      }
     }
     c->launches += 1;
   }
@@ -538,14 +539,14 @@ int gemm_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dL
       if (mg.sq) mg.sq += (size_t)w0 * hs2;
       DOS_TIMED(c, DOS_KERNEL_GEMM_PROPAGATION,
                 dos::gemm_propagate(g, nc, c->hq_slot(l) + (size_t)w0 * hs2, c->hs, true, nullptr, nullptr, c->of,
-                                    c->fov, mg, c->stream),
+                                    c->fov, mg, &c->launches, c->stream),
                 "GEMM adjoint propagation");
       DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
                 dos::gemm_adj_layer(g, nc, c->ckpt + ((size_t)(l - 1) * c->nw + w0) * n2, n2,
                                     d_h + (size_t)(l - 1) * n2, c->chan + w0,
                                     c->partial + ((size_t)chunk * c->K + (l - 1)) * n2, c->stream),
                 "GEMM adjoint layer");
-      c->launches += 10;
+      c->launches += 1;
       if (l > 1) {
         DOS_TIMED(c, DOS_KERNEL_GEMM_FIELD,
                   dos::gemm_prep_field(g, nc, g.fld, nullptr, nullptr, nullptr, 0, 0, 0, c->stream), "GEMM field");

@@ -18,6 +18,8 @@
 // and ends cleanly.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "dos_gemm.cuh"
 #include "dos_internal.h"
 #include "dos_pass.cuh"
@@ -27,7 +29,8 @@ namespace dos {
 constexpr int GTM = 128, GTN = 256, GTK = 64;  // one MMA: 128 x 256 x 16 per K step
 constexpr int GCM = 2 * GTM;                    // rows per CTA
 constexpr int GSTAGES = 3;
-constexpr int kGemmThreads = 128;
+constexpr int kGemmThreads = 512;  // 16 warps: the epilogue splits the columns in four, by w / 4
+constexpr int kColSplit = kGemmThreads / 128;
 constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier wait (a fraction of a second)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -73,16 +76,130 @@ struct __align__(1024) GemmSmem {
   uint32_t tmem;
 };
 
+// ------------------------------------------------------------ epilogues
+// x -> bf16 parts: each the round-to-nearest of what the earlier parts leave
+__device__ __forceinline__ void split_store(const Parts& P, size_t i, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  P.p[0][i] = h;
+  const float r1 = v - __bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  P.p[1][i] = m;
+  if (P.k > 2) P.p[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// x -> bf16 parts of 8 consecutive K entries (8-aligned) of one operand row:
+// one 16-byte store per part
+__device__ __forceinline__ void split_store8(const Parts& P, size_t at, const float* x) {
+  uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float v = x[2 * e + q];
+      h[q] = __float2bfloat16_rn(v);
+      const float r1 = v - __bfloat162float(h[q]);
+      m[q] = __float2bfloat16_rn(r1);
+      l[q] = __float2bfloat16_rn(r1 - __bfloat162float(m[q]));
+    }
+    w0[e] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+    w1[e] = (uint32_t)__bfloat16_as_ushort(m[0]) | ((uint32_t)__bfloat16_as_ushort(m[1]) << 16);
+    w2[e] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+  }
+  *reinterpret_cast<uint4*>(P.p[0] + at) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  *reinterpret_cast<uint4*>(P.p[1] + at) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  if (P.k > 2) *reinterpret_cast<uint4*>(P.p[2] + at) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+// accumulator row r, columns cb .. cb+31 (values v) -> the destination of MODE
+template <int MODE>
+__device__ __forceinline__ void epilogue(const GemmArgs& g, int r, int cb, const float* v) {
+  if constexpr (MODE == GEMM_OUT_ROWS) {
+    const int k = r >> 1, p = r & 1;
+    if (g.nj % 8 == 0) {
+      // 8-aligned groups never straddle a channel: one 16-byte store per part
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = cb + 8 * q;
+        if (c >= g.vcols) break;
+        const int w = c / g.nj, j = c - w * g.nj;
+        split_store8(g.xo, gemm_tiled((size_t)w * g.nk + k, p * g.nj + j, g.kpo), v + 8 * q);
+      }
+    } else {
+      for (int q = 0; q < 32; ++q) {
+        const int c = cb + q;
+        if (c >= g.vcols) break;
+        const int w = c / g.nj, j = c - w * g.nj;
+        split_store(g.xo, gemm_tiled((size_t)w * g.nk + k, p * g.nj + j, g.kpo), v[q]);
+      }
+    }
+  } else if constexpr (MODE == GEMM_OUT_SPECTRUM) {
+    // row r = (w, kx); columns 2ky + {0, 1}: sixteen spectrum values
+    const int m = g.m, w = r / m, kx = r - w * m;
+    const int bx = min(kx, m - kx);
+    const float2* Hw = g.Hq + (size_t)w * g.hs * g.hs;
+    const float* Sw = g.mis.sq ? g.mis.sq + (size_t)w * g.hs * g.hs : nullptr;
+    const int ky0 = cb >> 1;  // multiple of 16
+    if (ky0 >= m) return;
+    float re[16], im[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int ky = ky0 + q;
+      float2 val = make_float2(0.f, 0.f);
+      if (ky < m) {
+        const size_t qi = (size_t)min(ky, m - ky) * g.hs + bx;
+        float2 hv = Hw[qi];
+        if (Sw) hv = cmul(hv, misalign_factor(g.mis, ky, kx, m, Sw[qi]));
+        const float2 b = make_float2(v[2 * q], v[2 * q + 1]);
+        val = g.adj ? cmulc(b, hv) : cmul(b, hv);
+      }
+      re[q] = val.x;
+      im[q] = val.y;
+    }
+    // m is a multiple of 8 for every compiled size: whole groups of 8
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (ky0 + 8 * q >= m) break;
+      split_store8(g.xo, gemm_tiled((size_t)r, ky0 + 8 * q, g.kpo), re + 8 * q);
+      split_store8(g.xo, gemm_tiled((size_t)r, m + ky0 + 8 * q, g.kpo), im + 8 * q);
+    }
+  } else {
+    // row r = (w, y); columns 2x + {0, 1}: sixteen field values
+    const int n = g.n, w = r / n, y = r - w * n;
+    const int x0 = cb >> 1;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int x = x0 + q;
+      if (x >= n) break;
+      const float2 val = make_float2(v[2 * q], v[2 * q + 1]);
+      if (g.o) {
+        const int fy = y - g.of, fx = x - g.of;
+        if (fy >= 0 && fy < g.fov && fx >= 0 && fx < g.fov) {
+          const size_t qo = ((size_t)w * g.fov + fy) * g.fov + fx;
+          g.o[qo] = val;
+          if (g.I) g.I[qo] = fmaf(val.x, val.x, val.y * val.y);
+        }
+      } else {
+        g.fld[((size_t)w * n + y) * n + x] = val;
+      }
+    }
+  }
+}
+
 // Operands are stored tile by tile (gemm_tiled): one 256-row x 64-K tile is
 // 32 KB, contiguous, already in the shared-memory order the MMAs read, so a
 // stage is two bulk copies issued by one thread.  Thread 0 also issues the
 // MMAs; the other warps wait at the block barrier and then drain the
-// accumulators.
-__global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
+// accumulators through the epilogue of MODE.
+template <int MODE>
+__global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gsm_raw);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int mt = blockIdx.x, nt = blockIdx.y;
+  // the CTAs that share an operand tile of the data run together: the DFT
+  // matrix's (few) tiles are the fast grid dimension
+  const int mt = g.w_is_b ? blockIdx.y : blockIdx.x;
+  const int nt = g.w_is_b ? blockIdx.x : blockIdx.y;
   const int m0 = mt * GCM, n0 = nt * GTN;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
@@ -171,31 +288,27 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     for (int h = 0; h < 2; ++h) {
-      const int row = m0 + h * GTM + warp * 32 + lane;
-      float* drow = g.D + (size_t)row * g.ldd;
-      for (int c0 = 0; c0 < GTN; c0 += 32) {
-        uint32_t r[32];
-        const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * GTN + c0);
+      // warp w reads TMEM lanes 32 (w % 4) .. +31 (its lane quarter) and the
+      // columns of part w / 4
+      const int r = m0 + h * GTM + (warp & 3) * 32 + lane;  // accumulator row of this thread
+      constexpr int kCols = GTN / kColSplit;
+      for (int c0 = (warp >> 2) * kCols; c0 < ((warp >> 2) + 1) * kCols; c0 += 32) {
+        uint32_t u[32];
+        const uint32_t addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * GTN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+              "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+              "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
+              "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
             : "r"(addr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const int cb = n0 + c0;
-        if (cb + 32 <= g.cols && (g.ldd & 3) == 0) {
+        if (r >= g.vrows) continue;
+        float v[32];
 #pragma unroll
-          for (int j = 0; j < 32; j += 4)
-            *reinterpret_cast<float4*>(drow + cb + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                                    __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (cb + j < g.cols) drow[cb + j] = __uint_as_float(r[j]);
-        }
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
+        epilogue<MODE>(g, r, n0 + c0, v);
       }
     }
   }
@@ -204,30 +317,30 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(GemmArgs g) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * GTN));
 }
 
-cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s) {
+template <int MODE>
+static cudaError_t launch_mode(const GemmArgs& g, cudaStream_t s) {
   const size_t sm = sizeof(GemmSmem) + 1024;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // row tiles fastest: the CTAs of one column tile (same B operand) run together
-  const dim3 grid(g.rows / GCM, (g.cols + GTN - 1) / GTN);
-  k_tc_gemm<<<grid, kGemmThreads, sm, s>>>(g);
+  const int ta = g.rows / GCM, tb = (g.cols + GTN - 1) / GTN;
+  const dim3 grid = g.w_is_b ? dim3(tb, ta) : dim3(ta, tb);
+  k_tc_gemm<MODE><<<grid, kGemmThreads, sm, s>>>(g);
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------ constant matrices
-// x -> bf16 parts: each the round-to-nearest of what the earlier parts leave
-__device__ __forceinline__ void split_store(const Parts& P, size_t i, float v) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  P.p[0][i] = h;
-  const float r1 = v - __bfloat162float(h);
-  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-  P.p[1][i] = m;
-  if (P.k > 2) P.p[2][i] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s) {
+  switch (g.mode) {
+    case GEMM_OUT_ROWS: return launch_mode<GEMM_OUT_ROWS>(g, s);
+    case GEMM_OUT_SPECTRUM: return launch_mode<GEMM_OUT_SPECTRUM>(g, s);
+    default: return launch_mode<GEMM_OUT_FIELD>(g, s);
+  }
 }
+
+// ------------------------------------------------------------ constant matrices
 
 // W rows r: output o = r / 2 (re for even r, im for odd r); K index c: input
 // element c (its real part) for c < kin, input c - kin (imaginary part) for
@@ -289,94 +402,17 @@ __global__ void k_prep_field(const float2* __restrict__ v, float2* __restrict__ 
   }
 }
 
-// D (rows 2k+{0,1}, cols (w, j) of width nj) -> X rows (w, k): [Re over j, Im over j, 0 ...]
-__global__ void k_prep_rows(const float* __restrict__ D, size_t ldd, Parts X, int nk, int nj, int kp) {
-  const int wk = blockIdx.x;  // w * nk + k
-  const int w = wk / nk, k = wk % nk;
-  const float* dre = D + (size_t)(2 * k) * ldd + (size_t)w * nj;
-  const float* dim = dre + ldd;
-  for (int c = threadIdx.x; c < kp; c += blockDim.x) {
-    float val = 0.f;
-    if (c < nj) val = dre[c];
-    else if (c < 2 * nj) val = dim[c - nj];
-    split_store(X, gemm_tiled((size_t)wk, c, kp), val);
-  }
-}
-
-// D (rows 2ky+{0,1}, cols (w, kx) of width m) times H_w(|ky|,|kx|) (conj if adj)
-// -> X rows (w, kx): [Re over ky, Im over ky, 0 ...] (32 x 32 transpose in smem)
-__global__ void k_prep_spectrum(const float* __restrict__ D, size_t ldd, const float2* __restrict__ Hq, int hs,
-                                Parts X, int m, int kp, int adj, Misalign mis) {
-  __shared__ float2 tile[32][33];
-  const int w = blockIdx.z;
-  const int ky0 = blockIdx.y * 32, kx0 = blockIdx.x * 32;
-  const float2* Hw = Hq + (size_t)w * hs * hs;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int ky = ky0 + r, kx = kx0 + threadIdx.x;
-    float2 val = make_float2(0.f, 0.f);
-    if (ky < m && kx < m) {
-      const size_t col = (size_t)w * m + kx;
-      const float2 b = make_float2(D[(size_t)(2 * ky) * ldd + col], D[(size_t)(2 * ky + 1) * ldd + col]);
-      const size_t qi = (size_t)min(ky, m - ky) * hs + min(kx, m - kx);
-      float2 hv = Hw[qi];
-      if (mis.sq) hv = cmul(hv, misalign_factor(mis, ky, kx, m, mis.sq[(size_t)w * hs * hs + qi]));
-      val = adj ? cmulc(b, hv) : cmul(b, hv);
-    }
-    tile[r][threadIdx.x] = val;
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int kx = kx0 + r, ky = ky0 + threadIdx.x;
-    if (kx < m && ky < m) {
-      const float2 val = tile[threadIdx.x][r];
-      const size_t row = (size_t)w * m + kx;
-      split_store(X, gemm_tiled(row, ky, kp), val.x);
-      split_store(X, gemm_tiled(row, m + ky, kp), val.y);
-    }
-  }
-  // zero the K padding of the rows this block owns (once, by the ky0 == 0 blocks)
-  if (blockIdx.y == 0) {
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-      const int kx = kx0 + r;
-      if (kx >= m) continue;
-      const size_t row = (size_t)w * m + kx;
-      for (int c = 2 * m + threadIdx.x; c < kp; c += 32) split_store(X, gemm_tiled(row, c, kp), 0.f);
-    }
-  }
-}
-
-// D (rows 2x+{0,1}, cols (w, y)) -> field[w][y][x] (32 x 32 transpose); when o
-// is given, only the FOV is written, to o and I.
-__global__ void k_prep_out(const float* __restrict__ D, size_t ldd, float2* __restrict__ field, float2* __restrict__ o,
-                           float* __restrict__ I, int n, int of, int fov) {
-  __shared__ float2 tile[32][33];
-  const int w = blockIdx.z;
-  const int x0 = blockIdx.y * 32, y0 = blockIdx.x * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int x = x0 + r, y = y0 + threadIdx.x;
-    float2 val = make_float2(0.f, 0.f);
-    if (x < n && y < n) {
-      const size_t col = (size_t)w * n + y;
-      val = make_float2(D[(size_t)(2 * x) * ldd + col], D[(size_t)(2 * x + 1) * ldd + col]);
-    }
-    tile[r][threadIdx.x] = val;
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int y = y0 + r, x = x0 + threadIdx.x;
-    if (x >= n || y >= n) continue;
-    const float2 val = tile[threadIdx.x][r];
-    if (o) {
-      const int fy = y - of, fx = x - of;
-      if (fy >= 0 && fy < fov && fx >= 0 && fx < fov) {
-        const size_t q = ((size_t)w * fov + fy) * fov + fx;
-        o[q] = val;
-        if (I) I[q] = fmaf(val.x, val.x, val.y * val.y);
-      }
-    } else {
-      field[((size_t)w * n + y) * n + x] = val;
-    }
-  }
+// zero the K entries [k_from, kp) of operand rows [0, rows) (the padding of
+// K past the data, which the epilogues do not write)
+__global__ void k_zero_kpad(Parts X, size_t rows, int k_from, int kp) {
+  const int wk = kp - k_from;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * (size_t)wk) return;
+  const size_t r = i / wk;
+  const int k = k_from + (int)(i % wk);
+  const size_t at = gemm_tiled(r, k, kp);
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  for (int q = 0; q < X.k; ++q) X.p[q][at] = z;
 }
 
 // adjoint seed on the FOV: 2 dL/dI o, zero elsewhere
@@ -417,53 +453,74 @@ __global__ void k_field_adj(float2* __restrict__ field, const float2* __restrict
 }
 
 // ------------------------------------------------------------ one propagation
-struct GemmProp {
-  GemmPlan* p;
-  cudaStream_t s;
-  // D = W X^T over the kept products of the parts: (0,0), (0,1), (1,0) and,
-  // with three parts, (0,2), (2,0), (1,1).  The tensor core's FP32 accumulation
-  // loses a little of every partial sum (measured: the relative error grows with
-  // the number of accumulation steps at the accumulator's magnitude), so the
-  // small products go first and the large (0,0) product last: the error is then
-  // that of the (0,0) product alone.
-  cudaError_t gemm(const Parts& W, int rows, int K, int cols) {
-    static const int ta2[3] = {0, 1, 0}, tb2[3] = {1, 0, 0};
-    static const int ta3[6] = {1, 0, 2, 0, 1, 0}, tb3[6] = {1, 2, 0, 1, 0, 0};
-    GemmArgs g;
-    g.nseg = p->parts == 3 ? 6 : 3;
-    for (int t = 0; t < g.nseg; ++t) {
-      g.a[t] = W.p[p->parts == 3 ? ta3[t] : ta2[t]];
-      g.b[t] = p->X.p[p->parts == 3 ? tb3[t] : tb2[t]];
-    }
-    g.rows = rows;
-    g.cols = cols;
-    g.K = K;
-    g.D = p->D;
-    g.ldd = (size_t)cols;
-    g.err = p->err;
-    return launch_tc_gemm(g, s);
+// The kept products of the parts: (0,0), (0,1), (1,0) and, with three parts,
+// (0,2), (2,0), (1,1).  The tensor core's FP32 accumulation loses a little of
+// every partial sum (measured: the relative error grows with the number of
+// accumulation steps at the accumulator's magnitude), so the small products go
+// first and the large (0,0) product last: the error is then that of the (0,0)
+// product alone.
+static void set_terms(GemmArgs& g, const Parts& A, const Parts& B) {
+  static const int ta2[3] = {0, 1, 0}, tb2[3] = {1, 0, 0};
+  static const int ta3[6] = {1, 0, 2, 0, 1, 0}, tb3[6] = {1, 2, 0, 1, 0, 0};
+  const bool three = A.k == 3;
+  g.nseg = three ? 6 : 3;
+  for (int t = 0; t < g.nseg; ++t) {
+    g.a[t] = A.p[three ? ta3[t] : ta2[t]];
+    g.b[t] = B.p[three ? tb3[t] : tb2[t]];
   }
-};
+}
+
+static cudaError_t zero_kpad(const Parts& X, size_t rows, int k_from, int kp, int* launches, cudaStream_t s) {
+  if (k_from >= kp) return cudaSuccess;
+  const size_t total = rows * (size_t)(kp - k_from);
+  k_zero_kpad<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, rows, k_from, kp);
+  ++*launches;
+  return cudaGetLastError();
+}
 
 // X rows (w, y) of the chunk hold the field; computes the propagated field
-// (into fld) or, with o non-null, the output plane.
+// (into fld) or, with o non-null, the output plane.  Operands alternate
+// between the X and Y buffers: X1 (field) -> Y (after the row DFT) -> X (after
+// the column DFT and H) -> Y (after the column IDFT) -> field.
 cudaError_t gemm_propagate(GemmPlan& p, int nwc, const float2* Hq, int hs, bool adj, float2* o, float* I, int of,
-                           int fov, const Misalign& mis, cudaStream_t s) {
-  GemmProp g{&p, s};
+                           int fov, const Misalign& mis, int* launches, cudaStream_t s) {
   const int n = p.n, m = p.m;
-  cudaError_t e;
+  auto pad256 = [](int v) { return (v + 255) / 256 * 256; };
   const int c1 = nwc * n, c2 = nwc * m;
-  if ((e = g.gemm(p.F, p.rp1, p.kp1, c1)) != cudaSuccess) return e;        // row DFT
-  k_prep_rows<<<nwc * m, 128, 0, s>>>(p.D, (size_t)c1, p.X, m, n, p.kp1);
-  if ((e = g.gemm(p.F, p.rp1, p.kp1, c2)) != cudaSuccess) return e;        // column DFT
-  k_prep_spectrum<<<dim3((m + 31) / 32, (m + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c2, Hq, hs, p.X, m,
-                                                                                  p.kp2, adj ? 1 : 0, mis);
-  if ((e = g.gemm(p.G, p.rp2, p.kp2, c2)) != cudaSuccess) return e;        // column IDFT
-  k_prep_rows<<<nwc * n, 128, 0, s>>>(p.D, (size_t)c2, p.X, n, m, p.kp2);
-  if ((e = g.gemm(p.G, p.rp2, p.kp2, c1)) != cudaSuccess) return e;        // row IDFT
-  k_prep_out<<<dim3((n + 31) / 32, (n + 31) / 32, nwc), dim3(32, 8), 0, s>>>(p.D, (size_t)c1, p.fld, o, I, n, of,
-                                                                             fov);
-  return cudaGetLastError();
+  cudaError_t e;
+  GemmArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.err = p.err;
+  // row DFT: D = F X1^T -> Y rows (w, kx), K = p n + y
+  if ((e = zero_kpad(p.Y, (size_t)pad256(c2), 2 * n, p.kp1, launches, s)) != cudaSuccess) return e;
+  set_terms(g, p.F, p.X);
+  g.rows = p.rp1; g.cols = c1; g.K = p.kp1; g.w_is_b = 0;
+  g.mode = GEMM_OUT_ROWS; g.vrows = 2 * m; g.vcols = c1; g.nk = m; g.nj = n; g.xo = p.Y; g.kpo = p.kp1;
+  if ((e = launch_tc_gemm(g, s)) != cudaSuccess) return e;
+  ++*launches;
+  // column DFT and H: D = Y F^T -> X rows (w, kx), K = ky | m + ky
+  if ((e = zero_kpad(p.X, (size_t)pad256(c2), 2 * m, p.kp2, launches, s)) != cudaSuccess) return e;
+  set_terms(g, p.Y, p.F);
+  g.rows = pad256(c2); g.cols = 2 * m; g.K = p.kp1; g.w_is_b = 1;
+  g.mode = GEMM_OUT_SPECTRUM; g.vrows = c2; g.vcols = 2 * m; g.xo = p.X; g.kpo = p.kp2;
+  g.Hq = Hq; g.hs = hs; g.m = m; g.adj = adj ? 1 : 0; g.mis = mis;
+  if ((e = launch_tc_gemm(g, s)) != cudaSuccess) return e;
+  ++*launches;
+  // column IDFT: D = G X^T -> Y rows (w, y), K = p m + kx
+  if ((e = zero_kpad(p.Y, (size_t)pad256(c1), 2 * m, p.kp2, launches, s)) != cudaSuccess) return e;
+  set_terms(g, p.G, p.X);
+  g.rows = p.rp2; g.cols = c2; g.K = p.kp2; g.w_is_b = 0;
+  g.mode = GEMM_OUT_ROWS; g.vrows = 2 * n; g.vcols = c2; g.nk = n; g.nj = m; g.xo = p.Y; g.kpo = p.kp2;
+  if ((e = launch_tc_gemm(g, s)) != cudaSuccess) return e;
+  ++*launches;
+  // row IDFT: D = Y G^T -> field (or the output plane)
+  set_terms(g, p.Y, p.G);
+  g.rows = pad256(c1); g.cols = 2 * n; g.K = p.kp2; g.w_is_b = 1;
+  g.mode = GEMM_OUT_FIELD; g.vrows = c1; g.vcols = 2 * n; g.fld = p.fld; g.o = o; g.I = I; g.n = n; g.of = of;
+  g.fov = fov;
+  if ((e = launch_tc_gemm(g, s)) != cudaSuccess) return e;
+  ++*launches;
+  return cudaSuccess;
 }
 
 cudaError_t gemm_prep_field(GemmPlan& p, int nwc, const float2* v, float2* ckpt, const float* h,
