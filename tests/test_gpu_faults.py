@@ -54,3 +54,42 @@ def test_expired_bulk_wait_is_reported_and_context_recovers(monkeypatch):
     assert rel_l2(I, fwd["I"]) <= TOL_INTENSITY
     assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref)
     st.close()
+
+
+def test_out_of_memory_is_reported_and_nothing_leaks():
+    """A design whose checkpoints cannot fit (64 layers of 256 x 256 for 16384
+    channels: 550 GB, after 26 GB of tables and spectra were allocated) fails in
+    dos_create with DOS_ERR_OOM and a message; the device memory in use
+    afterwards is what it was before."""
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    lam = np.linspace(450e-9, 750e-9, 16384)
+    with pytest.raises(L.DosError) as e:
+        DiffractiveStack(n=256, m=512, n_layers=64, lambdas=lam, gaps=np.full(65, 1e-4), pitch=3e-7,
+                         n_index=1.7, fov=64, path="multipass", device=DEV)
+    assert e.value.code == L.DOS_ERR_OOM
+    assert "cudaMalloc" in str(e.value)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert abs(free1 - free0) < 64 << 20
+    # the library is still usable
+    w = W.workload("tiny")
+    st = DiffractiveStack.from_workload(w, device=DEV, path="multipass")
+    st.forward(torch.tensor(W.thickness(w, 0), dtype=torch.float32, device=DEV))
+    st.close()
+
+
+def test_non_finite_thickness_propagates_without_a_fault():
+    """A NaN thickness pixel gives non-finite outputs (the caller's check finds
+    them); no kernel traps and the context stays usable."""
+    w = W.workload("tiny")
+    h = W.thickness(w, 0).copy()
+    st = DiffractiveStack.from_workload(w, device=DEV, path="multipass")
+    hb = h.copy()
+    hb[0, w.n // 2, w.n // 2] = np.nan
+    I = st.forward(torch.tensor(hb, dtype=torch.float32, device=DEV))
+    torch.cuda.synchronize()
+    assert not torch.isfinite(I).all()
+    I2 = st.forward(torch.tensor(h, dtype=torch.float32, device=DEV)).cpu().numpy().astype(np.float64)
+    ref = O.forward(h, keep_fields=False, **oracle_model(w))["I"]
+    assert rel_l2(I2, ref) <= TOL_INTENSITY
+    st.close()
