@@ -1,23 +1,23 @@
 // dos_gemm.cu - split-BF16 DFT-GEMM form of the propagation (tcgen05, TMEM).
 //
-// See dos_gemm.cuh for the formulation.  The GEMM kernel: one CTA computes a
-// 256 x 256 FP32 tile in tensor memory (two 128-row MMAs sharing each B
-// chunk, all 512 TMEM columns: operand bytes per FLOP are what bound the
-// kernel, through L2); K is consumed in chunks of 64 bf16
-// staged in shared memory in the canonical K-major, non-swizzled core-matrix
-// layout (8 rows x 16 bytes per core matrix; 128 B between core matrices
-// along K, 1024 B between 8-row groups).  Both operands are kept in global
-// memory in that order, tile by tile (gemm_tiled), so each stage arrives by
-// two 32 KB bulk copies (cp.async.bulk, completion counted in bytes on the
-// stage's "full" mbarrier) through a GSTAGES-deep ring: while the tensor core
-// works on chunk i (issued by one thread, completion signalled to the stage's
-// "empty" mbarrier by tcgen05.commit), the copies of chunks i+1 .. i+GSTAGES-1
-// are in flight.  The grid runs the CTAs of one column tile (which share its B
-// operand) next to each other.  Every wait is bounded: on expiry the kernel
-// records an error flag, lets its copies and MMAs in flight finish (bounded)
-// and ends cleanly.
+// See dos_gemm.cuh for the formulation.  The GEMM kernel is persistent and
+// warp-specialised: one CTA per SM walks its share of the 128 x 256 output
+// tiles.  Warp 0 (one lane) streams the operands: both are kept in global
+// memory tile by tile in the tensor core's K-major core-matrix order
+// (gemm_tiled), so a K chunk of 64 is two bulk copies (16 KB of A, 32 KB of B,
+// cp.async.bulk with completion counted in bytes on the stage's "full"
+// mbarrier) into a GSTAGES-deep ring.  Warp 1 (one lane) issues the MMAs into
+// one of two TMEM accumulators (2 x 256 columns) and frees each stage through
+// tcgen05.commit on its "empty" mbarrier; a commit on "acc_full" hands a
+// finished accumulator to the sixteen epilogue warps, which drain it (warp w
+// reads TMEM lanes 32 (w % 4) .. +31 and a quarter of the columns) while the
+// MMAs of the next tile run into the other accumulator, and release it on
+// "acc_empty".  Every wait is bounded and watches a shared abort flag: on
+// expiry the CTA records the error flag, lets its copies and MMAs in flight
+// finish (bounded) and ends cleanly.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "dos_gemm.cuh"
@@ -26,12 +26,11 @@
 
 namespace dos {
 
-constexpr int GTM = 128, GTN = 256, GTK = 64;  // one MMA: 128 x 256 x 16 per K step
-constexpr int GCM = 2 * GTM;                    // rows per CTA
-constexpr int GSTAGES = 3;
-constexpr int kGemmThreads = 512;  // 16 warps: the epilogue splits the columns in four, by w / 4
-constexpr int kColSplit = kGemmThreads / 128;
-constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier wait (a fraction of a second)
+constexpr int GTM = 128, GTN = 256, GTK = 64;  // one tile and MMA: 128 x 256, K steps of 16
+constexpr int GSTAGES = 4;                      // 48 KB per stage
+constexpr int kEpiWarps = 16;                   // 4 per TMEM lane quarter, a quarter of the columns each
+constexpr int kGemmThreads = 32 * (2 + kEpiWarps);
+constexpr long kSpinLimit = 1L << 26;           // bounded mbarrier wait (a fraction of a second)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -45,16 +44,24 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) {
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GTN >> 3) << 17) |
                             ((uint32_t)(GTM >> 4) << 24);
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (long it = 0; it < kSpinLimit && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  }
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
   return done != 0;
+}
+// bounded wait; gives up early when another role of the CTA raised *abort
+// (then returns false without raising it again)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort = nullptr) {
+  for (long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (abort && (it & 255) == 255 && *abort) return false;
+  }
+  if (abort) *abort = 1;
+  return false;
 }
 
 __device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
@@ -69,11 +76,14 @@ __device__ __forceinline__ void bulk_tile(void* dst, const void* src, uint32_t b
 }
 
 struct __align__(1024) GemmSmem {
-  uint8_t a[GSTAGES][GCM * GTK * 2];  // 32 KB per stage (one operand tile)
+  uint8_t a[GSTAGES][GTM * GTK * 2];  // 16 KB per stage
   uint8_t b[GSTAGES][GTN * GTK * 2];  // 32 KB per stage
   uint64_t full[GSTAGES];             // copies of the stage landed
   uint64_t empty[GSTAGES];            // MMAs reading the stage done
+  uint64_t acc_full[2];               // accumulator ready for the epilogue
+  uint64_t acc_empty[2];              // accumulator drained (one arrival per epilogue warp)
   uint32_t tmem;
+  int abort;
 };
 
 // ------------------------------------------------------------ epilogues
@@ -186,31 +196,27 @@ __device__ __forceinline__ void epilogue(const GemmArgs& g, int r, int cb, const
   }
 }
 
-// Operands are stored tile by tile (gemm_tiled): one 256-row x 64-K tile is
-// 32 KB, contiguous, already in the shared-memory order the MMAs read, so a
-// stage is two bulk copies issued by one thread.  Thread 0 also issues the
-// MMAs; the other warps wait at the block barrier and then drain the
-// accumulators through the epilogue of MODE.
 template <int MODE>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t gsm_raw[];
   GemmSmem& sm = *reinterpret_cast<GemmSmem*>(gsm_raw);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  // the CTAs that share an operand tile of the data run together: the DFT
-  // matrix's (few) tiles are the fast grid dimension
-  const int mt = g.w_is_b ? blockIdx.y : blockIdx.x;
-  const int nt = g.w_is_b ? blockIdx.x : blockIdx.y;
-  const int m0 = mt * GCM, n0 = nt * GTN;
+  volatile int* abort = &sm.abort;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sm.tmem)),
                  "r"(2 * GTN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid == 0) {
+  if (tid == 32) {
     for (int s = 0; s < GSTAGES; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.empty[s])));
     }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&sm.acc_full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&sm.acc_empty[b])), "r"(kEpiWarps));
+    }
+    sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -218,83 +224,112 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const __grid_consta
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = sm.tmem;
   const int kchunks = g.K / GTK;
-  const int total = g.nseg * kchunks;
-  constexpr uint32_t kTile = GCM * GTK * 2;  // bytes of one operand tile (A and B alike)
-  static_assert(GCM == GTN, "A and B tiles have the same shape");
-  bool ok = true;
-  if (tid == 0) {
-    int copied = 0;    // chunks whose copies were issued
-    int landed = 0;    // chunks whose copies were waited for
-    int committed = 0; // chunks whose MMAs were committed
-    auto issue = [&](int c) {
-      const int st = c % GSTAGES, seg = c / kchunks, kc = c % kchunks;
-      const uint32_t fb = smem_addr(&sm.full[st]);
-      bar_expect_tx(fb, 2 * kTile);
-      bulk_tile(sm.a[st], g.a[seg] + ((size_t)mt * kchunks + kc) * (kTile / 2), kTile, fb);
-      bulk_tile(sm.b[st], g.b[seg] + ((size_t)nt * kchunks + kc) * (kTile / 2), kTile, fb);
-      copied = c + 1;
-    };
-    for (int c = 0; c < GSTAGES - 1 && c < total; ++c) issue(c);
-    for (int it = 0; it < total && ok; ++it) {
-      const int st = it % GSTAGES;
-      if (!mbar_wait(smem_addr(&sm.full[st]), (uint32_t)((it / GSTAGES) & 1))) {
-        ok = false;
-        break;
-      }
-      landed = it + 1;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t sa = smem_addr(sm.a[st]), sb = smem_addr(sm.b[st]);
-#pragma unroll
-      for (int kk = 0; kk < GTK / 16; ++kk) {
-        const uint64_t db = kmajor_desc(sb + kk * 256);
-        const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {  // rows h*128.. of the tile: A core matrices from byte 16 KB * h
-          const uint64_t da = kmajor_desc(sa + h * (GTM / 8) * (GTK / 8) * 128 + kk * 256);
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(h * GTN)),
-              "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+  const int total = g.nseg * kchunks;  // K chunks per tile
+  // tiles, the DFT matrix's (few) tiles the fast index: the CTAs that share a
+  // data tile run together
+  const int tilesA = g.rows / GTM, tilesB = (g.cols + GTN - 1) / GTN;
+  const int ntiles = tilesA * tilesB;
+  auto tile_of = [&](int t, int& mt, int& nt) {
+    if (g.w_is_b) {
+      nt = t % tilesB;
+      mt = t / tilesB;
+    } else {
+      mt = t % tilesA;
+      nt = t / tilesA;
+    }
+  };
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int c = 0;
+      int last[GSTAGES];
+      for (int s = 0; s < GSTAGES; ++s) last[s] = -1;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int mt, nt;
+        tile_of(t, mt, nt);
+        for (int it = 0; it < total; ++it, ++c) {
+          const int st = c % GSTAGES;
+          if (c >= GSTAGES &&
+              !mbar_wait(smem_addr(&sm.empty[st]), (uint32_t)(((c / GSTAGES) - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          const int seg = it / kchunks, kc = it % kchunks;
+          const uint32_t fb = smem_addr(&sm.full[st]);
+          bar_expect_tx(fb, (GTM + GTN) * GTK * 2);
+          // 128-row A tile mt: half (mt & 1) of the stored 256-row tile mt / 2
+          bulk_tile(sm.a[st], g.a[seg] + (((size_t)(mt >> 1) * kchunks + kc) << 14) + ((size_t)(mt & 1) << 13),
+                    GTM * GTK * 2, fb);
+          bulk_tile(sm.b[st], g.b[seg] + (((size_t)nt * kchunks + kc) << 14), GTN * GTK * 2, fb);
+          last[st] = c;
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(&sm.empty[st])));
-      committed = it + 1;
-      // refill the stage of chunk it-1 with chunk it+GSTAGES-1 once its MMAs are done
-      const int nx = it + GSTAGES - 1;
-      if (nx < total) {
-        if (it >= 1 && !mbar_wait(smem_addr(&sm.empty[(it - 1) % GSTAGES]), (uint32_t)(((it - 1) / GSTAGES) & 1))) {
+      // no copy may still target shared memory when the CTA ends
+      for (int s = 0; s < GSTAGES; ++s)
+        if (last[s] >= 0) (void)mbar_wait(smem_addr(&sm.full[s]), (uint32_t)((last[s] / GSTAGES) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      int c = 0, tc = 0;
+      uint32_t last_bar = 0, last_par = 0;  // the latest commit (covers every MMA before it)
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+        const int b = tc & 1;
+        if (tc >= 2 && !mbar_wait(smem_addr(&sm.acc_empty[b]), (uint32_t)(((tc >> 1) - 1) & 1), abort)) {
           ok = false;
           break;
         }
-        issue(nx);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t acc0 = tmem + (uint32_t)(b * GTN);
+        for (int it = 0; it < total; ++it, ++c) {
+          const int st = c % GSTAGES;
+          if (!mbar_wait(smem_addr(&sm.full[st]), (uint32_t)((c / GSTAGES) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sa = smem_addr(sm.a[st]), sb = smem_addr(sm.b[st]);
+#pragma unroll
+          for (int kk = 0; kk < GTK / 16; ++kk) {
+            const uint64_t da = kmajor_desc(sa + kk * 256), db = kmajor_desc(sb + kk * 256);
+            const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc0),
+                "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+          }
+          last_bar = smem_addr(&sm.empty[st]);
+          last_par = (uint32_t)((c / GSTAGES) & 1);
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(last_bar));
+        }
+        if (!ok) break;
+        last_bar = smem_addr(&sm.acc_full[b]);
+        last_par = (uint32_t)((tc >> 1) & 1);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(last_bar));
       }
+      // no MMA may still write tensor memory when it is released
+      if (last_bar) (void)mbar_wait(last_bar, last_par);
     }
-    // the last commit covers every MMA issued before it
-    if (ok && committed > 0 &&
-        !mbar_wait(smem_addr(&sm.empty[(committed - 1) % GSTAGES]), (uint32_t)(((committed - 1) / GSTAGES) & 1)))
-      ok = false;
-    if (!ok) {
-      // a wait gave up: give the copies and MMAs in flight a bounded chance to
-      // finish before the shared and tensor memory they use is released
-      for (int c = landed; c < copied; ++c)
-        (void)mbar_wait(smem_addr(&sm.full[c % GSTAGES]), (uint32_t)((c / GSTAGES) & 1));
-      if (committed > 0)
-        (void)mbar_wait(smem_addr(&sm.empty[(committed - 1) % GSTAGES]), (uint32_t)(((committed - 1) / GSTAGES) & 1));
-      atomicExch(g.err, 1);
-    }
-  }
-  ok = __syncthreads_and(ok);
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok) {
-    for (int h = 0; h < 2; ++h) {
-      // warp w reads TMEM lanes 32 (w % 4) .. +31 (its lane quarter) and the
-      // columns of part w / 4
-      const int r = m0 + h * GTM + (warp & 3) * 32 + lane;  // accumulator row of this thread
-      constexpr int kCols = GTN / kColSplit;
-      for (int c0 = (warp >> 2) * kCols; c0 < ((warp >> 2) + 1) * kCols; c0 += 32) {
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;                 // TMEM lane quarter
+    const int part = (warp - 2) >> 2;       // column quarter
+    int tc = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+      const int b = tc & 1;
+      if (!mbar_wait(smem_addr(&sm.acc_full[b]), (uint32_t)((tc >> 1) & 1), abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      int mt, nt;
+      tile_of(t, mt, nt);
+      const int r = mt * GTM + q * 32 + lane;  // accumulator row of this thread
+#pragma unroll 1
+      for (int c0 = part * (GTN / 4); c0 < (part + 1) * (GTN / 4); c0 += 32) {
         uint32_t u[32];
-        const uint32_t addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * GTN + c0);
+        const uint32_t addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * GTN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -304,16 +339,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const __grid_consta
               "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
             : "r"(addr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (r >= g.vrows) continue;
-        float v[32];
+        if (r < g.vrows) {
+          float v[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
-        epilogue<MODE>(g, r, n0 + c0, v);
+          for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
+          epilogue<MODE>(g, r, nt * GTN + c0, v);
+        }
       }
+      // this warp is done with the accumulator
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&sm.acc_empty[b])) : "memory");
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
+  if (tid == 0 && sm.abort) atomicExch(g.err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * GTN));
 }
 
@@ -326,9 +367,15 @@ static cudaError_t launch_mode(const GemmArgs& g, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int ta = g.rows / GCM, tb = (g.cols + GTN - 1) / GTN;
-  const dim3 grid = g.w_is_b ? dim3(tb, ta) : dim3(ta, tb);
-  k_tc_gemm<MODE><<<grid, kGemmThreads, sm, s>>>(g);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int tiles = (g.rows / GTM) * ((g.cols + GTN - 1) / GTN);
+  k_tc_gemm<MODE><<<std::min(tiles, sms), kGemmThreads, sm, s>>>(g);
   return cudaGetLastError();
 }
 
