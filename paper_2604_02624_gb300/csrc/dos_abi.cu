@@ -578,6 +578,8 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
     f.h = d_h;
     f.ckpt = c->ckpt;
     f.ckt = c->ckt;
+    c->ckpt1_is_v1 = c->v1 && !c->mis_on;
+    f.v1 = c->ckpt1_is_v1 ? c->v1 : nullptr;
     f.o = c->o;
     f.I = d_I;
     f.sq = c->mis_on ? c->sq : nullptr;
@@ -660,6 +662,7 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
     f.h = d_h;
     f.ckpt = c->ckpt;
     f.ckt = c->ckt;
+    f.v1 = c->ckpt1_is_v1 ? c->v1 : nullptr;
     f.o = c->o;
     f.dLdI = d_dLdI;
     f.sq = c->mis_on ? c->sq : nullptr;
@@ -1127,7 +1130,8 @@ DOS_API int dos_layer_field(dos_ctx* c, int layer, float* d_v) {
   if (layer < 1 || layer > c->K) return fail(DOS_ERR_ARG, "layer must be in [1, n_layers]");
   if (!d_v) return fail(DOS_ERR_ARG, "d_v is NULL");
   const size_t n2 = (size_t)c->n * c->n;
-  const bool table = layer == 1 && c->ckpt1_is_v1 && (c->path == DOS_PATH_MULTIPASS || c->path == DOS_PATH_MULTIPASS_BULK);
+  const bool table = layer == 1 && c->ckpt1_is_v1 &&
+                     (c->path == DOS_PATH_MULTIPASS || c->path == DOS_PATH_MULTIPASS_BULK || c->path == DOS_PATH_FUSED);
   DOS_CUDA(cudaMemcpyAsync(d_v, table ? c->v1 : c->ckpt + (size_t)(layer - 1) * c->nw * n2,
                            sizeof(float2) * c->nw * n2, cudaMemcpyDeviceToDevice, c->stream),
            "copy layer field");

@@ -43,6 +43,8 @@ struct FusedArgs {
   const ChanConst* chan;     // [nw]
   const float* h;            // [K][n][n]
   float2* ckpt;              // [K][nw][n][n] incoming field v of each layer
+  const float2* v1;          // [nw][n][n] create-time input field v1 = P_z0(aperture), or null:
+                             // then layer 1 starts from it (no gap-0 phase) and it is layer 1's checkpoint
   float2* ckt;               // [K][nw][n][n] transmission t of each layer and channel
   float2* o;                 // [nw][fov][fov]
   float* I;                  // [nw][fov][fov] or null
@@ -202,6 +204,7 @@ struct Fused {
     const float* hl = a.h + (size_t)layer * a.n * a.n;
     float2* ck = a.ckpt + ((size_t)layer * a.nw + w) * a.n * a.n;
     float2* ct = a.ckt + ((size_t)layer * a.nw + w) * a.n * a.n;
+    const bool from_v1 = layer == 0 && a.v1;
     // the column buffers double as row-phase exchange space, at the row-slot
     // stride (ZS): with the row phase's thread layout that stride is conflict-free
     float2* zc = s.colz + l * ZS;
@@ -218,11 +221,24 @@ struct Fused {
         hv[i] = (ok && x < a.n) ? __ldg(hrow + x) : 0.f;
       }
       float2 r[E];
-#pragma unroll
-      for (int i = 0; i < E; ++i) r[i] = z[t + T * i];
-      __syncthreads();
-      LF::template fft<true, LF::P, QH, false>(r, t, z, s.tw);
       const size_t ro = (size_t)(ok ? row : 0) * a.n;
+      if (from_v1) {
+        // layer 1 from the input-field table (uniform across the block); the
+        // barrier keeps the previous round's readers of zc ahead of this
+        // round's forward DFT, as the inverse DFT's barriers do otherwise
+        const float2* vrow = a.v1 + (size_t)w * a.n * a.n + ro;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int x = t + T * i;
+          r[i] = (i < EH && ok && x < a.n) ? vrow[x] : czero();
+        }
+        __syncthreads();
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) r[i] = z[t + T * i];
+        __syncthreads();
+        LF::template fft<true, LF::P, QH, false>(r, t, z, s.tw);
+      }
 #pragma unroll
       for (int i = 0; i < EH; ++i) {
         const int x = t + T * i;
@@ -230,7 +246,7 @@ struct Fused {
           const float2 v = r[i];
           const float2 tt = transmission(hv[i], cc);
           if (ok && a.save) {
-            ck[ro + x] = v;
+            if (!from_v1) ck[ro + x] = v;
             ct[ro + x] = tt;
           }
           r[i] = cmul(tt, v);
@@ -320,7 +336,8 @@ struct Fused {
     const int l = threadIdx.x / T;
     const int rank = (int)cl.block_rank();
     const ChanConst cc = a.chan[w];
-    const float2* ck = a.ckpt + ((size_t)layer * a.nw + w) * a.n * a.n;
+    const float2* ck = (layer == 0 && a.v1) ? a.v1 + (size_t)w * a.n * a.n
+                                            : a.ckpt + ((size_t)layer * a.nw + w) * a.n * a.n;
     const float2* ct = a.ckt + ((size_t)layer * a.nw + w) * a.n * a.n;
     float* pl = part + (size_t)layer * a.n * a.n;
     const bool last = layer == 0;
@@ -394,8 +411,10 @@ struct Fused {
     const int cid = blockIdx.x / C;
     const int ncl = gridDim.x / C;
     for (int w = cid; w < a.nw; w += ncl) {
-      col_phase<false, true>(cl, s, table(a, 0, w), a.arow, a.n, a.hs, 0, 0, 0, a.n, sqt(a, w), mis(a, 0));
-      cl.sync();
+      if (!a.v1) {  // gap 0 from the aperture (the table is not used with displaced layers)
+        col_phase<false, true>(cl, s, table(a, 0, w), a.arow, a.n, a.hs, 0, 0, 0, a.n, sqt(a, w), mis(a, 0));
+        cl.sync();
+      }
       for (int layer = 0; layer < a.K; ++layer) {
         row_fwd_phase(cl, s, a, layer, w);
         cl.sync();

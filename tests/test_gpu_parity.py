@@ -442,3 +442,26 @@ def test_forced_configuration_and_tuning_cache(tmp_path, monkeypatch):
     st = _stack(w, path="auto")
     assert st.path == first and "tuning cache" in L.dos_describe(st.handle)
     st.close()
+
+
+@pytest.mark.parametrize("path", ["dft_gemm", "dft_gemm_x3"])
+@pytest.mark.parametrize("n,m,k", [(50, 128, 2), (7, 16, 1), (100, 200, 3)])
+def test_split_bf16_ragged_shapes(path, n, m, k):
+    """Shapes off the tile grid: N not a multiple of 8 (the row-DFT epilogue
+    stores element by element), K padding (2N, 2M not multiples of 64), a
+    data operand that is not a whole number of 256-row tiles, M = 16."""
+    fov = n if n < 16 else (n // 2 if (n - n // 2) % 2 == 0 else n // 2 + 1)
+    w = custom(n, m, k, [480, 610, 720], 30, fov, kappa=0.01, name="gemm-ragged")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    st = _stack(w, path=path)
+    hd = _t(h)
+    I = st.forward(hd)
+    o = st.output_field()
+    _, _, dl = st.loss(_t(T))
+    g = _np(st.backward(hd, dl)).astype(np.float64)
+    L_ref, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    assert rel_l2(_np(o).astype(np.complex128), fwd["o"]) <= SPLIT_TARGET
+    assert rel_l2(_np(I).astype(np.float64), fwd["I"]) <= SPLIT_TARGET
+    assert rel_l2(g, g_ref) <= TOL_GRAD_FD
+    st.close()
