@@ -79,9 +79,7 @@ struct PassOps {
   cudaError_t (*row_back)(const PassArgs&, cudaStream_t);  // row spectra -> caller field
   cudaError_t (*row_first)(const PassArgs&, cudaStream_t); // t(h) * field (fin) -> row spectra
   // the same column / forward row / adjoint row passes with bulk-async prefetch
-  // (dos_pass_bulk.cuh); bulk_row_lines rows per row block
-  int bulk_row_lines;
-  size_t (*bulk_col_smem)(int n);
+  // (dos_pass_bulk.cuh)
   cudaError_t (*bulk_col)(const PassArgs&, bool adjoint, cudaStream_t);
   cudaError_t (*bulk_row_fwd)(const PassArgs&, bool save, cudaStream_t);
   cudaError_t (*bulk_row_adj)(const PassArgs&, bool first, cudaStream_t);

@@ -496,8 +496,8 @@ const PassOps* pass_ops_table() {
   static const PassOps o = {LF::M,       LF::P,          LF::Q,          LF::T,
                             Pass<LF>::ROWL, Pass<LF>::COLL, &PL::col,    &PL::row_fwd,
                             &PL::row_out, &PL::row_seed,  &PL::row_adj,  &PL::row_in,
-                            &PL::row_back, &PL::row_first, RL, &PassBulk<LF, RL>::col_smem,
-                            &PBL::col,    &PBL::row_fwd,  &PBL::row_adj};
+                            &PL::row_back, &PL::row_first, &PBL::col, &PBL::row_fwd,
+                            &PBL::row_adj};
   return &o;
 }
 
