@@ -360,20 +360,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const __grid_consta
 
 template <int MODE>
 static cudaError_t launch_mode(const GemmArgs& g, cudaStream_t s) {
+  // attribute and SM count of the current device, every launch (contexts may
+  // live on different devices of one process; both calls are host-side only)
   const size_t sm = sizeof(GemmSmem) + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   const int tiles = (g.rows / GTM) * ((g.cols + GTN - 1) / GTN);
   k_tc_gemm<MODE><<<std::min(tiles, sms), kGemmThreads, sm, s>>>(g);
   return cudaGetLastError();
