@@ -34,9 +34,6 @@ sys.path.insert(0, ROOT)
 # kernel kind); the bench scales them to the launch's channels.  An entry must
 # be removed (traffic reported as null) when its kernel changes.
 TRAFFIC_PER_CHANNEL = {
-    ("multipass", 200, 400, "column_forward"): (1.4064e6, "profiles/column_pass_multipass_batched.md"),
-    ("multipass_bulk", 200, 400, "column_forward"): (1.4006e6, "profiles/column_pass_bulk_batched.md"),
-    ("multipass_bulk", 200, 400, "column_adjoint"): (1.4015e6, "profiles/column_pass_bulk_batched.md"),
 }
 
 METRIC = "lambda-channel layer-propagations/s (fwd+adjoint, 4096 lambda)"

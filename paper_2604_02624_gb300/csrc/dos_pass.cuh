@@ -50,9 +50,19 @@ constexpr int row_line_stride(int m, int zs) {
   return m == 400 ? 420 : m == 200 ? 222 : m == 128 ? 148 : m == 32 ? 42 : zs;
 }
 
-template <class LF>
+// HALF (N <= M / 2, every compiled design with M = 2N): the field half of a
+// line, x < M / 2, holds every non-zero input of a forward DFT and every output
+// that is kept of an inverse one.  Thread t's elements t + T i with i < E / 2
+// are exactly that half, and so are the first P / 2 inputs of each first-step
+// sub-DFT and the first Q / 2 outputs of each second-step one: the line DFTs
+// are pruned at compile time (NZF, NOI) and the field-domain loops stop at EF.
+template <class LF, bool HALF = false>
 struct Pass {
   static constexpr int T = LF::T, E = LF::E, M = LF::M;
+  static constexpr int NZF = HALF ? LF::P / 2 : LF::P;  // forward DFT of a field: non-zero inputs per sub-DFT
+  static constexpr int NOI = HALF ? LF::Q / 2 : LF::Q;  // inverse DFT to a field: outputs kept per sub-DFT
+  static constexpr int EF = HALF ? E / 2 : E;           // field-domain elements of a thread
+  static_assert(!HALF || (LF::P % 2 == 0 && LF::Q % 2 == 0), "halving needs even factors");
   static constexpr int ROWL = 16;  // rows per block in the row passes
   static constexpr int COLL = 16;  // columns per block in the column pass
   // column pass: line = tid % COLL, an odd stride keeps the lines apart
@@ -90,9 +100,9 @@ struct Pass {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int row = t + T * i;
-        r[i] = (ok && row >= a.in_r0 && row < a.in_r1) ? src[(size_t)row * M] : czero();
+        r[i] = (i < EF && ok && row >= a.in_r0 && row < a.in_r1) ? src[(size_t)row * M] : czero();
       }
-      LF::template fft<false>(r, t, z, tw);
+      LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
     }
     const float2* Hw = a.Hq + (size_t)w * a.hs * a.hs;
     const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
@@ -105,12 +115,12 @@ struct Pass {
       if (Sw) hv = cmul(hv, misalign_factor(a.mis, k, cc, M, Sw[qi]));
       r[i] = ADJ ? cmulc(r[i], hv) : cmul(r[i], hv);
     }
-    LF::template fft<true>(r, t, z, tw);
+    LF::template fft<true, LF::P, NOI>(r, t, z, tw);
     float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int row = t + T * i;
-      if (ok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
+      if (i < EF && ok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
     }
   }
 
@@ -144,14 +154,14 @@ struct Pass {
     float2 r[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-    LF::template fft<true>(r, t, rc.z, rc.tw);
+    LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
     const ChanConst cc = a.chan[w];
     const float* hrow = a.h + (size_t)rr * a.n;
     float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int x = t + T * i;
-      if (x < a.n) {
+      if (i < EF && x < a.n) {
         const float2 v = r[i];
         if (SAVE && ok) ck[x] = v;
         r[i] = cmul(transmission(hrow[x], cc), v);
@@ -159,7 +169,7 @@ struct Pass {
         r[i] = czero();
       }
     }
-    LF::template fft<false>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
     if (ok) {
 #pragma unroll
       for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -183,9 +193,9 @@ struct Pass {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int x = t + T * i;
-      r[i] = x < a.n ? cmul(transmission(hrow[x], cc), vrow[x]) : czero();
+      r[i] = (i < EF && x < a.n) ? cmul(transmission(hrow[x], cc), vrow[x]) : czero();
     }
-    LF::template fft<false>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* srow = a.S + ((size_t)w * a.n + row) * M;
 #pragma unroll
@@ -205,14 +215,14 @@ struct Pass {
     float2 r[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-    LF::template fft<true>(r, t, rc.z, rc.tw);
+    LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* orow = a.o + ((size_t)w * a.fov + fr) * a.fov;
       float* irow = a.I ? a.I + ((size_t)w * a.fov + fr) * a.fov : nullptr;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int x = t + T * i - a.of;
-        if (x >= 0 && x < a.fov) {
+        if (i < EF && x >= 0 && x < a.fov) {
           orow[x] = r[i];
           if (irow) irow[x] = fmaf(r[i].x, r[i].x, r[i].y * r[i].y);
         }
@@ -234,9 +244,9 @@ struct Pass {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int x = t + T * i - a.of;
-      r[i] = (ok && x >= 0 && x < a.fov) ? cscale(orow[x], 2.0f * grow[x]) : czero();
+      r[i] = (i < EF && ok && x >= 0 && x < a.fov) ? cscale(orow[x], 2.0f * grow[x]) : czero();
     }
-    LF::template fft<false>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* srow = a.S + ((size_t)w * a.n + a.of + fr) * M;
 #pragma unroll
@@ -267,12 +277,12 @@ struct Pass {
       float2 r[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-      LF::template fft<true>(r, t, rc.z, rc.tw);
+      LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
       const ChanConst cc = a.chan[w];
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int x = t + T * i;
-        if (x < a.n) {
+        if (i < EF && x < a.n) {
           const float2 au = r[i];
           const float2 tt = transmission(hrow[x], cc);
           const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
@@ -283,7 +293,7 @@ struct Pass {
         }
       }
       if constexpr (!FIRST) {
-        LF::template fft<false>(r, t, rc.z, rc.tw);
+        LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -295,7 +305,7 @@ struct Pass {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int x = t + T * i;
-        if (x < a.n) prow[x] = g[i];
+        if (i < EF && x < a.n) prow[x] = g[i];
       }
     }
   }
@@ -313,9 +323,9 @@ struct Pass {
 #pragma unroll
     for (int i = 0; i < E; ++i) {
       const int x = t + T * i;
-      r[i] = x < a.n ? frow[x] : czero();
+      r[i] = (i < EF && x < a.n) ? frow[x] : czero();
     }
-    LF::template fft<false>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* srow = a.S + ((size_t)w * a.n + row) * M;
 #pragma unroll
@@ -335,13 +345,13 @@ struct Pass {
     float2 r[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-    LF::template fft<true>(r, t, rc.z, rc.tw);
+    LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* frow = a.fout + ((size_t)w * a.n + row) * a.n;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int x = t + T * i;
-        if (x < a.n) frow[x] = r[i];
+        if (i < EF && x < a.n) frow[x] = r[i];
       }
     }
   }
@@ -354,37 +364,37 @@ struct Pass {
 template <class LF>
 constexpr int pass_min_blocks() { return LF::E <= 20 ? 3 : 1; }
 
-template <class LF, bool ADJ, bool APERTURE>
+template <class LF, bool HALF, bool ADJ, bool APERTURE>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::COLL) k_col(PassArgs a) {
-  Pass<LF>::template col<ADJ, APERTURE>(a);
+  Pass<LF, HALF>::template col<ADJ, APERTURE>(a);
 }
-template <class LF, bool SAVE>
+template <class LF, bool HALF, bool SAVE>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>()) k_row_fwd(PassArgs a) {
-  Pass<LF>::template row_fwd<SAVE>(a);
+  Pass<LF, HALF>::template row_fwd<SAVE>(a);
 }
-template <class LF>
+template <class LF, bool HALF>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>()) k_row_first(PassArgs a) {
-  Pass<LF>::row_first(a);
+  Pass<LF, HALF>::row_first(a);
 }
-template <class LF>
+template <class LF, bool HALF>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_out(PassArgs a) {
-  Pass<LF>::row_out(a);
+  Pass<LF, HALF>::row_out(a);
 }
-template <class LF>
+template <class LF, bool HALF>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_seed(PassArgs a) {
-  Pass<LF>::row_seed(a);
+  Pass<LF, HALF>::row_seed(a);
 }
-template <class LF, bool FIRST>
+template <class LF, bool HALF, bool FIRST>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_adj(PassArgs a) {
-  Pass<LF>::template row_adj<FIRST>(a);
+  Pass<LF, HALF>::template row_adj<FIRST>(a);
 }
-template <class LF>
+template <class LF, bool HALF>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_in(PassArgs a) {
-  Pass<LF>::row_in(a);
+  Pass<LF, HALF>::row_in(a);
 }
-template <class LF>
+template <class LF, bool HALF>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_back(PassArgs a) {
-  Pass<LF>::row_back(a);
+  Pass<LF, HALF>::row_back(a);
 }
 
 template <typename K>
@@ -397,47 +407,74 @@ static cudaError_t launch_k(K kernel, dim3 grid, int threads, size_t smem, const
   return cudaGetLastError();
 }
 
+// Each launcher picks the halved (pruned) kernels when the design allows it.
 template <class LF>
 struct PassLaunch {
   using PS = Pass<LF>;
   static constexpr int RT = LF::T * PS::ROWL;
   static constexpr int CT = LF::T * PS::COLL;
   static int row_blocks(int rows) { return (rows + PS::ROWL - 1) / PS::ROWL; }
+  static bool half(const PassArgs& a) { return 2 * a.n <= LF::M; }
 
-  static cudaError_t col(const PassArgs& a, bool adj, bool ap, cudaStream_t s) {
+  template <bool H>
+  static cudaError_t col_h(const PassArgs& a, bool adj, bool ap, cudaStream_t s) {
     const dim3 g((LF::M + PS::COLL - 1) / PS::COLL, a.nw);
     const size_t sm = PS::smem_bytes(PS::COLL);
-    if (ap) return adj ? launch_k(k_col<LF, true, true>, g, CT, sm, a, s)
-                       : launch_k(k_col<LF, false, true>, g, CT, sm, a, s);
-    return adj ? launch_k(k_col<LF, true, false>, g, CT, sm, a, s)
-               : launch_k(k_col<LF, false, false>, g, CT, sm, a, s);
+    if (ap) return adj ? launch_k(k_col<LF, H, true, true>, g, CT, sm, a, s)
+                       : launch_k(k_col<LF, H, false, true>, g, CT, sm, a, s);
+    return adj ? launch_k(k_col<LF, H, true, false>, g, CT, sm, a, s)
+               : launch_k(k_col<LF, H, false, false>, g, CT, sm, a, s);
   }
-  static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
+  static cudaError_t col(const PassArgs& a, bool adj, bool ap, cudaStream_t s) {
+    return half(a) ? col_h<true>(a, adj, ap, s) : col_h<false>(a, adj, ap, s);
+  }
+  template <bool H>
+  static cudaError_t row_fwd_h(const PassArgs& a, bool save, cudaStream_t s) {
     const dim3 g(row_blocks(a.n), a.nw);
     const size_t sm = PS::row_smem_bytes(PS::ROWL);
-    return save ? launch_k(k_row_fwd<LF, true>, g, RT, sm, a, s)
-                : launch_k(k_row_fwd<LF, false>, g, RT, sm, a, s);
+    return save ? launch_k(k_row_fwd<LF, H, true>, g, RT, sm, a, s)
+                : launch_k(k_row_fwd<LF, H, false>, g, RT, sm, a, s);
+  }
+  static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
+    return half(a) ? row_fwd_h<true>(a, save, s) : row_fwd_h<false>(a, save, s);
   }
   static cudaError_t row_first(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_first<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
+    const dim3 g(row_blocks(a.n), a.nw);
+    const size_t sm = PS::row_smem_bytes(PS::ROWL);
+    return half(a) ? launch_k(k_row_first<LF, true>, g, RT, sm, a, s)
+                   : launch_k(k_row_first<LF, false>, g, RT, sm, a, s);
   }
   static cudaError_t row_out(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_out<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
+    const dim3 g(row_blocks(a.fov), a.nw);
+    const size_t sm = PS::row_smem_bytes(PS::ROWL);
+    return half(a) ? launch_k(k_row_out<LF, true>, g, RT, sm, a, s) : launch_k(k_row_out<LF, false>, g, RT, sm, a, s);
   }
   static cudaError_t row_seed(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_seed<LF>, dim3(row_blocks(a.fov), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
+    const dim3 g(row_blocks(a.fov), a.nw);
+    const size_t sm = PS::row_smem_bytes(PS::ROWL);
+    return half(a) ? launch_k(k_row_seed<LF, true>, g, RT, sm, a, s)
+                   : launch_k(k_row_seed<LF, false>, g, RT, sm, a, s);
   }
-  static cudaError_t row_adj(const PassArgs& a, bool first, cudaStream_t s) {
+  template <bool H>
+  static cudaError_t row_adj_h(const PassArgs& a, bool first, cudaStream_t s) {
     const dim3 g(row_blocks(a.n), a.n_chunks);
     const size_t sm = PS::row_smem_bytes(PS::ROWL);
-    return first ? launch_k(k_row_adj<LF, true>, g, RT, sm, a, s)
-                 : launch_k(k_row_adj<LF, false>, g, RT, sm, a, s);
+    return first ? launch_k(k_row_adj<LF, H, true>, g, RT, sm, a, s)
+                 : launch_k(k_row_adj<LF, H, false>, g, RT, sm, a, s);
+  }
+  static cudaError_t row_adj(const PassArgs& a, bool first, cudaStream_t s) {
+    return half(a) ? row_adj_h<true>(a, first, s) : row_adj_h<false>(a, first, s);
   }
   static cudaError_t row_in(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_in<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
+    const dim3 g(row_blocks(a.n), a.nw);
+    const size_t sm = PS::row_smem_bytes(PS::ROWL);
+    return half(a) ? launch_k(k_row_in<LF, true>, g, RT, sm, a, s) : launch_k(k_row_in<LF, false>, g, RT, sm, a, s);
   }
   static cudaError_t row_back(const PassArgs& a, cudaStream_t s) {
-    return launch_k(k_row_back<LF>, dim3(row_blocks(a.n), a.nw), RT, PS::row_smem_bytes(PS::ROWL), a, s);
+    const dim3 g(row_blocks(a.n), a.nw);
+    const size_t sm = PS::row_smem_bytes(PS::ROWL);
+    return half(a) ? launch_k(k_row_back<LF, true>, g, RT, sm, a, s)
+                   : launch_k(k_row_back<LF, false>, g, RT, sm, a, s);
   }
 };
 

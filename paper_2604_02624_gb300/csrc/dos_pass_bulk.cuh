@@ -75,9 +75,11 @@ constexpr int row_stage_stride(int m) {
   return m == 400 ? 404 : m == 200 ? 202 : m == 128 ? 132 : m == 64 ? 68 : m == 32 ? 34 : m == 16 ? 18 : m;
 }
 
-template <class LF, int RL>
+// HALF: the pruned line DFTs and field-half loops of Pass<LF, true> (N <= M / 2).
+template <class LF, int RL, bool HALF = false>
 struct PassBulk {
   static constexpr int T = LF::T, E = LF::E, M = LF::M;
+  static constexpr int NZF = Pass<LF, HALF>::NZF, NOI = Pass<LF, HALF>::NOI, EF = Pass<LF, HALF>::EF;
   static constexpr int COLL = Pass<LF>::COLL, ZL = Pass<LF>::ZL, RZL = Pass<LF>::RZL;
   static constexpr int SR = row_stage_stride(M);  // even: every staged row starts 16-byte aligned
   static_assert(SR % 2 == 0 && SR >= M, "staged rows must be 16-byte aligned and hold M values");
@@ -138,7 +140,7 @@ struct PassBulk {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int row = t + T * i;
-        r[i] = row < a.n ? stage[(size_t)row * COLL + l] : czero();
+        r[i] = (i < EF && row < a.n) ? stage[(size_t)row * COLL + l] : czero();
       }
       __syncthreads();  // stage consumed: the next item may land in it
       if (it + (int)gridDim.x < items) fetch(it + gridDim.x);
@@ -155,7 +157,7 @@ struct PassBulk {
           hv[i] = __ldg(Hw + (size_t)min(kk, M - kk) * a.hs + bc);
         }
       }
-      LF::template fft<false>(r, t, z, tw);
+      LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         float2 h;
@@ -171,12 +173,12 @@ struct PassBulk {
         }
         r[i] = ADJ ? cmulc(r[i], h) : cmul(r[i], h);
       }
-      LF::template fft<true>(r, t, z, tw);
+      LF::template fft<true, LF::P, NOI>(r, t, z, tw);
       float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int row = t + T * i;
-        if (cok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
+        if (i < EF && cok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
       }
     }
     if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
@@ -229,7 +231,7 @@ struct PassBulk {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int x = t + T * i;
-        hv[i] = (x < a.n) ? __ldg(hrow + x) : 0.f;
+        hv[i] = (i < EF && x < a.n) ? __ldg(hrow + x) : 0.f;
       }
     }
     float g[E];
@@ -247,14 +249,14 @@ struct PassBulk {
       for (int i = 0; i < E; ++i) r[i] = stage[(size_t)(ok ? l : 0) * SR + t + T * i];
       __syncthreads();  // stage consumed: the next channel may land in it
       if (w + 1 < w1) fetch(w + 1);
-      LF::template fft<true>(r, t, z, tw);
+      LF::template fft<true, LF::P, NOI>(r, t, z, tw);
       float2* srow = a.S + ((size_t)w * a.n + rr) * M;
       if constexpr (!ADJ) {
         float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           const int x = t + T * i;
-          if (x < a.n) {
+          if (i < EF && x < a.n) {
             const float2 v = r[i];
             if (FLAG && ok) ck[x] = v;
             r[i] = cmul(transmission(hv[i], cc), v);
@@ -262,7 +264,7 @@ struct PassBulk {
             r[i] = czero();
           }
         }
-        LF::template fft<false>(r, t, z, tw);
+        LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -272,7 +274,7 @@ struct PassBulk {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           const int x = t + T * i;
-          if (x < a.n) {
+          if (i < EF && x < a.n) {
             const float2 au = r[i];
             const float2 tt = transmission(__ldg(hrow + x), cc);
             const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
@@ -283,7 +285,7 @@ struct PassBulk {
           }
         }
         if constexpr (!FLAG) {
-          LF::template fft<false>(r, t, z, tw);
+          LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
           if (ok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -301,7 +303,7 @@ struct PassBulk {
 #pragma unroll
         for (int i = 0; i < E; ++i) {
           const int x = t + T * i;
-          if (x < a.n) prow[x] = g[i];
+          if (i < EF && x < a.n) prow[x] = g[i];
         }
       }
     }
@@ -374,14 +376,14 @@ struct PassBulk {
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
       const ChanConst cc = a.chan[w];
-      LF::template fft<true>(r, t, z, tw);
+      LF::template fft<true, LF::P, NOI>(r, t, z, tw);
       if (!bulk_wait(&bar[b], (uint32_t)((k >> 1) & 1))) okw = false;
       if (!__syncthreads_and(okw)) break;
       const float2* ck = ckb + ((size_t)b * RL + (ok ? l : 0)) * cks;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int x = t + T * i;
-        if (x < a.n) {
+        if (i < EF && x < a.n) {
           const float2 au = r[i];
           const float2 tt = transmission(__ldg(hrow + x), cc);
           const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
@@ -392,7 +394,7 @@ struct PassBulk {
         }
       }
       if constexpr (!FIRST) {
-        LF::template fft<false>(r, t, z, tw);
+        LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -412,7 +414,7 @@ struct PassBulk {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int x = t + T * i;
-        if (x < a.n) prow[x] = g[i];
+        if (i < EF && x < a.n) prow[x] = g[i];
       }
     }
   }
@@ -422,18 +424,18 @@ struct PassBulk {
 template <class LF>
 constexpr int bulk_min_blocks() { return LF::E <= 20 ? 2 : 1; }
 
-template <class LF, int RL, bool FIRST>
+template <class LF, int RL, bool HALF, bool FIRST>
 __global__ void __launch_bounds__(LF::T * RL, bulk_min_blocks<LF>()) k_row_adj_ck(PassArgs a) {
-  PassBulk<LF, RL>::template row_adj_ck<FIRST>(a);
+  PassBulk<LF, RL, HALF>::template row_adj_ck<FIRST>(a);
 }
-template <class LF, int RL, bool ADJ>
+template <class LF, int RL, bool HALF, bool ADJ>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, bulk_min_blocks<LF>())
     k_col_bulk(PassArgs a, const __grid_constant__ CUtensorMap map) {
-  PassBulk<LF, RL>::template col<ADJ>(a, &map);
+  PassBulk<LF, RL, HALF>::template col<ADJ>(a, &map);
 }
-template <class LF, int RL, bool ADJ, bool FLAG>
+template <class LF, int RL, bool HALF, bool ADJ, bool FLAG>
 __global__ void __launch_bounds__(LF::T * RL, bulk_min_blocks<LF>()) k_row_bulk(PassArgs a) {
-  PassBulk<LF, RL>::template row<ADJ, FLAG>(a);
+  PassBulk<LF, RL, HALF>::template row<ADJ, FLAG>(a);
 }
 
 // Launchers.  The column pass runs one persistent block per resident slot
@@ -456,35 +458,48 @@ struct PassBulkLaunch {
   // The tensor copy needs every row [0, N) as input and N <= 256 (one box);
   // other column passes (the adjoint's first, FOV-rows-only gap) run the
   // plain kernel.
-  static cudaError_t col(const PassArgs& a, bool adj, cudaStream_t s) {
-    const size_t sm = PB::col_smem(a.n);
-    if (!a.tmap || a.in_r0 != 0 || a.in_r1 != a.n || a.n > 256 || sm > 227 * 1024)
-      return PassLaunch<LF>::col(a, adj, false, s);
+  static bool half(const PassArgs& a) { return 2 * a.n <= LF::M; }
+  template <bool H>
+  static cudaError_t col_h(const PassArgs& a, bool adj, size_t sm, cudaStream_t s) {
     const int items = a.nw * ((LF::M + PB::COLL - 1) / PB::COLL);
     if (items == 0) return cudaSuccess;
     int n_slots = 0;
-    auto kern = adj ? k_col_bulk<LF, RL, true> : k_col_bulk<LF, RL, false>;
+    auto kern = adj ? k_col_bulk<LF, RL, H, true> : k_col_bulk<LF, RL, H, false>;
     cudaError_t e = slots(kern, PB::CT, sm, &n_slots);
     if (e != cudaSuccess) return e;
     kern<<<std::min(items, n_slots), PB::CT, sm, s>>>(a, *static_cast<const CUtensorMap*>(a.tmap));
     return cudaGetLastError();
   }
-  static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
+  static cudaError_t col(const PassArgs& a, bool adj, cudaStream_t s) {
+    const size_t sm = PB::col_smem(a.n);
+    if (!a.tmap || a.in_r0 != 0 || a.in_r1 != a.n || a.n > 256 || sm > 227 * 1024)
+      return PassLaunch<LF>::col(a, adj, false, s);
+    return half(a) ? col_h<true>(a, adj, sm, s) : col_h<false>(a, adj, sm, s);
+  }
+  template <bool H>
+  static cudaError_t row_fwd_h(const PassArgs& a, bool save, cudaStream_t s) {
     const dim3 g((a.n + RL - 1) / RL, a.n_chunks);
     const size_t sm = PB::row_smem();
-    return save ? launch_k(k_row_bulk<LF, RL, false, true>, g, PB::RT, sm, a, s)
-                : launch_k(k_row_bulk<LF, RL, false, false>, g, PB::RT, sm, a, s);
+    return save ? launch_k(k_row_bulk<LF, RL, H, false, true>, g, PB::RT, sm, a, s)
+                : launch_k(k_row_bulk<LF, RL, H, false, false>, g, PB::RT, sm, a, s);
   }
-  static cudaError_t row_adj(const PassArgs& a, bool first, cudaStream_t s) {
+  static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
+    return half(a) ? row_fwd_h<true>(a, save, s) : row_fwd_h<false>(a, save, s);
+  }
+  template <bool H>
+  static cudaError_t row_adj_h(const PassArgs& a, bool first, cudaStream_t s) {
     const dim3 g((a.n + RL - 1) / RL, a.n_chunks);
     if (a.n % 2 == 0 && PB::adj_ck_smem(a.n) <= 227 * 1024) {
       const size_t sm = PB::adj_ck_smem(a.n);
-      return first ? launch_k(k_row_adj_ck<LF, RL, true>, g, PB::RT, sm, a, s)
-                   : launch_k(k_row_adj_ck<LF, RL, false>, g, PB::RT, sm, a, s);
+      return first ? launch_k(k_row_adj_ck<LF, RL, H, true>, g, PB::RT, sm, a, s)
+                   : launch_k(k_row_adj_ck<LF, RL, H, false>, g, PB::RT, sm, a, s);
     }
     const size_t sm = PB::row_smem();
-    return first ? launch_k(k_row_bulk<LF, RL, true, true>, g, PB::RT, sm, a, s)
-                 : launch_k(k_row_bulk<LF, RL, true, false>, g, PB::RT, sm, a, s);
+    return first ? launch_k(k_row_bulk<LF, RL, H, true, true>, g, PB::RT, sm, a, s)
+                 : launch_k(k_row_bulk<LF, RL, H, true, false>, g, PB::RT, sm, a, s);
+  }
+  static cudaError_t row_adj(const PassArgs& a, bool first, cudaStream_t s) {
+    return half(a) ? row_adj_h<true>(a, first, s) : row_adj_h<false>(a, first, s);
   }
 };
 
