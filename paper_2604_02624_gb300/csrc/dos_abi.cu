@@ -110,6 +110,9 @@ struct KernelTimer {
   }
 };
 
+// Multi-pass pass kinds that may run their bulk-prefetching kernels.
+constexpr unsigned kBulkCol = 1, kBulkRowFwd = 2, kBulkRowAdj = 4, kBulkAll = 7;
+
 struct dos_ctx {
   KernelTimer timer;
   int n = 0, m = 0, K = 0, nw = 0, nw_total = 0, fov = 0, ap = 0, of = 0, oa = 0, hs = 0;
@@ -137,14 +140,16 @@ struct dos_ctx {
   double* d_loss = nullptr;
   double* h_loss = nullptr;  // pinned
   int chunk = 1, n_chunks = 1;
-  bool bulk = false;       // multi-pass with bulk-async prefetch (DOS_PATH_MULTIPASS_BULK)
+  // multi-pass passes that run their bulk-async prefetching kernels
+  // (DOS_PATH_MULTIPASS_BULK: all three; the autotuner may mix them per kind)
+  unsigned bulk = 0;
   int* d_err = nullptr;    // set by a kernel whose bounded wait expired
   int* h_err = nullptr;    // pinned copy
   bool inject_stall = false;  // DOS_INJECT_WAIT_TIMEOUT: the next bulk pass stalls (tests)
   CUtensorMap tmap_S;        // S as [nw][n][m] 8-byte elements, box {col_lines, n, 1}
   bool have_tmap = false;     // the bulk column pass runs the plain kernel without it
-  int take_stall() {
-    const int v = (bulk && inject_stall) ? 1 : 0;
+  int take_stall(unsigned kind) {
+    const int v = ((bulk & kind) && inject_stall) ? 1 : 0;
     if (v) inject_stall = false;
     return v;
   }
@@ -623,9 +628,9 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
       a.fin = c->v1;
       DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_first(a, c->stream), "first row pass");
     } else {
-      a.stall = c->take_stall();
+      a.stall = c->take_stall(kBulkRowFwd);
       DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,
-                c->bulk ? op->bulk_row_fwd(a, save != 0, c->stream) : op->row_fwd(a, save != 0, c->stream),
+                (c->bulk & kBulkRowFwd) ? op->bulk_row_fwd(a, save != 0, c->stream) : op->row_fwd(a, save != 0, c->stream),
                 "forward row pass");
     }
     a.Hq = c->hq_slot(l);
@@ -634,9 +639,9 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
     a.in_r1 = c->n;
     a.out_r0 = l == c->K ? c->of : 0;
     a.out_r1 = l == c->K ? c->of + c->fov : c->n;
-    a.stall = c->take_stall();
+    a.stall = c->take_stall(kBulkCol);
     DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD,
-              c->bulk ? op->bulk_col(a, false, c->stream) : op->col(a, false, false, c->stream),
+              (c->bulk & kBulkCol) ? op->bulk_col(a, false, c->stream) : op->col(a, false, false, c->stream),
               "forward column pass");
     c->launches += 2;
   }
@@ -701,16 +706,16 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
     a.in_r1 = l == c->K ? c->of + c->fov : c->n;
     a.out_r0 = 0;
     a.out_r1 = c->n;
-    a.stall = c->take_stall();
+    a.stall = c->take_stall(kBulkCol);
     DOS_TIMED(c, DOS_KERNEL_COLUMN_ADJOINT,
-              c->bulk ? op->bulk_col(a, true, c->stream) : op->col(a, true, false, c->stream),
+              (c->bulk & kBulkCol) ? op->bulk_col(a, true, c->stream) : op->col(a, true, false, c->stream),
               "adjoint column pass");
     a.h = d_h + (size_t)(l - 1) * n2;
     a.ckpt = (l == 1 && c->ckpt1_is_v1) ? c->v1 : c->ckpt + (size_t)(l - 1) * c->nw * n2;
     a.partial = c->partial + (size_t)(l - 1) * c->n_chunks * n2;
-    a.stall = c->take_stall();
+    a.stall = c->take_stall(kBulkRowAdj);
     DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT,
-              c->bulk ? op->bulk_row_adj(a, l == 1, c->stream) : op->row_adj(a, l == 1, c->stream),
+              (c->bulk & kBulkRowAdj) ? op->bulk_row_adj(a, l == 1, c->stream) : op->row_adj(a, l == 1, c->stream),
               "adjoint row pass");
     c->launches += 2;
   }
@@ -722,13 +727,24 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
 }
 
 // ------------------------------------------------------------ autotuner
-// Choices of the autotuner: kPlain / kBulk (multi-pass without / with
-// bulk-async prefetch) or an index into the cluster-resident candidates.
-constexpr int kPlain = -2, kBulk = -1;
+// Choices of the autotuner: a multi-pass choice -1 - mask, where mask says
+// which pass kinds run their bulk-prefetching kernels (kPlain: none, kBulk:
+// all), or an index into the cluster-resident candidates.
+constexpr int kPlain = -1, kBulk = -1 - (int)kBulkAll;
+constexpr int multipass_choice(unsigned mask) { return -1 - (int)mask; }
+unsigned choice_mask(int idx) { return (unsigned)(-1 - idx); }
 
 std::string choice_name(const dos_ctx* x, int idx) {
   if (idx == kPlain) return "multipass";
   if (idx == kBulk) return "multipass:bulk";
+  if (idx < 0) {
+    const unsigned m = choice_mask(idx);
+    std::string s = "multipass:bulk[";
+    if (m & kBulkCol) s += "col";
+    if (m & kBulkRowFwd) s += std::string(s.back() == '[' ? "" : "+") + "row_fwd";
+    if (m & kBulkRowAdj) s += std::string(s.back() == '[' ? "" : "+") + "row_adj";
+    return s + "]";
+  }
   const dos::FusedOps* f = x->fcands[idx];
   return "fused:C" + std::to_string(f->C) + ":L" + std::to_string(f->lines);
 }
@@ -746,9 +762,9 @@ std::string tune_key(const dos_ctx* x) {
 
 
 void set_choice(dos_ctx* x, int idx) {
-  x->bulk = idx == kBulk;
+  x->bulk = idx < 0 ? choice_mask(idx) : 0;
   if (idx < 0) {
-    x->path = idx == kBulk ? DOS_PATH_MULTIPASS_BULK : DOS_PATH_MULTIPASS;
+    x->path = x->bulk ? DOS_PATH_MULTIPASS_BULK : DOS_PATH_MULTIPASS;
     x->fops = nullptr;
     x->n_clusters = 0;
   } else {
@@ -766,8 +782,11 @@ std::string choice_detail(const dos_ctx* x, int idx) {
   return d.str();
 }
 
-// time forward(save) + backward of the current choice on zero thickness / zero seed
-int time_choice(dos_ctx* x, const float* h0, const float* g0, float* d0, float* ms_out) {
+// time forward(save) + backward of the current choice on zero thickness / zero
+// seed; with kind_ms, one more forward + backward with per-launch events gives
+// the time of every kernel kind
+int time_choice(dos_ctx* x, const float* h0, const float* g0, float* d0, float* ms_out,
+                double* kind_ms = nullptr) {
   int rc;
   if ((rc = run_forward(x, h0, nullptr, 1)) || (rc = run_backward(x, h0, g0, d0))) return rc;
   cudaEvent_t a, b;
@@ -789,6 +808,25 @@ int time_choice(dos_ctx* x, const float* h0, const float* g0, float* d0, float* 
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (!rc && kind_ms) {
+    // the caller's accumulated times survive
+    cudaError_t e = x->timer.collect();
+    int count0[DOS_KERNEL_KINDS];
+    double ms0[DOS_KERNEL_KINDS];
+    const bool on0 = x->timer.on;
+    for (int k = 0; k < DOS_KERNEL_KINDS; ++k) count0[k] = x->timer.count[k], ms0[k] = x->timer.ms[k];
+    x->timer.reset();
+    x->timer.on = true;
+    if (e == cudaSuccess && !(rc = run_forward(x, h0, nullptr, 1))) rc = run_backward(x, h0, g0, d0);
+    if (e == cudaSuccess) e = x->timer.collect();
+    if (!rc && e != cudaSuccess) rc = fail(DOS_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(e));
+    for (int k = 0; k < DOS_KERNEL_KINDS; ++k) {
+      kind_ms[k] = x->timer.ms[k];
+      x->timer.count[k] = count0[k];
+      x->timer.ms[k] = ms0[k];
+    }
+    x->timer.on = on0;
+  }
   if (!rc) rc = err_check(x);
   *ms_out = best;
   return rc;
@@ -798,7 +836,7 @@ int choose_path(dos_ctx* x, int requested) {
   if (requested == DOS_PATH_DFT_GEMM || requested == DOS_PATH_DFT_GEMM_X3) {
     x->path = requested;
     x->fops = nullptr;
-    x->bulk = false;
+    x->bulk = 0;
     x->describe = std::string(requested == DOS_PATH_DFT_GEMM_X3 ? "path=dft_gemm_x3" : "path=dft_gemm") +
                   " chunk=" + std::to_string(x->gp.nwc) + " kp=" + std::to_string(x->gp.kp1) + "/" +
                   std::to_string(x->gp.kp2) + " rows=" + std::to_string(x->gp.rp1) + "/" + std::to_string(x->gp.rp2) +
@@ -830,15 +868,23 @@ int choose_path(dos_ctx* x, int requested) {
     x->describe = choice_detail(x, cands[0]) + " (only candidate)";
     return DOS_OK;
   }
+  // a choice by name: the candidates, and under auto every per-kind mix of
+  // plain and bulk-prefetching multi-pass kernels
+  auto by_name = [&](const std::string& name, int* out) {
+    for (int idx : cands)
+      if (choice_name(x, idx) == name) return *out = idx, true;
+    if (requested == DOS_PATH_AUTO)
+      for (unsigned m = 1; m < kBulkAll; ++m)
+        if (choice_name(x, multipass_choice(m)) == name) return *out = multipass_choice(m), true;
+    return false;
+  };
   // explicit override (profiling, reproducible benchmarks): a name as printed by dos_describe
   const char* force = std::getenv("DOS_FORCE_CONFIG");
-  if (force && *force) {
-    for (int idx : cands)
-      if (choice_name(x, idx) == force) {
-        set_choice(x, idx);
-        x->describe = choice_detail(x, idx) + " (DOS_FORCE_CONFIG)";
-        return DOS_OK;
-      }
+  int named = 0;
+  if (force && *force && by_name(force, &named)) {
+    set_choice(x, named);
+    x->describe = choice_detail(x, named) + " (DOS_FORCE_CONFIG)";
+    return DOS_OK;
   }
   // cached decision
   const char* cache = std::getenv("DOS_TUNE_CACHE");
@@ -849,12 +895,11 @@ int choose_path(dos_ctx* x, int requested) {
     while (std::getline(in, line)) {
       if (line.compare(0, key.size() + 1, key + "\t") != 0) continue;
       const std::string v = line.substr(key.size() + 1);
-      for (int idx : cands)
-        if (choice_name(x, idx) == v) {
-          set_choice(x, idx);
-          x->describe = choice_detail(x, idx) + " (tuning cache)";
-          return DOS_OK;
-        }
+      if (by_name(v, &named)) {
+        set_choice(x, named);
+        x->describe = choice_detail(x, named) + " (tuning cache)";
+        return DOS_OK;
+      }
     }
   }
   const size_t n2 = (size_t)x->n * x->n;
@@ -870,12 +915,24 @@ int choose_path(dos_ctx* x, int requested) {
   float best_ms = 1e30f;
   std::ostringstream d;
   d << "tuned (fwd+bwd ms):";
+  // per-kind times of the plain and the bulk-prefetching multi-pass kernels;
+  // a mix of the faster of each kind becomes one more candidate
+  double kind_plain[DOS_KERNEL_KINDS] = {0}, kind_bulk[DOS_KERNEL_KINDS] = {0};
   for (size_t k = 0; rc == DOS_OK && k < cands.size(); ++k) {
     const int idx = cands[k];
     set_choice(x, idx);
     float ms = 0.f;
-    rc = time_choice(x, h0, g0, d0, &ms);
+    rc = time_choice(x, h0, g0, d0, &ms, idx == kPlain ? kind_plain : idx == kBulk ? kind_bulk : nullptr);
     if (rc) break;
+    if (idx == kBulk && requested == DOS_PATH_AUTO) {
+      unsigned mix = 0;
+      if (kind_bulk[DOS_KERNEL_COLUMN_FORWARD] + kind_bulk[DOS_KERNEL_COLUMN_ADJOINT] <
+          kind_plain[DOS_KERNEL_COLUMN_FORWARD] + kind_plain[DOS_KERNEL_COLUMN_ADJOINT])
+        mix |= kBulkCol;
+      if (kind_bulk[DOS_KERNEL_ROW_FORWARD] < kind_plain[DOS_KERNEL_ROW_FORWARD]) mix |= kBulkRowFwd;
+      if (kind_bulk[DOS_KERNEL_ROW_ADJOINT] < kind_plain[DOS_KERNEL_ROW_ADJOINT]) mix |= kBulkRowAdj;
+      if (mix != 0 && mix != kBulkAll) cands.insert(cands.begin() + k + 1, multipass_choice(mix));
+    }
     d << " " << choice_name(x, idx);
     if (idx >= 0) d << "x" << x->fcand_clusters[idx];
     d << "=" << ms;

@@ -363,9 +363,12 @@ struct Pass {
 // two; the column pass is faster with its own register allocation).
 template <class LF>
 constexpr int pass_min_blocks() { return LF::E <= 20 ? 3 : 1; }
+// column pass: the halved kernel fits three blocks per SM without spills
+template <class LF, bool HALF>
+constexpr int col_min_blocks() { return HALF && LF::M == 400 ? 3 : 0; }
 
 template <class LF, bool HALF, bool ADJ, bool APERTURE>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL) k_col(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, col_min_blocks<LF, HALF>()) k_col(PassArgs a) {
   Pass<LF, HALF>::template col<ADJ, APERTURE>(a);
 }
 template <class LF, bool HALF, bool SAVE>
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_seed(PassArgs a)
   Pass<LF, HALF>::row_seed(a);
 }
 template <class LF, bool HALF, bool FIRST>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_adj(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, col_min_blocks<LF, HALF>()) k_row_adj(PassArgs a) {
   Pass<LF, HALF>::template row_adj<FIRST>(a);
 }
 template <class LF, bool HALF>

@@ -444,6 +444,28 @@ def test_forced_configuration_and_tuning_cache(tmp_path, monkeypatch):
     st.close()
 
 
+@pytest.mark.parametrize("mix", ["col", "row_fwd", "row_adj", "col+row_fwd", "col+row_adj", "row_fwd+row_adj"])
+def test_mixed_multipass_kernels_match_oracle(monkeypatch, mix):
+    """Under auto the tuner may run plain kernels for some pass kinds and the
+    bulk-prefetching ones for the others; each mix is reachable by name and
+    computes the oracle's field and gradient."""
+    w = custom(100, 200, 3, [480, 610, 720], 30, 50, name="mixed")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    monkeypatch.setenv("DOS_FORCE_CONFIG", f"multipass:bulk[{mix}]")
+    st = _stack(w, path="auto")
+    assert st.path == "multipass_bulk" and f"bulk[{mix}]" in L.dos_describe(st.handle)
+    hd = _t(h)
+    st.forward(hd)
+    o = st.output_field()
+    _, _, dl = st.loss(_t(T))
+    g = _np(st.backward(hd, dl)).astype(np.float64)
+    L_ref, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    assert rel_l2(_np(o).astype(np.complex128), fwd["o"]) <= TOL_FIELD
+    assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
+    st.close()
+
+
 @pytest.mark.parametrize("path", ["dft_gemm", "dft_gemm_x3"])
 @pytest.mark.parametrize("n,m,k", [(50, 128, 2), (7, 16, 1), (100, 200, 3)])
 def test_split_bf16_ragged_shapes(path, n, m, k):
