@@ -37,6 +37,39 @@ DOS_HD float2 cmulc(float2 a, float2 b) {
 DOS_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 DOS_HD float2 czero() { return make_float2(0.f, 0.f); }
 
+// Complex add / subtract as one packed FP32-pair instruction (add/sub.f32x2 of
+// the sm_100 family) when PK is set, as two scalar ones otherwise.  Packed
+// operands are opaque to the compiler (no folding of known zeros), so only the
+// unpruned butterflies use them.
+template <bool PK>
+DOS_HD float2 vadd(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (PK) {
+    float2 d;
+    asm("{\n .reg .b64 pa, pb, pd;\n mov.b64 pa, {%2, %3};\n mov.b64 pb, {%4, %5};\n"
+        " add.rn.f32x2 pd, pa, pb;\n mov.b64 {%0, %1}, pd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+  }
+#endif
+  return cadd(a, b);
+}
+template <bool PK>
+DOS_HD float2 vsub(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (PK) {
+    float2 d;
+    asm("{\n .reg .b64 pa, pb, pd;\n mov.b64 pa, {%2, %3};\n mov.b64 pb, {%4, %5};\n"
+        " sub.rn.f32x2 pd, pa, pb;\n mov.b64 {%0, %1}, pd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+  }
+#endif
+  return csub(a, b);
+}
+
 // ------------------------------------------------- compile-time trigonometry
 namespace ct {
 constexpr double kPi = 3.14159265358979323846264338327950288;
@@ -120,49 +153,49 @@ DOS_HD float2 twiddle(float2 x) {
 }
 
 // ------------------------------------------------------------- butterflies
-template <bool INV>
+template <bool INV, bool PK = false>
 DOS_HD void bfly2(float2* x) {
   const float2 a = x[0], b = x[1];
-  x[0] = cadd(a, b);
-  x[1] = csub(a, b);
+  x[0] = vadd<PK>(a, b);
+  x[1] = vsub<PK>(a, b);
 }
-template <bool INV>
+template <bool INV, bool PK = false>
 DOS_HD void bfly3(float2* x) {
   constexpr float c = -0.5f;
   constexpr float s = INV ? 0.86602540378443864676f : -0.86602540378443864676f;
-  const float2 t = cadd(x[1], x[2]);
-  const float2 d = csub(x[1], x[2]);
+  const float2 t = vadd<PK>(x[1], x[2]);
+  const float2 d = vsub<PK>(x[1], x[2]);
   const float2 m = make_float2(fmaf(c, t.x, x[0].x), fmaf(c, t.y, x[0].y));
-  x[0] = cadd(x[0], t);
+  x[0] = vadd<PK>(x[0], t);
   // j*s*d
   const float2 jd = make_float2(-s * d.y, s * d.x);
   x[1] = cadd(m, jd);
   x[2] = csub(m, jd);
 }
-template <bool INV>
+template <bool INV, bool PK = false>
 DOS_HD void bfly4(float2* x) {
-  const float2 t0 = cadd(x[0], x[2]);
-  const float2 t1 = csub(x[0], x[2]);
-  const float2 t2 = cadd(x[1], x[3]);
-  const float2 d = csub(x[1], x[3]);
+  const float2 t0 = vadd<PK>(x[0], x[2]);
+  const float2 t1 = vsub<PK>(x[0], x[2]);
+  const float2 t2 = vadd<PK>(x[1], x[3]);
+  const float2 d = vsub<PK>(x[1], x[3]);
   // forward: -j*d, inverse: +j*d
   const float2 t3 = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
-  x[0] = cadd(t0, t2);
-  x[2] = csub(t0, t2);
+  x[0] = vadd<PK>(t0, t2);
+  x[2] = vsub<PK>(t0, t2);
   x[1] = cadd(t1, t3);
   x[3] = csub(t1, t3);
 }
-template <bool INV>
+template <bool INV, bool PK = false>
 DOS_HD void bfly5(float2* x) {
   constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
   constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
   constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
   constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
   const float2 x0 = x[0];
-  const float2 t1 = cadd(x[1], x[4]);
-  const float2 t2 = cadd(x[2], x[3]);
-  const float2 t3 = csub(x[1], x[4]);
-  const float2 t4 = csub(x[2], x[3]);
+  const float2 t1 = vadd<PK>(x[1], x[4]);
+  const float2 t2 = vadd<PK>(x[2], x[3]);
+  const float2 t3 = vsub<PK>(x[1], x[4]);
+  const float2 t4 = vsub<PK>(x[2], x[3]);
   const float2 a1 = make_float2(fmaf(c2, t2.x, fmaf(c1, t1.x, x0.x)), fmaf(c2, t2.y, fmaf(c1, t1.y, x0.y)));
   const float2 a2 = make_float2(fmaf(c1, t2.x, fmaf(c2, t1.x, x0.x)), fmaf(c1, t2.y, fmaf(c2, t1.y, x0.y)));
   const float2 b1 = make_float2(fmaf(s2, t4.x, s1 * t3.x), fmaf(s2, t4.y, s1 * t3.y));
@@ -170,7 +203,7 @@ DOS_HD void bfly5(float2* x) {
   // forward: X1 = a1 - j b1, X4 = a1 + j b1, X2 = a2 - j b2, X3 = a2 + j b2
   const float2 jb1 = INV ? make_float2(-b1.y, b1.x) : make_float2(b1.y, -b1.x);
   const float2 jb2 = INV ? make_float2(-b2.y, b2.x) : make_float2(b2.y, -b2.x);
-  x[0] = make_float2(x0.x + t1.x + t2.x, x0.y + t1.y + t2.y);
+  x[0] = vadd<PK>(vadd<PK>(x0, t1), t2);
   x[1] = cadd(a1, jb1);
   x[4] = csub(a1, jb1);
   x[2] = cadd(a2, jb2);
@@ -194,7 +227,7 @@ DOS_HD void dft_direct(float2* x) {
 }
 
 // N-point DFT in registers; only x[0..NZ) are read, only X[0..NO) are produced.
-template <int N, bool INV, int NZ = N, int NO = N>
+template <int N, bool INV, int NZ = N, int NO = N, bool PK = false>
 DOS_HD void dft(float2* x) {
   static_assert(NZ >= 0 && NZ <= N && NO >= 0 && NO <= N, "bad pruning");
   if constexpr (N == 1 || NO == 0) {
@@ -208,10 +241,11 @@ DOS_HD void dft(float2* x) {
       dft_direct<N, INV, NZ, NO>(x);
     } else {
       if constexpr (NZ < N) static_for<NZ, N>([&](auto k) { x[k] = czero(); });
-      if constexpr (N == 2) bfly2<INV>(x);
-      else if constexpr (N == 3) bfly3<INV>(x);
-      else if constexpr (N == 4) bfly4<INV>(x);
-      else bfly5<INV>(x);
+      constexpr bool pk = PK && NZ == N;  // zero inputs fold only in scalar form
+      if constexpr (N == 2) bfly2<INV, pk>(x);
+      else if constexpr (N == 3) bfly3<INV, pk>(x);
+      else if constexpr (N == 4) bfly4<INV, pk>(x);
+      else bfly5<INV, pk>(x);
     }
   } else {
     // N = A*B; input n = B*a + b, output k = k1 + A*k2.
@@ -226,7 +260,7 @@ DOS_HD void dft(float2* x) {
       if constexpr (nza > 0) {
         float2 t[A];
         static_for<0, nza>([&](auto aa) { t[aa] = x[B * aa + b]; });
-        dft<A, INV, nza, NOA>(t);
+        dft<A, INV, nza, NOA, PK>(t);
         static_for<0, NOA>([&](auto kk) {
           constexpr int k1 = kk;
           y[b * A + k1] = twiddle<N, (long)b * k1, INV>(t[k1]);
@@ -239,7 +273,7 @@ DOS_HD void dft(float2* x) {
       if constexpr (nob > 0) {
         float2 t[B];
         static_for<0, NZB>([&](auto bb) { t[bb] = y[bb * A + k1]; });
-        dft<B, INV, NZB, nob>(t);
+        dft<B, INV, NZB, nob, PK>(t);
         static_for<0, nob>([&](auto k2) { x[k1 + A * k2] = t[k2]; });
       }
     });
@@ -264,13 +298,13 @@ struct Line {
   // Step 1: the Q/T sub-DFTs of length P owned by thread t (q = t + T*j),
   // twiddled and written to the exchange matrix z[q][k1].
   // NZP: leading non-zero inputs of each sub-DFT (zero padding).
-  template <bool INV, int NZP = P>
+  template <bool INV, int NZP = P, bool PK = false>
   DOS_HD static void step1(const float2 (&r)[E], int t, float2* z, const float2* tw) {
     static_for<0, QJ>([&](auto jj) {
       constexpr int j = jj;
       float2 a[P];
       static_for<0, NZP>([&](auto pp) { a[pp] = r[j + QJ * pp]; });
-      dft<P, INV, NZP, P>(a);
+      dft<P, INV, NZP, P, PK>(a);
       const int q = t + T * j;
       const float2* twq = tw + q * RP;
       float2* zq = z + q * RP;
@@ -284,25 +318,26 @@ struct Line {
   // Step 2: the P/T sub-DFTs of length Q owned by thread t (k1 = t + T*j),
   // read as columns of z; outputs k1 + P*k2 land in r[j + (P/T)*k2].
   // NOQ: leading outputs of each sub-DFT that are needed (cropping).
-  template <bool INV, int NOQ = Q>
+  template <bool INV, int NOQ = Q, bool PK = false>
   DOS_HD static void step2(float2 (&r)[E], int t, const float2* z) {
     static_for<0, PJ>([&](auto jj) {
       constexpr int j = jj;
       const int k1 = t + T * j;
       float2 b[Q];
       static_for<0, Q>([&](auto qq) { b[qq] = z[qq * RP + k1]; });
-      dft<Q, INV, Q, NOQ>(b);
+      dft<Q, INV, Q, NOQ, PK>(b);
       static_for<0, NOQ>([&](auto k2) { r[j + PJ * k2] = b[k2]; });
     });
   }
   // TRAIL: end with a barrier so that z may be rewritten right away; callers
   // that next write a different buffer (and reach another barrier before
   // reusing z) pass false.
-  template <bool INV, int NZP = P, int NOQ = Q, bool TRAIL = true>
+  // PK: the unpruned butterflies add and subtract in packed FP32 pairs
+  template <bool INV, int NZP = P, int NOQ = Q, bool TRAIL = true, bool PK = false>
   __device__ static __forceinline__ void fft(float2 (&r)[E], int t, float2* z, const float2* tw) {
-    step1<INV, NZP>(r, t, z, tw);
+    step1<INV, NZP, PK>(r, t, z, tw);
     __syncthreads();
-    step2<INV, NOQ>(r, t, z);
+    step2<INV, NOQ, PK>(r, t, z);
     if constexpr (TRAIL) __syncthreads();
   }
 };

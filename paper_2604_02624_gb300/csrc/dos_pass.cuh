@@ -63,6 +63,11 @@ struct Pass {
   static constexpr int NOI = HALF ? LF::Q / 2 : LF::Q;  // inverse DFT to a field: outputs kept per sub-DFT
   static constexpr int EF = HALF ? E / 2 : E;           // field-domain elements of a thread
   static_assert(!HALF || (LF::P % 2 == 0 && LF::Q % 2 == 0), "halving needs even factors");
+  // Packed FP32-pair butterflies (Line::fft's PK) where they measured faster
+  // on the 400-point line: the row passes but the adjoint one (PKA) and not
+  // this column pass (PKC), whose three-blocks-per-SM register budget they
+  // overflow.
+  static constexpr bool PKR = true, PKA = false, PKC = false;
   static constexpr int ROWL = 16;  // rows per block in the row passes
   static constexpr int COLL = 16;  // columns per block in the column pass
   // column pass: line = tid % COLL, an odd stride keeps the lines apart
@@ -102,7 +107,7 @@ struct Pass {
         const int row = t + T * i;
         r[i] = (i < EF && ok && row >= a.in_r0 && row < a.in_r1) ? src[(size_t)row * M] : czero();
       }
-      LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
+      LF::template fft<false, NZF, LF::Q, true, PKC>(r, t, z, tw);
     }
     const float2* Hw = a.Hq + (size_t)w * a.hs * a.hs;
     const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
@@ -115,7 +120,7 @@ struct Pass {
       if (Sw) hv = cmul(hv, misalign_factor(a.mis, k, cc, M, Sw[qi]));
       r[i] = ADJ ? cmulc(r[i], hv) : cmul(r[i], hv);
     }
-    LF::template fft<true, LF::P, NOI>(r, t, z, tw);
+    LF::template fft<true, LF::P, NOI, true, PKC>(r, t, z, tw);
     float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -154,7 +159,7 @@ struct Pass {
     float2 r[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-    LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
+    LF::template fft<true, LF::P, NOI, true, PKR>(r, t, rc.z, rc.tw);
     const ChanConst cc = a.chan[w];
     const float* hrow = a.h + (size_t)rr * a.n;
     float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
@@ -169,7 +174,7 @@ struct Pass {
         r[i] = czero();
       }
     }
-    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, rc.z, rc.tw);
     if (ok) {
 #pragma unroll
       for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -195,7 +200,7 @@ struct Pass {
       const int x = t + T * i;
       r[i] = (i < EF && x < a.n) ? cmul(transmission(hrow[x], cc), vrow[x]) : czero();
     }
-    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* srow = a.S + ((size_t)w * a.n + row) * M;
 #pragma unroll
@@ -215,7 +220,7 @@ struct Pass {
     float2 r[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-    LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
+    LF::template fft<true, LF::P, NOI, true, PKR>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* orow = a.o + ((size_t)w * a.fov + fr) * a.fov;
       float* irow = a.I ? a.I + ((size_t)w * a.fov + fr) * a.fov : nullptr;
@@ -246,7 +251,7 @@ struct Pass {
       const int x = t + T * i - a.of;
       r[i] = (i < EF && ok && x >= 0 && x < a.fov) ? cscale(orow[x], 2.0f * grow[x]) : czero();
     }
-    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* srow = a.S + ((size_t)w * a.n + a.of + fr) * M;
 #pragma unroll
@@ -277,7 +282,7 @@ struct Pass {
       float2 r[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-      LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
+      LF::template fft<true, LF::P, NOI, true, PKA>(r, t, rc.z, rc.tw);
       const ChanConst cc = a.chan[w];
 #pragma unroll
       for (int i = 0; i < E; ++i) {
@@ -293,7 +298,7 @@ struct Pass {
         }
       }
       if constexpr (!FIRST) {
-        LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
+        LF::template fft<false, NZF, LF::Q, true, PKA>(r, t, rc.z, rc.tw);
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -325,7 +330,7 @@ struct Pass {
       const int x = t + T * i;
       r[i] = (i < EF && x < a.n) ? frow[x] : czero();
     }
-    LF::template fft<false, NZF, LF::Q>(r, t, rc.z, rc.tw);
+    LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* srow = a.S + ((size_t)w * a.n + row) * M;
 #pragma unroll
@@ -345,7 +350,7 @@ struct Pass {
     float2 r[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-    LF::template fft<true, LF::P, NOI>(r, t, rc.z, rc.tw);
+    LF::template fft<true, LF::P, NOI, true, PKR>(r, t, rc.z, rc.tw);
     if (ok) {
       float2* frow = a.fout + ((size_t)w * a.n + row) * a.n;
 #pragma unroll

@@ -80,6 +80,9 @@ template <class LF, int RL, bool HALF = false>
 struct PassBulk {
   static constexpr int T = LF::T, E = LF::E, M = LF::M;
   static constexpr int NZF = Pass<LF, HALF>::NZF, NOI = Pass<LF, HALF>::NOI, EF = Pass<LF, HALF>::EF;
+  // packed FP32-pair butterflies in every bulk pass (faster than scalar ones
+  // in each of them on the 400-point line)
+  static constexpr bool PKR = true, PKC = true;
   static constexpr int COLL = Pass<LF>::COLL, ZL = Pass<LF>::ZL, RZL = Pass<LF>::RZL;
   static constexpr int SR = row_stage_stride(M);  // even: every staged row starts 16-byte aligned
   static_assert(SR % 2 == 0 && SR >= M, "staged rows must be 16-byte aligned and hold M values");
@@ -157,7 +160,7 @@ struct PassBulk {
           hv[i] = __ldg(Hw + (size_t)min(kk, M - kk) * a.hs + bc);
         }
       }
-      LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
+      LF::template fft<false, NZF, LF::Q, true, PKC>(r, t, z, tw);
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         float2 h;
@@ -173,7 +176,7 @@ struct PassBulk {
         }
         r[i] = ADJ ? cmulc(r[i], h) : cmul(r[i], h);
       }
-      LF::template fft<true, LF::P, NOI>(r, t, z, tw);
+      LF::template fft<true, LF::P, NOI, true, PKC>(r, t, z, tw);
       float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
@@ -249,7 +252,7 @@ struct PassBulk {
       for (int i = 0; i < E; ++i) r[i] = stage[(size_t)(ok ? l : 0) * SR + t + T * i];
       __syncthreads();  // stage consumed: the next channel may land in it
       if (w + 1 < w1) fetch(w + 1);
-      LF::template fft<true, LF::P, NOI>(r, t, z, tw);
+      LF::template fft<true, LF::P, NOI, true, PKR>(r, t, z, tw);
       float2* srow = a.S + ((size_t)w * a.n + rr) * M;
       if constexpr (!ADJ) {
         float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
@@ -264,7 +267,7 @@ struct PassBulk {
             r[i] = czero();
           }
         }
-        LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
+        LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -285,7 +288,7 @@ struct PassBulk {
           }
         }
         if constexpr (!FLAG) {
-          LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
+          LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
           if (ok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -376,7 +379,7 @@ struct PassBulk {
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
       const ChanConst cc = a.chan[w];
-      LF::template fft<true, LF::P, NOI>(r, t, z, tw);
+      LF::template fft<true, LF::P, NOI, true, PKR>(r, t, z, tw);
       if (!bulk_wait(&bar[b], (uint32_t)((k >> 1) & 1))) okw = false;
       if (!__syncthreads_and(okw)) break;
       const float2* ck = ckb + ((size_t)b * RL + (ok ? l : 0)) * cks;
@@ -394,7 +397,7 @@ struct PassBulk {
         }
       }
       if constexpr (!FIRST) {
-        LF::template fft<false, NZF, LF::Q>(r, t, z, tw);
+        LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
