@@ -147,7 +147,8 @@ struct dos_ctx {
   int* h_err = nullptr;    // pinned copy
   bool inject_stall = false;  // DOS_INJECT_WAIT_TIMEOUT: the next bulk pass stalls (tests)
   CUtensorMap tmap_S;        // S as [nw][n][m] 8-byte elements, box {col_lines, n, 1}
-  bool have_tmap = false;     // the bulk column pass runs the plain kernel without it
+  CUtensorMap tmap_F;        // the same with box {col_lines, fov, 1}: the adjoint's first column pass
+  bool have_tmap = false;     // the bulk column pass runs the plain kernel without them
   int take_stall(unsigned kind) {
     const int v = ((bulk & kind) && inject_stall) ? 1 : 0;
     if (v) inject_stall = false;
@@ -239,6 +240,7 @@ struct dos_ctx {
     a.n_chunks = n_chunks;
     a.err = d_err;
     a.tmap = have_tmap ? &tmap_S : nullptr;
+    a.tmap_rows = n;
     return a;
   }
 };
@@ -292,7 +294,8 @@ int choose_path(dos_ctx* x, int requested);
 
 // Tensor map of the row spectra S for the bulk column pass: [nw][n][m]
 // elements of 8 bytes (complex64 moved as opaque 64-bit words), box
-// {col_lines columns, n rows, 1 channel}, columns past m read as zeros.
+// {col_lines columns, n rows, 1 channel} (tmap_S) or {col_lines, fov, 1}
+// (tmap_F), columns past m read as zeros.
 // A driver without the entry point leaves the plain column kernel in use.
 int make_spectra_map(dos_ctx* x) {
   x->have_tmap = false;
@@ -306,12 +309,18 @@ int make_spectra_map(dos_ctx* x) {
   }
   const cuuint64_t dims[3] = {(cuuint64_t)x->m, (cuuint64_t)x->n, (cuuint64_t)x->nw};
   const cuuint64_t strides[2] = {(cuuint64_t)x->m * 8, (cuuint64_t)x->n * x->m * 8};
-  const cuuint32_t box[3] = {(cuuint32_t)x->ops->col_lines, (cuuint32_t)x->n, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
-      &x->tmap_S, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, x->S, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(DOS_ERR_CUDA, "cuTensorMapEncodeTiled(row spectra) failed: " + std::to_string((int)r));
+  const int box_rows[2] = {x->n, x->fov};
+  CUtensorMap* maps[2] = {&x->tmap_S, &x->tmap_F};
+  for (int i = 0; i < 2; ++i) {  // both are encoded, also when fov == n
+    const cuuint32_t box[3] = {(cuuint32_t)x->ops->col_lines, (cuuint32_t)box_rows[i], 1};
+    const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
+        maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, x->S, dims, strides, box, estr,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(DOS_ERR_CUDA, "cuTensorMapEncodeTiled(row spectra) failed: " + std::to_string((int)r));
+  }
   x->have_tmap = true;
   return DOS_OK;
 }
@@ -704,6 +713,8 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
     a.mis = c->gap_mis(l);
     a.in_r0 = l == c->K ? c->of : 0;
     a.in_r1 = l == c->K ? c->of + c->fov : c->n;
+    a.tmap = !c->have_tmap ? nullptr : l == c->K ? &c->tmap_F : &c->tmap_S;
+    a.tmap_rows = l == c->K ? c->fov : c->n;
     a.out_r0 = 0;
     a.out_r1 = c->n;
     a.stall = c->take_stall(kBulkCol);

@@ -64,6 +64,7 @@ struct PassArgs {
   int* err;               // set to 1 by a bulk-copy pass whose bounded wait expired
   int stall;              // fault injection: bulk passes expect bytes that are never copied
   const void* tmap;       // host CUtensorMap of S as [nw][n][m] 8-byte elements (bulk column pass), or null
+  int tmap_rows;          // rows of its box: the bulk column pass uses it when they are in_r1 - in_r0
 };
 
 // Kernel launchers of one padded size M (one translation unit per M).

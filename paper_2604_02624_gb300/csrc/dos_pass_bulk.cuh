@@ -87,6 +87,7 @@ struct PassBulk {
   static constexpr int SR = row_stage_stride(M);  // even: every staged row starts 16-byte aligned
   static_assert(SR % 2 == 0 && SR >= M, "staged rows must be 16-byte aligned and hold M values");
   static_assert(Pass<LF>::RZL >= LF::ZS, "exchange buffers must not overlap");
+  static_assert(Pass<LF>::COLL * 8 % 128 == 0, "a tensor copy into stage row in_r0 must start 128-byte aligned");
   static constexpr int CT = T * COLL, RT = T * RL;
   static constexpr bool EARLY_H = E <= 20;  // registers allow the H values in flight
 
@@ -97,8 +98,11 @@ struct PassBulk {
     return 128 + sizeof(float2) * ((size_t)n * COLL + (size_t)COLL * ZL + LF::ZS) + sizeof(uint64_t);
   }
 
-  // All N rows of every column tile are fetched by one tensor copy of the box
-  // {COLL columns, N rows, 1 channel} (columns past M read as zeros).
+  // The input rows [in_r0, in_r1) of every column tile (all N rows, or the
+  // field of view in the adjoint's first pass) are fetched by one tensor copy
+  // of the box {COLL columns, in_r1 - in_r0 rows, 1 channel} to their own rows
+  // of the stage (a row is COLL * 8 = 128 bytes, so every start stays 128-byte
+  // aligned); columns past M read as zeros.
   template <bool ADJ>
   __device__ static void col(const PassArgs& a, const CUtensorMap* map) {
     extern __shared__ __align__(16) unsigned char col_raw[];
@@ -110,7 +114,7 @@ struct PassBulk {
     float2* z = zb + l * ZL;
     constexpr int ntiles = (M + COLL - 1) / COLL;
     const int items = a.nw * ntiles;
-    const uint32_t bytes = (uint32_t)(COLL * 8) * (uint32_t)a.n;
+    const uint32_t bytes = (uint32_t)(COLL * 8) * (uint32_t)(a.in_r1 - a.in_r0);
     if (threadIdx.x == 0) {
       bulk_bar_init(bar);
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -125,8 +129,8 @@ struct PassBulk {
       const int w = it / ntiles, c0 = (it % ntiles) * COLL;
       asm volatile(
           "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-          "[%5];" ::"r"(sh_addr(stage)),
-          "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(0), "r"(w), "r"(sh_addr(bar))
+          "[%5];" ::"r"(sh_addr(stage + (size_t)a.in_r0 * COLL)),
+          "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(a.in_r0), "r"(w), "r"(sh_addr(bar))
           : "memory");
     };
     bool ok = true;
@@ -143,7 +147,7 @@ struct PassBulk {
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int row = t + T * i;
-        r[i] = (i < EF && row < a.n) ? stage[(size_t)row * COLL + l] : czero();
+        r[i] = (i < EF && row >= a.in_r0 && row < a.in_r1) ? stage[(size_t)row * COLL + l] : czero();
       }
       __syncthreads();  // stage consumed: the next item may land in it
       if (it + (int)gridDim.x < items) fetch(it + gridDim.x);
@@ -458,9 +462,8 @@ struct PassBulkLaunch {
     *out = std::max(1, per_sm) * sms;
     return cudaSuccess;
   }
-  // The tensor copy needs every row [0, N) as input and N <= 256 (one box);
-  // other column passes (the adjoint's first, FOV-rows-only gap) run the
-  // plain kernel.
+  // The tensor copy needs a map whose box holds the input rows (at most 256);
+  // without one the plain kernel runs.
   static bool half(const PassArgs& a) { return 2 * a.n <= LF::M; }
   template <bool H>
   static cudaError_t col_h(const PassArgs& a, bool adj, size_t sm, cudaStream_t s) {
@@ -475,7 +478,7 @@ struct PassBulkLaunch {
   }
   static cudaError_t col(const PassArgs& a, bool adj, cudaStream_t s) {
     const size_t sm = PB::col_smem(a.n);
-    if (!a.tmap || a.in_r0 != 0 || a.in_r1 != a.n || a.n > 256 || sm > 227 * 1024)
+    if (!a.tmap || a.tmap_rows != a.in_r1 - a.in_r0 || a.tmap_rows > 256 || sm > 227 * 1024)
       return PassLaunch<LF>::col(a, adj, false, s);
     return half(a) ? col_h<true>(a, adj, sm, s) : col_h<false>(a, adj, sm, s);
   }
