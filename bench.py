@@ -29,12 +29,30 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) per channel of one launch of a kernel, from one ncu
-# capture of the same build on the 256-channel design, keyed by (path, N, M,
-# kernel kind); the bench scales them to the launch's channels.  An entry must
-# be removed (traffic reported as null) when its kernel changes.
+# DRAM bytes (read + write) per channel of one launch of a kernel kind (the
+# average over the kind's launches of a step), from ncu captures of the same
+# build on the 256-channel design, keyed by (kernel family, N, M, kernel kind);
+# the bench scales them to the launch's channels.  An entry must be removed
+# (traffic reported as null) when its kernel changes.
 TRAFFIC_PER_CHANNEL = {
+    # TMA column pass with packed butterflies: forward 1.3986 MB; adjoint 0.9130 MB
+    # (first gap, field-of-view input rows) and 1.4007 MB (the other K - 1 gaps)
+    ("column_bulk", 200, 400, "column_forward"): (1.398564e6, "profiles/column_pass_bulk_batched.md"),
+    ("column_bulk", 200, 400, "column_adjoint"): ((0.912978e6 + 4 * 1.400745e6) / 5,
+                                                  "profiles/column_pass_bulk_batched.md"),
 }
+
+
+def kernel_family(detail, kind):
+    """Which kernel of a multi-pass kind ran: 'column_bulk' / 'column_plain'
+    for the column passes, from the configuration name dos_describe prints
+    (multipass, multipass:bulk or multipass:bulk[col+...])."""
+    name = detail.split("|")[0].strip().split()[0].removeprefix("path=")
+    if not kind.startswith("column") or not name.startswith("multipass"):
+        return None
+    bulk = name == "multipass:bulk" or (name.startswith("multipass:bulk[") and "col" in name)
+    return "column_bulk" if bulk else "column_plain"
+
 
 METRIC = "lambda-channel layer-propagations/s (fwd+adjoint, 4096 lambda)"
 UNIT = "propagations/s"
@@ -287,7 +305,8 @@ def run_ours(a):
     # algorithmic bytes per launch (every channel once): complex64 = 8 B
     algo = {
         "column_forward": nw * (16 * n * m + 8 * hs * hs),
-        "column_adjoint": nw * (16 * n * m + 8 * hs * hs),
+        # the adjoint's first column pass reads only the F field-of-view rows
+        "column_adjoint": nw * ((K - 1) * (16 * n * m + 8 * hs * hs) + (8 * F * m + 8 * n * m + 8 * hs * hs)) / K,
         "row_forward": nw * (16 * n * m + 8 * n * n),
         "row_adjoint": nw * (16 * n * m + 8 * n * n),
         # fused sweeps: checkpoints, transfer table, output field / seed
@@ -311,7 +330,7 @@ def run_ours(a):
                 "algorithmic_bytes_per_launch": algo, "ms_per_launch": per_launch_ms, "launches": n_l}
     elif algo:
         ach = algo / (per_launch_ms * 1e-3) / 1e9
-        tr = TRAFFIC_PER_CHANNEL.get((stack.path, w.n, w.m, dom))
+        tr = TRAFFIC_PER_CHANNEL.get((kernel_family(L.dos_describe(stack.handle), dom), w.n, w.m, dom))
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "peak_source": peak_src,
                 "traffic": tr[0] * nw if tr else None,
