@@ -425,6 +425,145 @@ struct PassBulk {
       }
     }
   }
+
+  // ------------------------------------------- adjoint row pass, both inputs staged
+  // Both inputs of a channel arrive by bulk copies: its spectra rows (into a
+  // stage that is emptied into registers at the top of the iteration, so the
+  // next channel's copy overlaps the whole iteration) and its checkpoint rows
+  // (read after the inverse DFT; the next channel's copy is issued as soon as
+  // every thread is past them, at the barrier inside the forward DFT).  With
+  // few rows per block three blocks fit on an SM.  Needs N even.
+  // dynamic shared memory: stage[RL][SR] | ck[RL][cks] | exchange[RL][RZL] | tw[ZS] | barrier[2]
+  static size_t adj_staged_smem(int n) {
+    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS) +
+           2 * sizeof(uint64_t);
+  }
+
+  template <bool FIRST>
+  __device__ static void row_adj_staged(const PassArgs& a) {
+    extern __shared__ __align__(16) float2 smem[];
+    const int cks = ck_stride(a.n);
+    float2* stage = smem;
+    float2* ckb = stage + (size_t)RL * SR;
+    float2* zb = ckb + (size_t)RL * cks;
+    float2* tw = zb + (size_t)RL * RZL;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);  // [0] spectra rows, [1] checkpoint rows
+    const int l = threadIdx.x / T, t = threadIdx.x % T;
+    float2* z = zb + l * RZL;
+    const int r0 = blockIdx.x * RL;
+    const int nrows = min(RL, a.n - r0);
+    const int row = r0 + l;
+    const bool ok = l < nrows;
+    const int rr = ok ? row : r0;
+    const int lr = ok ? l : 0;
+    const int w0 = blockIdx.y * a.chunk;
+    const int w1 = min(a.nw, w0 + a.chunk);
+    if (threadIdx.x == 0) {
+      bulk_bar_init(&bar[0]);
+      bulk_bar_init(&bar[1]);
+    }
+    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    __syncthreads();
+    // thread 0 copies the block's rows of channel w: spectra (M * 8 bytes a
+    // row) into the stage, checkpoint (N * 8 bytes a row) into ck
+    auto fetch_s = [&](int w) {
+      if (threadIdx.x != 0) return;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(&bar[0], (uint32_t)nrows * M * 8u);
+      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      const float2* src = a.S + ((size_t)w * a.n + r0) * M;
+      for (int q = 0; q < nrows; ++q) bulk_g2s(stage + (size_t)q * SR, src + (size_t)q * M, M * 8u, &bar[0]);
+    };
+    auto fetch_c = [&](int w) {
+      if (threadIdx.x != 0) return;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(&bar[1], (uint32_t)nrows * a.n * 8u);
+      if (a.stall) return;
+      const float2* src = a.ckpt + ((size_t)w * a.n + r0) * a.n;
+      for (int q = 0; q < nrows; ++q) bulk_g2s(ckb + (size_t)q * cks, src + (size_t)q * a.n, a.n * 8u, &bar[1]);
+    };
+    const float* hrow = a.h + (size_t)rr * a.n;
+    float g[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) g[i] = 0.f;
+    bool okw = true;
+    int issued_s = 0, issued_c = 0, done_s = 0, done_c = 0;  // copies per barrier (thread 0's view)
+    if (w0 < w1) {
+      fetch_s(w0);
+      fetch_c(w0);
+      issued_s = issued_c = 1;
+    }
+    for (int w = w0; w < w1; ++w) {
+      const ChanConst cc = a.chan[w];
+      if (!bulk_wait(&bar[0], (uint32_t)(done_s & 1))) okw = false;
+      if (!__syncthreads_and(okw)) break;
+      ++done_s;
+      float2 r[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) r[i] = stage[(size_t)lr * SR + t + T * i];
+      __syncthreads();  // stage consumed: the next channel may land in it
+      if (w + 1 < w1) {
+        fetch_s(w + 1);
+        ++issued_s;
+      }
+      LF::template fft<true, LF::P, NOI, true, PKR>(r, t, z, tw);
+      if (!bulk_wait(&bar[1], (uint32_t)(done_c & 1))) okw = false;
+      if (!__syncthreads_and(okw)) break;
+      ++done_c;
+      const float2* ck = ckb + (size_t)lr * cks;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i;
+        if (i < EF && x < a.n) {
+          const float2 au = r[i];
+          const float2 tt = transmission(__ldg(hrow + x), cc);
+          const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
+          g[i] = fmaf(au.x, cu.x, fmaf(au.y, cu.y, g[i]));
+          r[i] = cmulc(au, tt);
+        } else {
+          r[i] = czero();
+        }
+      }
+      if constexpr (!FIRST) {
+        LF::template step1<false, NZF, PKR>(r, t, z, tw);
+        __syncthreads();  // every thread is past its checkpoint reads
+        if (w + 1 < w1) {
+          fetch_c(w + 1);
+          ++issued_c;
+        }
+        LF::template step2<false, LF::Q, PKR>(r, t, z);
+        __syncthreads();
+        if (ok) {
+          float2* srow = a.S + ((size_t)w * a.n + rr) * M;
+#pragma unroll
+          for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+        }
+      } else {
+        __syncthreads();  // every thread is past its checkpoint reads
+        if (w + 1 < w1) {
+          fetch_c(w + 1);
+          ++issued_c;
+        }
+      }
+    }
+    if (!okw) {
+      // copies still in flight land (bounded waits) before the block leaves
+      if (threadIdx.x == 0) {
+        if (issued_s > done_s) (void)bulk_wait(&bar[0], (uint32_t)(done_s & 1));
+        if (issued_c > done_c) (void)bulk_wait(&bar[1], (uint32_t)(done_c & 1));
+        atomicExch(a.err, 1);
+      }
+      return;
+    }
+    if (ok) {
+      float* prow = a.partial + ((size_t)blockIdx.y * a.n + row) * a.n;
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i;
+        if (i < EF && x < a.n) prow[x] = g[i];
+      }
+    }
+  }
 };
 
 // two resident blocks per SM where the line's registers allow it
@@ -434,6 +573,11 @@ constexpr int bulk_min_blocks() { return LF::E <= 20 ? 2 : 1; }
 template <class LF, int RL, bool HALF, bool FIRST>
 __global__ void __launch_bounds__(LF::T * RL, bulk_min_blocks<LF>()) k_row_adj_ck(PassArgs a) {
   PassBulk<LF, RL, HALF>::template row_adj_ck<FIRST>(a);
+}
+// the staged adjoint row pass: three blocks of few rows per SM
+template <class LF, int RL, bool HALF, bool FIRST>
+__global__ void __launch_bounds__(LF::T * RL, LF::E <= 20 ? 3 : 1) k_row_adj_staged(PassArgs a) {
+  PassBulk<LF, RL, HALF>::template row_adj_staged<FIRST>(a);
 }
 template <class LF, int RL, bool HALF, bool ADJ>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, bulk_min_blocks<LF>())
@@ -492,8 +636,17 @@ struct PassBulkLaunch {
   static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
     return half(a) ? row_fwd_h<true>(a, save, s) : row_fwd_h<false>(a, save, s);
   }
+  // rows per block of the staged adjoint row pass
+  static constexpr int RLA = RL >= 16 ? RL / 2 : RL;
+  using PBA = PassBulk<LF, RLA>;
   template <bool H>
   static cudaError_t row_adj_h(const PassArgs& a, bool first, cudaStream_t s) {
+    if (a.n % 2 == 0 && PBA::adj_staged_smem(a.n) <= 227 * 1024) {
+      const dim3 g((a.n + RLA - 1) / RLA, a.n_chunks);
+      const size_t sm = PBA::adj_staged_smem(a.n);
+      return first ? launch_k(k_row_adj_staged<LF, RLA, H, true>, g, PBA::RT, sm, a, s)
+                   : launch_k(k_row_adj_staged<LF, RLA, H, false>, g, PBA::RT, sm, a, s);
+    }
     const dim3 g((a.n + RL - 1) / RL, a.n_chunks);
     if (a.n % 2 == 0 && PB::adj_ck_smem(a.n) <= 227 * 1024) {
       const size_t sm = PB::adj_ck_smem(a.n);

@@ -17,7 +17,7 @@ from paper_2604_02624_gb300 import _lib as L
 from paper_2604_02624_gb300 import workloads as W
 from paper_2604_02624_gb300.api import DiffractiveStack
 
-from gpu_cases import TOL_INTENSITY, TOL_LOSS, oracle_model, rel_l2
+from gpu_cases import TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS, oracle_model, rel_l2
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -53,6 +53,40 @@ def test_expired_bulk_wait_is_reported_and_context_recovers(monkeypatch):
     L_ref, _, _, fwd = O.loss_and_grad(h, T, **oracle_model(w))
     assert rel_l2(I, fwd["I"]) <= TOL_INTENSITY
     assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref)
+    st.close()
+
+
+def test_expired_wait_in_the_staged_adjoint_row_pass(monkeypatch):
+    """With only the adjoint row pass on its bulk kernel (both inputs staged by
+    bulk copies), the injected stall reaches that pass: its blocks give up
+    after the bounded waits, let their other copy land, and the next call that
+    reads the device flag reports DOS_ERR_TIMEOUT; the context then computes
+    the oracle's gradient."""
+    w = W.workload("tiny")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    monkeypatch.setenv("DOS_INJECT_WAIT_TIMEOUT", "1")
+    monkeypatch.setenv("DOS_FORCE_CONFIG", "multipass:bulk[row_adj]")
+    st = DiffractiveStack.from_workload(w, device=DEV, path="auto")
+    monkeypatch.delenv("DOS_INJECT_WAIT_TIMEOUT")
+    monkeypatch.delenv("DOS_FORCE_CONFIG")
+    assert "bulk[row_adj]" in L.dos_describe(st.handle)
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    Td = torch.tensor(T, dtype=torch.float32, device=DEV)
+    t0 = time.time()
+    st.forward(hd)
+    _, _, dl = st.loss(Td)          # the forward passes are plain: no stall yet
+    st.backward(hd, dl)             # the first bulk pass: its waits expire
+    st.forward(hd)
+    with pytest.raises(L.DosError) as e:
+        st.loss(Td)
+    assert e.value.code == L.DOS_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    st.forward(hd)
+    _, _, dl = st.loss(Td)
+    g = st.backward(hd, dl).cpu().numpy().astype(np.float64)
+    _, _, g_ref, _ = O.loss_and_grad(h, T, **oracle_model(w))
+    assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
     st.close()
 
 
