@@ -584,8 +584,11 @@ __global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, bulk_min_blocks<LF>())
     k_col_bulk(PassArgs a, const __grid_constant__ CUtensorMap map) {
   PassBulk<LF, RL, HALF>::template col<ADJ>(a, &map);
 }
+// the row passes: as many resident blocks as their shared memory allows
+template <class LF, int RL>
+constexpr int row_bulk_min_blocks() { return LF::E <= 20 ? (RL <= 8 ? 4 : 2) : 1; }
 template <class LF, int RL, bool HALF, bool ADJ, bool FLAG>
-__global__ void __launch_bounds__(LF::T * RL, bulk_min_blocks<LF>()) k_row_bulk(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * RL, row_bulk_min_blocks<LF, RL>()) k_row_bulk(PassArgs a) {
   PassBulk<LF, RL, HALF>::template row<ADJ, FLAG>(a);
 }
 
