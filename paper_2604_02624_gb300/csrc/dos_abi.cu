@@ -635,7 +635,10 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
     a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
     if (l == 1 && c->ckpt1_is_v1) {
       a.fin = c->v1;
-      DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD, op->row_first(a, c->stream), "first row pass");
+      a.stall = c->take_stall(kBulkRowFwd);
+      DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,
+                (c->bulk & kBulkRowFwd) ? op->bulk_row_first(a, c->stream) : op->row_first(a, c->stream),
+                "first row pass");
     } else {
       a.stall = c->take_stall(kBulkRowFwd);
       DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,

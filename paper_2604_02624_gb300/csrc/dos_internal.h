@@ -84,6 +84,7 @@ struct PassOps {
   cudaError_t (*bulk_col)(const PassArgs&, bool adjoint, cudaStream_t);
   cudaError_t (*bulk_row_fwd)(const PassArgs&, bool save, cudaStream_t);
   cudaError_t (*bulk_row_adj)(const PassArgs&, bool first, cudaStream_t);
+  cudaError_t (*bulk_row_first)(const PassArgs&, cudaStream_t);  // t(h) * field (fin) -> row spectra
 };
 
 const PassOps* pass_ops_for_m(int m);

@@ -316,6 +316,75 @@ struct PassBulk {
     }
   }
 
+  // -------------------------------------------------------- first row pass
+  // t(h) * v1 -> pad -> DFT (as Pass::row_first) with the next channel's rows
+  // of the input-field table v1 (fin) staged by bulk copies.  Needs N even.
+  // dynamic shared memory: stage[RL][cks] | exchange[RL][RZL] | tw[ZS] | barrier
+  static size_t first_smem(int n) {
+    return sizeof(float2) * ((size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS) + sizeof(uint64_t);
+  }
+
+  __device__ static void row_first_staged(const PassArgs& a) {
+    extern __shared__ __align__(16) float2 smem[];
+    const int cks = ck_stride(a.n);
+    float2* stage = smem;
+    float2* zb = stage + (size_t)RL * cks;
+    float2* tw = zb + (size_t)RL * RZL;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    const int l = threadIdx.x / T, t = threadIdx.x % T;
+    float2* z = zb + l * RZL;
+    const int r0 = blockIdx.x * RL;
+    const int nrows = min(RL, a.n - r0);
+    const int row = r0 + l;
+    const bool ok = l < nrows;
+    const int rr = ok ? row : r0;
+    const int lr = ok ? l : 0;
+    const int w0 = blockIdx.y * a.chunk;
+    const int w1 = min(a.nw, w0 + a.chunk);
+    const uint32_t bytes = (uint32_t)nrows * a.n * 8u;
+    if (threadIdx.x == 0) bulk_bar_init(bar);
+    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    __syncthreads();
+    auto fetch = [&](int w) {
+      if (threadIdx.x != 0) return;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(bar, bytes);
+      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      const float2* src = a.fin + ((size_t)w * a.n + r0) * a.n;
+      for (int q = 0; q < nrows; ++q) bulk_g2s(stage + (size_t)q * cks, src + (size_t)q * a.n, a.n * 8u, bar);
+    };
+    const float* hrow = a.h + (size_t)rr * a.n;
+    float hv[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = t + T * i;
+      hv[i] = (i < EF && x < a.n) ? __ldg(hrow + x) : 0.f;
+    }
+    bool okw = true;
+    if (w0 < w1) fetch(w0);
+    int k = 0;
+    for (int w = w0; w < w1; ++w, ++k) {
+      const ChanConst cc = a.chan[w];
+      if (!bulk_wait(bar, (uint32_t)(k & 1))) okw = false;
+      if (!__syncthreads_and(okw)) break;
+      float2 r[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) {
+        const int x = t + T * i;
+        r[i] = (i < EF && x < a.n) ? cmul(transmission(hv[i], cc), stage[(size_t)lr * cks + x]) : czero();
+      }
+      __syncthreads();  // stage consumed: the next channel may land in it
+      if (w + 1 < w1) fetch(w + 1);
+      LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
+      if (ok) {
+        float2* srow = a.S + ((size_t)w * a.n + rr) * M;
+#pragma unroll
+        for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
+      }
+    }
+    if (!okw && threadIdx.x == 0) atomicExch(a.err, 1);
+  }
+
   // ------------------------------------------------- adjoint row pass, checkpoint prefetch
   // The adjoint pass waits on its checkpoint loads (they follow the inverse
   // DFT); here the checkpoint rows of the next channel arrive by bulk copies
@@ -591,6 +660,10 @@ template <class LF, int RL, bool HALF, bool ADJ, bool FLAG>
 __global__ void __launch_bounds__(LF::T * RL, row_bulk_min_blocks<LF, RL>()) k_row_bulk(PassArgs a) {
   PassBulk<LF, RL, HALF>::template row<ADJ, FLAG>(a);
 }
+template <class LF, int RL, bool HALF>
+__global__ void __launch_bounds__(LF::T * RL, row_bulk_min_blocks<LF, RL>()) k_row_first_staged(PassArgs a) {
+  PassBulk<LF, RL, HALF>::row_first_staged(a);
+}
 
 // Launchers.  The column pass runs one persistent block per resident slot
 // (blocks per SM from the occupancy calculator x SMs); the row passes run
@@ -639,6 +712,15 @@ struct PassBulkLaunch {
   static cudaError_t row_fwd(const PassArgs& a, bool save, cudaStream_t s) {
     return half(a) ? row_fwd_h<true>(a, save, s) : row_fwd_h<false>(a, save, s);
   }
+  // the first forward row pass (t * v1 -> DFT) with staged input rows; the
+  // plain kernel where N is odd or the stage does not fit
+  static cudaError_t row_first(const PassArgs& a, cudaStream_t s) {
+    const size_t sm = PB::first_smem(a.n);
+    if (a.n % 2 != 0 || sm > 227 * 1024) return PassLaunch<LF>::row_first(a, s);
+    const dim3 g((a.n + RL - 1) / RL, a.n_chunks);
+    return half(a) ? launch_k(k_row_first_staged<LF, RL, true>, g, PB::RT, sm, a, s)
+                   : launch_k(k_row_first_staged<LF, RL, false>, g, PB::RT, sm, a, s);
+  }
   // rows per block of the staged adjoint row pass
   static constexpr int RLA = RL >= 16 ? RL / 2 : RL;
   using PBA = PassBulk<LF, RLA>;
@@ -674,7 +756,7 @@ const PassOps* pass_ops_table() {
                             Pass<LF>::ROWL, Pass<LF>::COLL, &PL::col,    &PL::row_fwd,
                             &PL::row_out, &PL::row_seed,  &PL::row_adj,  &PL::row_in,
                             &PL::row_back, &PL::row_first, &PBL::col, &PBL::row_fwd,
-                            &PBL::row_adj};
+                            &PBL::row_adj, &PBL::row_first};
   return &o;
 }
 
