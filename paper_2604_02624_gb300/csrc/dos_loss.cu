@@ -4,8 +4,10 @@
 // every channel and its target; reconstruction quality is a PSNR.  The
 // detector (Section 4: the FOV divided into output pixels) reads pixel (y, x)
 // as the sum of the b x b simulation intensities it covers (b = 1: I itself).
-// All sums run in FP64 in a fixed order (per-thread strided partial sums, then
-// a shared-memory tree), so results are reproducible bit for bit.
+// Per-pixel arithmetic and each thread's strided partial sums run in FP32 (a
+// thread sums at most a few hundred terms), the block tree and everything
+// after it in FP64 (GB300's FP64 rate is a small fraction of its FP32 rate);
+// every sum has a fixed order, so results are reproducible bit for bit.
 #include "dos_internal.h"
 
 #include "../../include/dos.h"
@@ -29,12 +31,12 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 __device__ __forceinline__ float intensity(float2 o) { return fmaf(o.x, o.x, o.y * o.y); }
 
 // detector pixel p = (y, x) of a channel's F x F output field: sum over its b x b block
-__device__ __forceinline__ double detector(const float2* ow, int fov, int b, int p) {
+__device__ __forceinline__ float detector(const float2* ow, int fov, int b, int p) {
   if (b == 1) return intensity(ow[p]);
   const int fd = fov / b, y = (p / fd) * b, x = (p % fd) * b;
-  double s = 0.0;
+  float s = 0.f;
   for (int i = 0; i < b; ++i)
-    for (int j = 0; j < b; ++j) s += (double)intensity(ow[(size_t)(y + i) * fov + x + j]);
+    for (int j = 0; j < b; ++j) s += intensity(ow[(size_t)(y + i) * fov + x + j]);
   return s;
 }
 
@@ -47,24 +49,26 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_stats(const float2* __rest
   const int fd = fov / b, det2 = fd * fd;
   const float2* ow = o + (size_t)w * fov * fov;
   const float* tw = T + (size_t)w * det2;
-  double sse = 0, sit = 0, sii = 0;
+  float fse = 0.f, fit = 0.f, fii = 0.f;
   for (int p = threadIdx.x; p < det2; p += kRedThreads) {
-    const double I = detector(ow, fov, b, p);
-    const double t = tw[p];
-    sse += (I - t) * (I - t);
-    sit += I * t;
-    sii += I * I;
+    const float I = detector(ow, fov, b, p);
+    const float t = tw[p];
+    const float d = I - t;
+    fse = fmaf(d, d, fse);
+    fit = fmaf(I, t, fit);
+    fii = fmaf(I, I, fii);
   }
-  sse = block_sum(sse, sh);
-  sit = block_sum(sit, sh);
-  sii = block_sum(sii, sh);
+  const double sse = block_sum(fse, sh);
+  const double sit = block_sum(fit, sh);
+  const double sii = block_sum(fii, sh);
   const double sigma = sii > 0.0 ? sit / sii : 0.0;
-  double ssc = 0;
+  const float sg = (float)sigma;
+  float fsc = 0.f;
   for (int p = threadIdx.x; p < det2; p += kRedThreads) {
-    const double d = sigma * detector(ow, fov, b, p) - (double)tw[p];
-    ssc += d * d;
+    const float d = fmaf(sg, detector(ow, fov, b, p), -tw[p]);
+    fsc = fmaf(d, d, fsc);
   }
-  ssc = block_sum(ssc, sh);
+  const double ssc = block_sum(fsc, sh);
   if (threadIdx.x == 0) {
     LossStats s;
     s.sse = sse;
@@ -106,29 +110,28 @@ cudaError_t launch_loss_final(const LossStats* st, int nw, int fov2, double norm
 // 2 (D - T) / norm, or 2 sigma (sigma D - T) / norm for the scaled loss
 __global__ void k_dldi(const float2* __restrict__ o, const float* __restrict__ T,
                        const LossStats* __restrict__ st, float* __restrict__ dLdI, size_t total,
-                       int fov, int b, double norm, int mode) {
+                       int fov, int b, float scale, int mode) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int fov2 = fov * fov, fd = fov / b;
   const size_t w = i / fov2;
   const int q = (int)(i % fov2);
   const int p = ((q / fov) / b) * fd + (q % fov) / b;  // detector pixel covering q
-  const double I = detector(o + w * fov2, fov, b, p);
-  const double t = T[w * fd * fd + p];
-  double g;
+  const float I = detector(o + w * fov2, fov, b, p);
+  const float t = T[w * fd * fd + p];
   if (mode == DOS_LOSS_MSE_SCALED) {
-    const double sg = st[w].sigma;
-    g = 2.0 * sg * (sg * I - t) / norm;
+    const float sg = (float)st[w].sigma;
+    dLdI[i] = scale * sg * fmaf(sg, I, -t);
   } else {
-    g = 2.0 * (I - t) / norm;
+    dLdI[i] = scale * (I - t);
   }
-  dLdI[i] = (float)g;
 }
 
 cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, float* dLdI, int nw,
                         int fov, int bin, double norm, int mode, cudaStream_t s) {
   const size_t total = (size_t)nw * fov * fov;
-  k_dldi<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(o, T, st, dLdI, total, fov, bin, norm, mode);
+  const float scale = (float)(2.0 / norm);  // dL/dD = 2 (D - T) / norm
+  k_dldi<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(o, T, st, dLdI, total, fov, bin, scale, mode);
   return cudaGetLastError();
 }
 
