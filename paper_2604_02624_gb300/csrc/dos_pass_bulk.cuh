@@ -551,7 +551,14 @@ struct PassBulk {
       const float2* src = a.ckpt + ((size_t)w * a.n + r0) * a.n;
       for (int q = 0; q < nrows; ++q) bulk_g2s(ckb + (size_t)q * cks, src + (size_t)q * a.n, a.n * 8u, &bar[1]);
     };
+    // the thickness row stays in registers across the chunk's channels
     const float* hrow = a.h + (size_t)rr * a.n;
+    float hv[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+      const int x = t + T * i;
+      hv[i] = (i < EF && x < a.n) ? __ldg(hrow + x) : 0.f;
+    }
     float g[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) g[i] = 0.f;
@@ -585,7 +592,7 @@ struct PassBulk {
         const int x = t + T * i;
         if (i < EF && x < a.n) {
           const float2 au = r[i];
-          const float2 tt = transmission(__ldg(hrow + x), cc);
+          const float2 tt = transmission(hv[i], cc);
           const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
           g[i] = fmaf(au.x, cu.x, fmaf(au.y, cu.y, g[i]));
           r[i] = cmulc(au, tt);
