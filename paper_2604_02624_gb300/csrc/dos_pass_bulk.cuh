@@ -655,8 +655,10 @@ template <class LF, int RL, bool HALF, bool FIRST>
 __global__ void __launch_bounds__(LF::T * RL, LF::E <= 20 ? 3 : 1) k_row_adj_staged(PassArgs a) {
   PassBulk<LF, RL, HALF>::template row_adj_staged<FIRST>(a);
 }
+// two blocks per SM for every line shape: one leaves too few warps to hide the
+// DFT's barriers and dependencies (M = 512: 8.5 ms per launch with one)
 template <class LF, int RL, bool HALF, bool ADJ>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, bulk_min_blocks<LF>())
+__global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, 2)
     k_col_bulk(PassArgs a, const __grid_constant__ CUtensorMap map) {
   PassBulk<LF, RL, HALF>::template col<ADJ>(a, &map);
 }
