@@ -10,8 +10,9 @@
 //                 one cp.async.bulk of M * 8 bytes per row (rows padded in
 //                 shared memory against bank conflicts).
 // One staging buffer per block suffices: the item is moved from the stage to
-// registers and the block synchronises before the next copy is issued, so
-// the copy overlaps the whole DFT / modulation / DFT / store of the item.
+// registers and the next copy is issued at the first block barrier after
+// that (the one inside the item's first line DFT), so the copy overlaps most
+// of the item's DFT / modulation / DFT / store.
 // Every wait is bounded (one second of global time): when it expires the
 // block sets *err, issues no further copy and leaves its loop (the copy it
 // waited for is its only one in flight).  PassArgs::stall (fault injection
@@ -149,8 +150,6 @@ struct PassBulk {
         const int row = t + T * i;
         r[i] = (i < EF && row >= a.in_r0 && row < a.in_r1) ? stage[(size_t)row * COLL + l] : czero();
       }
-      __syncthreads();  // stage consumed: the next item may land in it
-      if (it + (int)gridDim.x < items) fetch(it + gridDim.x);
       // transfer function of this column; with few elements per thread it is
       // loaded before the forward DFT so that the loads overlap it
       const float2* Hw = a.Hq + (size_t)w * a.hs * a.hs;
@@ -164,7 +163,11 @@ struct PassBulk {
           hv[i] = __ldg(Hw + (size_t)min(kk, M - kk) * a.hs + bc);
         }
       }
-      LF::template fft<false, NZF, LF::Q, true, PKC>(r, t, z, tw);
+      LF::template step1<false, NZF, PKC>(r, t, z, tw);
+      __syncthreads();  // every thread is past its stage reads: the next item may land there
+      if (it + (int)gridDim.x < items) fetch(it + gridDim.x);
+      LF::template step2<false, LF::Q, PKC>(r, t, z);
+      __syncthreads();
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         float2 h;
@@ -254,9 +257,11 @@ struct PassBulk {
       float2 r[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = stage[(size_t)(ok ? l : 0) * SR + t + T * i];
-      __syncthreads();  // stage consumed: the next channel may land in it
+      LF::template step1<true, LF::P, PKR>(r, t, z, tw);
+      __syncthreads();  // every thread is past its stage reads: the next channel may land there
       if (w + 1 < w1) fetch(w + 1);
-      LF::template fft<true, LF::P, NOI, true, PKR>(r, t, z, tw);
+      LF::template step2<true, NOI, PKR>(r, t, z);
+      __syncthreads();
       float2* srow = a.S + ((size_t)w * a.n + rr) * M;
       if constexpr (!ADJ) {
         float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
@@ -373,9 +378,11 @@ struct PassBulk {
         const int x = t + T * i;
         r[i] = (i < EF && x < a.n) ? cmul(transmission(hv[i], cc), stage[(size_t)lr * cks + x]) : czero();
       }
-      __syncthreads();  // stage consumed: the next channel may land in it
+      LF::template step1<false, NZF, PKR>(r, t, z, tw);
+      __syncthreads();  // every thread is past its stage reads: the next channel may land there
       if (w + 1 < w1) fetch(w + 1);
-      LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
+      LF::template step2<false, LF::Q, PKR>(r, t, z);
+      __syncthreads();
       if (ok) {
         float2* srow = a.S + ((size_t)w * a.n + rr) * M;
 #pragma unroll
@@ -577,12 +584,14 @@ struct PassBulk {
       float2 r[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = stage[(size_t)lr * SR + t + T * i];
-      __syncthreads();  // stage consumed: the next channel may land in it
+      LF::template step1<true, LF::P, PKR>(r, t, z, tw);
+      __syncthreads();  // every thread is past its stage reads: the next channel may land there
       if (w + 1 < w1) {
         fetch_s(w + 1);
         ++issued_s;
       }
-      LF::template fft<true, LF::P, NOI, true, PKR>(r, t, z, tw);
+      LF::template step2<true, NOI, PKR>(r, t, z);
+      __syncthreads();
       if (!bulk_wait(&bar[1], (uint32_t)(done_c & 1))) okw = false;
       if (!__syncthreads_and(okw)) break;
       ++done_c;
