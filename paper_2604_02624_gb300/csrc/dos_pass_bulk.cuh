@@ -183,7 +183,9 @@ struct PassBulk {
         }
         r[i] = ADJ ? cmulc(r[i], h) : cmul(r[i], h);
       }
-      LF::template fft<true, LF::P, NOI, true, PKC>(r, t, z, tw);
+      // no trailing barrier: the exchange buffer is next written after the
+      // barrier at the top of the next item
+      LF::template fft<true, LF::P, NOI, false, PKC>(r, t, z, tw);
       float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
@@ -276,7 +278,7 @@ struct PassBulk {
             r[i] = czero();
           }
         }
-        LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
+        LF::template fft<false, NZF, LF::Q, false, PKR>(r, t, z, tw);  // next z write follows the loop-top barrier
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -297,7 +299,7 @@ struct PassBulk {
           }
         }
         if constexpr (!FLAG) {
-          LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
+          LF::template fft<false, NZF, LF::Q, false, PKR>(r, t, z, tw);  // next z write follows the loop-top barrier
           if (ok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -381,8 +383,7 @@ struct PassBulk {
       LF::template step1<false, NZF, PKR>(r, t, z, tw);
       __syncthreads();  // every thread is past its stage reads: the next channel may land there
       if (w + 1 < w1) fetch(w + 1);
-      LF::template step2<false, LF::Q, PKR>(r, t, z);
-      __syncthreads();
+      LF::template step2<false, LF::Q, PKR>(r, t, z);  // next z write follows the loop-top barrier
       if (ok) {
         float2* srow = a.S + ((size_t)w * a.n + rr) * M;
 #pragma unroll
@@ -590,8 +591,7 @@ struct PassBulk {
         fetch_s(w + 1);
         ++issued_s;
       }
-      LF::template step2<true, NOI, PKR>(r, t, z);
-      __syncthreads();
+      LF::template step2<true, NOI, PKR>(r, t, z);  // the barrier below also ends its z reads
       if (!bulk_wait(&bar[1], (uint32_t)(done_c & 1))) okw = false;
       if (!__syncthreads_and(okw)) break;
       ++done_c;
@@ -616,8 +616,7 @@ struct PassBulk {
           fetch_c(w + 1);
           ++issued_c;
         }
-        LF::template step2<false, LF::Q, PKR>(r, t, z);
-        __syncthreads();
+        LF::template step2<false, LF::Q, PKR>(r, t, z);  // next z write follows the loop-top barrier
         if (ok) {
           float2* srow = a.S + ((size_t)w * a.n + rr) * M;
 #pragma unroll
