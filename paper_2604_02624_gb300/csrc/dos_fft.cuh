@@ -294,12 +294,18 @@ struct Line {
   static constexpr int RP = (P % 2 == 0) ? P + 1 : P;  // odd pitch: conflict-free columns
   static constexpr int ZS = Q * RP;
   static_assert(P % T == 0 && Q % T == 0, "T must divide P and Q");
+  // TR: the exchange matrix stored transposed (entry (q, k1) at k1 * RP + q).
+  // For a square line (P = Q = T) step 1 of thread t writes exactly the
+  // entries that step 2 of thread t read in the other layout, so two line
+  // DFTs in alternating layouts need no barrier between them.
+  static constexpr bool SQUARE = P == Q && T == P;
 
   // Step 1: the Q/T sub-DFTs of length P owned by thread t (q = t + T*j),
   // twiddled and written to the exchange matrix z[q][k1].
   // NZP: leading non-zero inputs of each sub-DFT (zero padding).
-  template <bool INV, int NZP = P, bool PK = false>
+  template <bool INV, int NZP = P, bool PK = false, bool TR = false>
   DOS_HD static void step1(const float2 (&r)[E], int t, float2* z, const float2* tw) {
+    static_assert(!TR || SQUARE, "the transposed exchange is for square lines");
     static_for<0, QJ>([&](auto jj) {
       constexpr int j = jj;
       float2 a[P];
@@ -307,24 +313,25 @@ struct Line {
       dft<P, INV, NZP, P, PK>(a);
       const int q = t + T * j;
       const float2* twq = tw + q * RP;
-      float2* zq = z + q * RP;
+      float2* zq = TR ? z + q : z + q * RP;
+      constexpr int ZK = TR ? RP : 1;  // stride of k1
       zq[0] = a[0];
       static_for<1, P>([&](auto kk) {
         const float2 w = twq[kk];
-        zq[kk] = INV ? cmulc(a[kk], w) : cmul(a[kk], w);
+        zq[kk * ZK] = INV ? cmulc(a[kk], w) : cmul(a[kk], w);
       });
     });
   }
   // Step 2: the P/T sub-DFTs of length Q owned by thread t (k1 = t + T*j),
   // read as columns of z; outputs k1 + P*k2 land in r[j + (P/T)*k2].
   // NOQ: leading outputs of each sub-DFT that are needed (cropping).
-  template <bool INV, int NOQ = Q, bool PK = false>
+  template <bool INV, int NOQ = Q, bool PK = false, bool TR = false>
   DOS_HD static void step2(float2 (&r)[E], int t, const float2* z) {
     static_for<0, PJ>([&](auto jj) {
       constexpr int j = jj;
       const int k1 = t + T * j;
       float2 b[Q];
-      static_for<0, Q>([&](auto qq) { b[qq] = z[qq * RP + k1]; });
+      static_for<0, Q>([&](auto qq) { b[qq] = TR ? z[k1 * RP + qq] : z[qq * RP + k1]; });
       dft<Q, INV, Q, NOQ, PK>(b);
       static_for<0, NOQ>([&](auto k2) { r[j + PJ * k2] = b[k2]; });
     });
@@ -333,11 +340,11 @@ struct Line {
   // that next write a different buffer (and reach another barrier before
   // reusing z) pass false.
   // PK: the unpruned butterflies add and subtract in packed FP32 pairs
-  template <bool INV, int NZP = P, int NOQ = Q, bool TRAIL = true, bool PK = false>
+  template <bool INV, int NZP = P, int NOQ = Q, bool TRAIL = true, bool PK = false, bool TR = false>
   __device__ static __forceinline__ void fft(float2 (&r)[E], int t, float2* z, const float2* tw) {
-    step1<INV, NZP, PK>(r, t, z, tw);
+    step1<INV, NZP, PK, TR>(r, t, z, tw);
     __syncthreads();
-    step2<INV, NOQ, PK>(r, t, z);
+    step2<INV, NOQ, PK, TR>(r, t, z);
     if constexpr (TRAIL) __syncthreads();
   }
 };

@@ -167,7 +167,9 @@ struct PassBulk {
       __syncthreads();  // every thread is past its stage reads: the next item may land there
       if (it + (int)gridDim.x < items) fetch(it + gridDim.x);
       LF::template step2<false, LF::Q, PKC>(r, t, z);
-      __syncthreads();
+      // square lines: the inverse DFT below writes the exchange matrix in
+      // the transposed layout, i.e. only what this thread just read
+      if constexpr (!LF::SQUARE) __syncthreads();
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         float2 h;
@@ -185,7 +187,7 @@ struct PassBulk {
       }
       // no trailing barrier: the exchange buffer is next written after the
       // barrier at the top of the next item
-      LF::template fft<true, LF::P, NOI, false, PKC>(r, t, z, tw);
+      LF::template fft<true, LF::P, NOI, false, PKC, LF::SQUARE>(r, t, z, tw);
       float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
@@ -263,7 +265,10 @@ struct PassBulk {
       __syncthreads();  // every thread is past its stage reads: the next channel may land there
       if (w + 1 < w1) fetch(w + 1);
       LF::template step2<true, NOI, PKR>(r, t, z);
-      __syncthreads();
+      // square lines: the forward DFT below writes the exchange matrix in the
+      // transposed layout (only what this thread just read); the adjoint's
+      // forward DFT does too
+      if constexpr (!LF::SQUARE) __syncthreads();
       float2* srow = a.S + ((size_t)w * a.n + rr) * M;
       if constexpr (!ADJ) {
         float2* ck = a.ckpt + ((size_t)w * a.n + rr) * a.n;
@@ -278,7 +283,7 @@ struct PassBulk {
             r[i] = czero();
           }
         }
-        LF::template fft<false, NZF, LF::Q, false, PKR>(r, t, z, tw);  // next z write follows the loop-top barrier
+        LF::template fft<false, NZF, LF::Q, false, PKR, LF::SQUARE>(r, t, z, tw);
         if (ok) {
 #pragma unroll
           for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -299,7 +304,7 @@ struct PassBulk {
           }
         }
         if constexpr (!FLAG) {
-          LF::template fft<false, NZF, LF::Q, false, PKR>(r, t, z, tw);  // next z write follows the loop-top barrier
+          LF::template fft<false, NZF, LF::Q, false, PKR, LF::SQUARE>(r, t, z, tw);
           if (ok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
@@ -610,13 +615,13 @@ struct PassBulk {
         }
       }
       if constexpr (!FIRST) {
-        LF::template step1<false, NZF, PKR>(r, t, z, tw);
+        LF::template step1<false, NZF, PKR, LF::SQUARE>(r, t, z, tw);
         __syncthreads();  // every thread is past its checkpoint reads
         if (w + 1 < w1) {
           fetch_c(w + 1);
           ++issued_c;
         }
-        LF::template step2<false, LF::Q, PKR>(r, t, z);  // next z write follows the loop-top barrier
+        LF::template step2<false, LF::Q, PKR, LF::SQUARE>(r, t, z);  // next z write follows the loop-top barrier
         if (ok) {
           float2* srow = a.S + ((size_t)w * a.n + rr) * M;
 #pragma unroll
