@@ -79,10 +79,13 @@ enum {
  * Implementation of the propagation passes.
  *  DOS_PATH_MULTIPASS: a row pass and a column pass kernel per gap over all
  *    channels, row spectra staged in HBM (any supported M).
- *  DOS_PATH_MULTIPASS_BULK: the same passes, but persistent blocks fetch their
- *    next item (a column tile, or the next channel's rows) with bulk-async
- *    copies into shared memory while computing the current one (needs the
- *    column stage, 128 N bytes + exchange, within 227 KB of shared memory).
+ *  DOS_PATH_MULTIPASS_BULK: the same passes, but blocks fetch their next item
+ *    (a column tile by a TMA tensor copy, or the next channel's rows by
+ *    bulk-async copies) into shared memory while computing the current one;
+ *    the adjoint row pass stages both the spectra rows and the checkpoint
+ *    rows. A pass whose stage does not fit (column: 128 N bytes + exchange
+ *    within 227 KB, N <= 256) or whose rows are not 16-byte multiples (odd N)
+ *    runs the plain kernel.
  *  DOS_PATH_FUSED: one persistent launch per sweep (forward or adjoint) in
  *    which a thread-block cluster carries one channel at a time through every
  *    gap with the field held in distributed shared memory (needs N <= M/2 and
@@ -95,11 +98,16 @@ enum {
  *    parts and six products kept (~1e-7 per GEMM, twice the tensor work).
  *  DOS_PATH_AUTO: dos_create times one forward+backward of every available
  *    multi-pass (plain and bulk) / cluster-resident configuration and keeps
- *    the fastest.
- * Environment: DOS_FORCE_CONFIG="multipass", "multipass:bulk" or
+ *    the fastest; from per-kernel event times of the plain and the bulk
+ *    multi-pass runs it also times the mix that runs the faster kernel of
+ *    each pass kind (column, forward row, adjoint row).
+ * Environment: DOS_FORCE_CONFIG="multipass", "multipass:bulk",
+ * "multipass:bulk[<kinds>]" (<kinds>: col, row_fwd, row_adj joined by '+',
+ * the kinds on bulk kernels; under DOS_PATH_AUTO only) or
  * "fused:C<c>:L<lines>" (names as printed by dos_describe) selects a
- * configuration without timing, when it is among the requested path's; DOS_TUNE_CACHE=<file> stores and reuses
- * the autotuner's decision per (device, N, M, K, N_w, F).
+ * configuration without timing, when it is among the requested path's;
+ * DOS_TUNE_CACHE=<file> stores and reuses the autotuner's decision per
+ * (device, N, M, K, N_w, F).
  * Fault injection (tests): DOS_INJECT_WAIT_TIMEOUT=1 at dos_create makes the
  * first bulk-prefetch pass that the context launches announce its bytes
  * without copying them, so that the bounded waits of its blocks expire (one
