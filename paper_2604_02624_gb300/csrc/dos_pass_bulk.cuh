@@ -398,115 +398,10 @@ struct PassBulk {
     if (!okw && threadIdx.x == 0) atomicExch(a.err, 1);
   }
 
-  // ------------------------------------------------- adjoint row pass, checkpoint prefetch
-  // The adjoint pass waits on its checkpoint loads (they follow the inverse
-  // DFT); here the checkpoint rows of the next channel arrive by bulk copies
-  // into the other half of a double buffer while the block works on the
-  // current one, and the row spectra are read directly (their loads open the
-  // iteration).  Needs N even (N * 8-byte rows, 16-byte multiples).
-  // dynamic shared memory: ck[2][RL][cks] | exchange[RL][RZL] | tw[ZS] | barrier[2]
-  __host__ __device__ static int ck_stride(int n) {
-    // >= n, and congruent to SR mod 16: the rows of consecutive lines fall in
-    // different banks the same way as in the staged spectra
-    return n + (((SR - n) % 16) + 16) % 16;
-  }
-  static size_t adj_ck_smem(int n) {
-    return sizeof(float2) * (2 * (size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS) + 2 * sizeof(uint64_t);
-  }
-
-  template <bool FIRST>
-  __device__ static void row_adj_ck(const PassArgs& a) {
-    extern __shared__ __align__(16) float2 smem[];
-    const int cks = ck_stride(a.n);
-    float2* ckb = smem;
-    float2* zb = ckb + 2 * (size_t)RL * cks;
-    float2* tw = zb + (size_t)RL * RZL;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
-    const int l = threadIdx.x / T, t = threadIdx.x % T;
-    float2* z = zb + l * RZL;
-    const int r0 = blockIdx.x * RL;
-    const int nrows = min(RL, a.n - r0);
-    const int row = r0 + l;
-    const bool ok = l < nrows;
-    const int rr = ok ? row : r0;
-    const int w0 = blockIdx.y * a.chunk;
-    const int w1 = min(a.nw, w0 + a.chunk);
-    const uint32_t bytes = (uint32_t)nrows * a.n * 8u;
-    if (threadIdx.x == 0) {
-      bulk_bar_init(&bar[0]);
-      bulk_bar_init(&bar[1]);
-    }
-    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
-    __syncthreads();
-    // thread 0 copies the block's checkpoint rows of channel w into half b
-    auto fetch = [&](int w, int b) {
-      if (threadIdx.x != 0) return;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bulk_expect(&bar[b], bytes);
-      if (a.stall) return;  // injected fault: the expected bytes never arrive
-      const float2* src = a.ckpt + ((size_t)w * a.n + r0) * a.n;
-      float2* dst = ckb + (size_t)b * RL * cks;
-      for (int q = 0; q < nrows; ++q) bulk_g2s(dst + (size_t)q * cks, src + (size_t)q * a.n, a.n * 8u, &bar[b]);
-    };
-    const float* hrow = a.h + (size_t)rr * a.n;
-    float g[E];
-#pragma unroll
-    for (int i = 0; i < E; ++i) g[i] = 0.f;
-    bool okw = true;
-    if (w0 < w1) fetch(w0, 0);
-    int k = 0;
-    for (int w = w0; w < w1; ++w, ++k) {
-      const int b = k & 1;
-      // the other half was read by the previous channel, which every thread
-      // has finished (barriers inside its DFTs): refill it with the next one
-      if (w + 1 < w1) fetch(w + 1, b ^ 1);
-      float2* srow = a.S + ((size_t)w * a.n + rr) * M;
-      float2 r[E];
-#pragma unroll
-      for (int i = 0; i < E; ++i) r[i] = srow[t + T * i];
-      const ChanConst cc = a.chan[w];
-      LF::template fft<true, LF::P, NOI, true, PKR>(r, t, z, tw);
-      if (!bulk_wait(&bar[b], (uint32_t)((k >> 1) & 1))) okw = false;
-      if (!__syncthreads_and(okw)) break;
-      const float2* ck = ckb + ((size_t)b * RL + (ok ? l : 0)) * cks;
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int x = t + T * i;
-        if (i < EF && x < a.n) {
-          const float2 au = r[i];
-          const float2 tt = transmission(__ldg(hrow + x), cc);
-          const float2 cu = cmul(make_float2(cc.c_re, cc.c_im), cmul(tt, ck[x]));
-          g[i] = fmaf(au.x, cu.x, fmaf(au.y, cu.y, g[i]));
-          r[i] = cmulc(au, tt);
-        } else {
-          r[i] = czero();
-        }
-      }
-      if constexpr (!FIRST) {
-        LF::template fft<false, NZF, LF::Q, true, PKR>(r, t, z, tw);
-        if (ok) {
-#pragma unroll
-          for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
-        }
-      } else {
-        __syncthreads();  // the half is refilled at the top of the next iteration
-      }
-    }
-    if (!okw) {
-      // the copy of the next channel may still be in flight: let it land
-      if (threadIdx.x == 0 && k + 1 < w1 - w0) (void)bulk_wait(&bar[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1));
-      if (threadIdx.x == 0) atomicExch(a.err, 1);
-      return;
-    }
-    if (ok) {
-      float* prow = a.partial + ((size_t)blockIdx.y * a.n + row) * a.n;
-#pragma unroll
-      for (int i = 0; i < E; ++i) {
-        const int x = t + T * i;
-        if (i < EF && x < a.n) prow[x] = g[i];
-      }
-    }
-  }
+  // Row stride in shared memory of staged N-point rows (checkpoint, input
+  // field): >= N, and congruent to SR mod 16, so that the rows of consecutive
+  // lines fall in different banks the same way as in the staged spectra.
+  __host__ __device__ static int ck_stride(int n) { return n + (((SR - n) % 16) + 16) % 16; }
 
   // ------------------------------------------- adjoint row pass, both inputs staged
   // Both inputs of a channel arrive by bulk copies: its spectra rows (into a
@@ -655,14 +550,6 @@ struct PassBulk {
   }
 };
 
-// two resident blocks per SM where the line's registers allow it
-template <class LF>
-constexpr int bulk_min_blocks() { return LF::E <= 20 ? 2 : 1; }
-
-template <class LF, int RL, bool HALF, bool FIRST>
-__global__ void __launch_bounds__(LF::T * RL, bulk_min_blocks<LF>()) k_row_adj_ck(PassArgs a) {
-  PassBulk<LF, RL, HALF>::template row_adj_ck<FIRST>(a);
-}
 // the staged adjoint row pass: three blocks of few rows per SM
 template <class LF, int RL, bool HALF, bool FIRST>
 __global__ void __launch_bounds__(LF::T * RL, LF::E <= 20 ? 3 : 1) k_row_adj_staged(PassArgs a) {
@@ -754,12 +641,8 @@ struct PassBulkLaunch {
       return first ? launch_k(k_row_adj_staged<LF, RLA, H, true>, g, PBA::RT, sm, a, s)
                    : launch_k(k_row_adj_staged<LF, RLA, H, false>, g, PBA::RT, sm, a, s);
     }
+    // odd N: the spectra rows staged, the checkpoint read directly
     const dim3 g((a.n + RL - 1) / RL, a.n_chunks);
-    if (a.n % 2 == 0 && PB::adj_ck_smem(a.n) <= 227 * 1024) {
-      const size_t sm = PB::adj_ck_smem(a.n);
-      return first ? launch_k(k_row_adj_ck<LF, RL, H, true>, g, PB::RT, sm, a, s)
-                   : launch_k(k_row_adj_ck<LF, RL, H, false>, g, PB::RT, sm, a, s);
-    }
     const size_t sm = PB::row_smem();
     return first ? launch_k(k_row_bulk<LF, RL, H, true, true>, g, PB::RT, sm, a, s)
                  : launch_k(k_row_bulk<LF, RL, H, true, false>, g, PB::RT, sm, a, s);
