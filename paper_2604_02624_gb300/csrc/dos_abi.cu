@@ -1037,16 +1037,12 @@ DOS_API int dos_loss(dos_ctx* c, const float* d_T, double* h_loss, float* d_psnr
   const int det2 = (c->fov / c->bin) * (c->fov / c->bin);
   const double norm = (double)c->nw_total * det2;
   c->launches = 0;
-  DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, c->fov, c->bin, c->stream),
-            "loss statistics");
+  DOS_TIMED(c, DOS_KERNEL_LOSS,
+            dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, c->fov, c->bin, d_dLdI, norm, c->loss, c->stream),
+            "loss statistics and dL/dI");
   DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_loss_final(c->stats, c->nw, det2, norm, c->loss, c->d_loss, d_psnr, c->stream),
             "loss total");
   c->launches += 2;
-  if (d_dLdI) {
-    DOS_TIMED(c, DOS_KERNEL_LOSS, dos::launch_dldi(c->o, d_T, c->stats, d_dLdI, c->nw, c->fov, c->bin, norm, c->loss, c->stream),
-              "dL/dI");
-    ++c->launches;
-  }
   c->have_loss = true;
   if (h_loss) return dos_read_loss(c, h_loss);
   return DOS_OK;
@@ -1149,13 +1145,13 @@ DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dL
       const double norm = (double)c->nw_total * det2;
       rc = run_forward(c, d_h, d_I, 1);
       const int fwd_launches = c->launches;
-      if (!rc) e = dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, c->fov, c->bin, c->gstream);
+      if (!rc)
+        e = dos::launch_loss_stats(c->o, d_T, c->stats, c->nw, c->fov, c->bin, c->dLdI_step, norm, c->loss,
+                                   c->gstream);
       if (!rc && e == cudaSuccess)
         e = dos::launch_loss_final(c->stats, c->nw, det2, norm, c->loss, c->d_loss, d_psnr, c->gstream);
-      if (!rc && e == cudaSuccess)
-        e = dos::launch_dldi(c->o, d_T, c->stats, c->dLdI_step, c->nw, c->fov, c->bin, norm, c->loss, c->gstream);
       if (!rc && e == cudaSuccess) rc = run_backward(c, d_h, c->dLdI_step, d_dLdh);
-      if (!rc) c->step_launches = fwd_launches + 3 + c->launches;
+      if (!rc) c->step_launches = fwd_launches + 2 + c->launches;
       cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
       if (e == cudaSuccess) e = e2;
     }

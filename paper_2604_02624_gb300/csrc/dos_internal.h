@@ -112,14 +112,13 @@ struct LossStats {
   double pad;
 };
 // o: [nw][fov][fov] output field; T: [nw][fov/bin][fov/bin] targets of the
-// detector pixels (bin x bin simulation pixels each); dLdI: [nw][fov][fov]
+// detector pixels (bin x bin simulation pixels each); dLdI: [nw][fov][fov] or
+// null (then not written); norm: the loss's divisor; mode: DOS_LOSS_*
 cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov, int bin,
-                              cudaStream_t s);
+                              float* dLdI, double norm, int mode, cudaStream_t s);
 // det2: detector pixels per channel (PSNR mean)
 cudaError_t launch_loss_final(const LossStats* st, int nw, int det2, double norm, int mode,
                               double* d_loss, float* d_psnr, cudaStream_t s);
-cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, float* dLdI, int nw,
-                        int fov, int bin, double norm, int mode, cudaStream_t s);
 cudaError_t launch_grad_reduce(const float* partial, float* grad, int n_chunks, size_t count,
                                size_t chunk_stride, cudaStream_t s);
 cudaError_t launch_grad_reduce_flat(const float* partial, float* grad, int n_parts, size_t count,

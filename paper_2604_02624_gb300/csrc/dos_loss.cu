@@ -40,10 +40,14 @@ __device__ __forceinline__ float detector(const float2* ow, int fov, int b, int 
   return s;
 }
 
-// per channel: sum (D-T)^2, sigma = sum D T / sum D^2, sum (sigma D - T)^2
+// per channel: sum (D-T)^2, sigma = sum D T / sum D^2, sum (sigma D - T)^2,
+// and (dLdI not null) dL/dI of the channel's simulation pixels: dL/dD of the
+// detector pixel covering it, 2 (D - T) / norm, or 2 sigma (sigma D - T) / norm
+// for the scaled loss (scale = 2 / norm)
 __global__ void __launch_bounds__(kRedThreads) k_loss_stats(const float2* __restrict__ o,
                                                             const float* __restrict__ T,
-                                                            LossStats* __restrict__ st, int fov, int b) {
+                                                            LossStats* __restrict__ st, int fov, int b,
+                                                            float* __restrict__ dLdI, float scale, int mode) {
   __shared__ double sh[kRedThreads];
   const int w = blockIdx.x;
   const int fd = fov / b, det2 = fd * fd;
@@ -77,11 +81,22 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_stats(const float2* __rest
     s.pad = 0;
     st[w] = s;
   }
+  if (dLdI) {
+    const int fov2 = fov * fov;
+    float* gw = dLdI + (size_t)w * fov2;
+    for (int q = threadIdx.x; q < fov2; q += kRedThreads) {
+      const int p = ((q / fov) / b) * fd + (q % fov) / b;  // detector pixel covering q
+      const float I = detector(ow, fov, b, p);
+      const float t = tw[p];
+      gw[q] = mode == DOS_LOSS_MSE_SCALED ? scale * sg * fmaf(sg, I, -t) : scale * (I - t);
+    }
+  }
 }
 
 cudaError_t launch_loss_stats(const float2* o, const float* T, LossStats* st, int nw, int fov, int bin,
-                              cudaStream_t s) {
-  k_loss_stats<<<nw, kRedThreads, 0, s>>>(o, T, st, fov, bin);
+                              float* dLdI, double norm, int mode, cudaStream_t s) {
+  const float scale = (float)(2.0 / norm);  // dL/dD = 2 (D - T) / norm
+  k_loss_stats<<<nw, kRedThreads, 0, s>>>(o, T, st, fov, bin, dLdI, scale, mode);
   return cudaGetLastError();
 }
 
@@ -103,35 +118,6 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_final(const LossStats* __r
 cudaError_t launch_loss_final(const LossStats* st, int nw, int fov2, double norm, int mode,
                               double* d_loss, float* d_psnr, cudaStream_t s) {
   k_loss_final<<<1, kRedThreads, 0, s>>>(st, nw, fov2, norm, mode, d_loss, d_psnr);
-  return cudaGetLastError();
-}
-
-// dL/dI of a simulation pixel = dL/dD of its detector pixel:
-// 2 (D - T) / norm, or 2 sigma (sigma D - T) / norm for the scaled loss
-__global__ void k_dldi(const float2* __restrict__ o, const float* __restrict__ T,
-                       const LossStats* __restrict__ st, float* __restrict__ dLdI, size_t total,
-                       int fov, int b, float scale, int mode) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  const int fov2 = fov * fov, fd = fov / b;
-  const size_t w = i / fov2;
-  const int q = (int)(i % fov2);
-  const int p = ((q / fov) / b) * fd + (q % fov) / b;  // detector pixel covering q
-  const float I = detector(o + w * fov2, fov, b, p);
-  const float t = T[w * fd * fd + p];
-  if (mode == DOS_LOSS_MSE_SCALED) {
-    const float sg = (float)st[w].sigma;
-    dLdI[i] = scale * sg * fmaf(sg, I, -t);
-  } else {
-    dLdI[i] = scale * (I - t);
-  }
-}
-
-cudaError_t launch_dldi(const float2* o, const float* T, const LossStats* st, float* dLdI, int nw,
-                        int fov, int bin, double norm, int mode, cudaStream_t s) {
-  const size_t total = (size_t)nw * fov * fov;
-  const float scale = (float)(2.0 / norm);  // dL/dD = 2 (D - T) / norm
-  k_dldi<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(o, T, st, dLdI, total, fov, bin, scale, mode);
   return cudaGetLastError();
 }
 
