@@ -14,8 +14,8 @@
 // that (the one inside the item's first line DFT), so the copy overlaps most
 // of the item's DFT / modulation / DFT / store.
 // Every wait is bounded (one second of global time): when it expires the
-// block sets *err, issues no further copy and leaves its loop (the copy it
-// waited for is its only one in flight).  PassArgs::stall (fault injection
+// block issues no further copy, leaves its loop, waits once more (bounded)
+// for the copy it was waiting for (its only one in flight) and sets *err.  PassArgs::stall (fault injection
 // for tests) makes the blocks announce their bytes without copying them, so
 // that the first wait of every block expires.
 #pragma once
@@ -195,7 +195,10 @@ struct PassBulk {
         if (i < EF && cok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
       }
     }
-    if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
+    if (!ok && threadIdx.x == 0) {
+      (void)bulk_wait(bar, (uint32_t)(k & 1));  // a late copy lands (bounded) before the block leaves
+      atomicExch(a.err, 1);
+    }
   }
 
   // ------------------------------------------------------------- row passes
@@ -313,7 +316,10 @@ struct PassBulk {
       }
     }
     if (!okw) {
-      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      if (threadIdx.x == 0) {
+        (void)bulk_wait(bar, (uint32_t)(k & 1));  // a late copy lands (bounded) before the block leaves
+        atomicExch(a.err, 1);
+      }
       return;
     }
     if constexpr (ADJ) {
@@ -395,7 +401,10 @@ struct PassBulk {
         for (int i = 0; i < E; ++i) srow[t + T * i] = r[i];
       }
     }
-    if (!okw && threadIdx.x == 0) atomicExch(a.err, 1);
+    if (!okw && threadIdx.x == 0) {
+      (void)bulk_wait(bar, (uint32_t)(k & 1));  // a late copy lands (bounded) before the block leaves
+      atomicExch(a.err, 1);
+    }
   }
 
   // Row stride in shared memory of staged N-point rows (checkpoint, input
