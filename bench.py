@@ -35,12 +35,40 @@ sys.path.insert(0, ROOT)
 # the bench scales them to the launch's channels.  An entry must be removed
 # (traffic reported as null) when its kernel changes.
 TRAFFIC_PER_CHANNEL = {
-    # TMA column pass with packed butterflies: forward 1.4017 MB; adjoint 0.9168 MB
-    # (first gap, field-of-view input rows) and 1.4020 MB (the other K - 1 gaps)
-    ("column_bulk", 200, 400, "column_forward"): (1.401686e6, "profiles/column_pass_bulk_batched.md"),
+    # TMA column pass with packed butterflies: forward 1.4017 MB (gaps 1..K-1) and
+    # 1.0758 MB (last gap, field-of-view output rows); adjoint 0.9168 MB (first
+    # gap, field-of-view input rows) and 1.4020 MB (the other K - 1 gaps)
+    ("column_bulk", 200, 400, "column_forward"): ((4 * 1.401686e6 + 1.075750e6) / 5,
+                                                  "profiles/column_pass_bulk_batched.md"),
     ("column_bulk", 200, 400, "column_adjoint"): ((0.916752e6 + 4 * 1.401998e6) / 5,
                                                   "profiles/column_pass_bulk_batched.md"),
 }
+
+
+def step_bytes(n, m, K, F, nw, bin_=1):
+    """Algorithmic bytes of one step (forward + loss + adjoint) of nw channels:
+    'design' = what the multi-pass kernels must move (complex64 = 8 B: the
+    create-time v1 table read by the first row pass, the row spectra N x M in
+    and out of every pass, the checkpoints, one transfer-table quadrant per
+    column pass, the field-of-view rows of the last forward / first adjoint gap,
+    output, loss and seed; the per-chunk gradient partials are left out), and
+    'ideal' = 40 N^2 B per layer-propagation (read v, write v_next forward;
+    read a and the checkpoint, write a_prev adjoint), the traffic of a design
+    that keeps the spectra on chip."""
+    hs = m // 2 + 1
+    det = (F // bin_) ** 2
+    fwd = (8 * n * n + 8 * n * m                                   # first row pass (v1 table)
+           + (K - 1) * (16 * n * m + 8 * n * n)                     # forward row passes + checkpoints
+           + (K - 1) * (16 * n * m + 8 * hs * hs)                   # column passes
+           + (8 * n * m + 8 * F * m + 8 * hs * hs)                  # last gap: field-of-view rows out
+           + (8 * F * m + 8 * F * F + 4 * F * F))                   # output row pass: o, I
+    loss = 8 * F * F + 4 * det + 4 * F * F                          # o and T in, dL/dI out
+    adj = ((8 * F * F + 4 * F * F + 8 * F * m)                      # seed row pass
+           + (8 * F * m + 8 * n * m + 8 * hs * hs)                  # first adjoint gap: FOV rows in
+           + (K - 1) * (16 * n * m + 8 * hs * hs)                   # adjoint column passes
+           + (K - 1) * (16 * n * m + 8 * n * n)                     # adjoint row passes
+           + (8 * n * m + 8 * n * n))                               # layer 1: no spectra written back
+    return {"design": nw * (fwd + loss + adj), "ideal": nw * (K + 1) * 40 * n * n}
 
 
 def kernel_family(detail, kind):
@@ -304,8 +332,9 @@ def run_ours(a):
     nw, n, m, K, F, hs = w.n_lambda, w.n, w.m, w.n_layers, w.fov, w.m // 2 + 1
     # algorithmic bytes per launch (every channel once): complex64 = 8 B
     algo = {
-        "column_forward": nw * (16 * n * m + 8 * hs * hs),
-        # the adjoint's first column pass reads only the F field-of-view rows
+        # the last forward column pass writes, and the adjoint's first reads,
+        # only the F field-of-view rows
+        "column_forward": nw * ((K - 1) * (16 * n * m + 8 * hs * hs) + (8 * F * m + 8 * n * m + 8 * hs * hs)) / K,
         "column_adjoint": nw * ((K - 1) * (16 * n * m + 8 * hs * hs) + (8 * F * m + 8 * n * m + 8 * hs * hs)) / K,
         "row_forward": nw * (16 * n * m + 8 * n * n),
         "row_adjoint": nw * (16 * n * m + 8 * n * n),
@@ -421,6 +450,15 @@ def run_ours(a):
             "gpu_launches": launches[0], "clocks": clk,
             "graph_step": {"ms_per_step": graph_ms, "value": units_per_step / (graph_ms * 1e-3),
                            "note": "forward + loss + backward replayed as one CUDA graph (dos_step)"}}
+    sb = step_bytes(w.n, w.m, w.n_layers, w.fov, w.n_lambda, getattr(w, "detector_bin", 1) or 1)
+    line["step_traffic"] = {
+        "design_bytes_per_step": sb["design"] * world, "ideal_bytes_per_step": sb["ideal"] * world,
+        "design_gbs": sb["design"] / (ms_step * 1e-3) / 1e9,
+        "design_frac_of_measured_hbm": sb["design"] / (ms_step * 1e-3) / 1e9 / hbm_peak,
+        "ideal_gbs": sb["ideal"] / (ms_step * 1e-3) / 1e9,
+        "ideal_frac_of_measured_hbm": sb["ideal"] / (ms_step * 1e-3) / 1e9 / hbm_peak,
+        "note": "whole step on one GPU: the multi-pass kernels' algorithmic bytes, and 40 N^2 B per "
+                "layer-propagation (spectra kept on chip)"}
     line["split_bf16"] = split
     if rank == 0:
         print(json.dumps(line), flush=True)

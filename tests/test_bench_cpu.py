@@ -23,3 +23,17 @@ def test_traffic_entries_cite_committed_profiles():
     for key, (bytes_per_channel, src) in bench.TRAFFIC_PER_CHANNEL.items():
         assert bytes_per_channel > 0
         assert os.path.isfile(os.path.join(ROOT, src)), (key, src)
+
+
+def test_step_bytes_structure():
+    """Each extra layer adds one forward and one adjoint row pass (spectra in
+    and out, checkpoint) and one forward and one adjoint column pass (spectra
+    in and out, a transfer-table quadrant); the ideal count is 40 N^2 bytes
+    per layer-propagation; both scale with the channels."""
+    n, m, F = 200, 400, 50
+    hs = m // 2 + 1
+    b2, b3 = bench.step_bytes(n, m, 2, F, 7), bench.step_bytes(n, m, 3, F, 7)
+    per_layer = 2 * (16 * n * m + 8 * n * n) + 2 * (16 * n * m + 8 * hs * hs)
+    assert b3["design"] - b2["design"] == 7 * per_layer
+    assert b3["ideal"] == 7 * 4 * 40 * n * n
+    assert bench.step_bytes(n, m, 5, F, 14)["design"] == 2 * bench.step_bytes(n, m, 5, F, 7)["design"]
