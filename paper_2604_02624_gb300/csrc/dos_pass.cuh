@@ -208,14 +208,17 @@ struct Pass {
     }
   }
 
-  // output plane: IDFT of the FOV rows -> o (complex) and I = |o|^2
+  // output plane: IDFT of the FOV rows -> o (complex) and I = |o|^2; a
+  // block's lines are consecutive (channel, FOV row) pairs, so no block is
+  // left with a few rows of a channel
   __device__ static void row_out(const PassArgs& a) {
     const RowCtx rc = row_ctx(a);
     const int t = rc.t;
-    const int w = blockIdx.y;
-    const int fr = blockIdx.x * ROWL + rc.l;  // FOV row
-    const bool ok = fr < a.fov;
-    const int row = a.of + (ok ? fr : 0);
+    const int line = blockIdx.x * ROWL + rc.l;
+    const bool ok = line < a.nw * a.fov;
+    const int w = ok ? line / a.fov : 0;
+    const int fr = ok ? line % a.fov : 0;  // FOV row
+    const int row = a.of + fr;
     const float2* srow = a.S + ((size_t)w * a.n + row) * M;
     float2 r[E];
 #pragma unroll
@@ -236,15 +239,16 @@ struct Pass {
   }
 
   // adjoint seed: grad_o = 2 dL/dI o on the FOV, zero elsewhere -> DFT of the FOV rows
+  // (lines as in row_out)
   __device__ static void row_seed(const PassArgs& a) {
     const RowCtx rc = row_ctx(a);
     const int t = rc.t;
-    const int w = blockIdx.y;
-    const int fr = blockIdx.x * ROWL + rc.l;
-    const bool ok = fr < a.fov;
-    const int frr = ok ? fr : 0;
-    const float2* orow = a.o + ((size_t)w * a.fov + frr) * a.fov;
-    const float* grow = a.dLdI + ((size_t)w * a.fov + frr) * a.fov;
+    const int line = blockIdx.x * ROWL + rc.l;
+    const bool ok = line < a.nw * a.fov;
+    const int w = ok ? line / a.fov : 0;
+    const int fr = ok ? line % a.fov : 0;
+    const float2* orow = a.o + ((size_t)w * a.fov + fr) * a.fov;
+    const float* grow = a.dLdI + ((size_t)w * a.fov + fr) * a.fov;
     float2 r[E];
 #pragma unroll
     for (int i = 0; i < E; ++i) {
@@ -453,12 +457,12 @@ struct PassLaunch {
                    : launch_k(k_row_first<LF, false>, g, RT, sm, a, s);
   }
   static cudaError_t row_out(const PassArgs& a, cudaStream_t s) {
-    const dim3 g(row_blocks(a.fov), a.nw);
+    const dim3 g(row_blocks(a.nw * a.fov));
     const size_t sm = PS::row_smem_bytes(PS::ROWL);
     return half(a) ? launch_k(k_row_out<LF, true>, g, RT, sm, a, s) : launch_k(k_row_out<LF, false>, g, RT, sm, a, s);
   }
   static cudaError_t row_seed(const PassArgs& a, cudaStream_t s) {
-    const dim3 g(row_blocks(a.fov), a.nw);
+    const dim3 g(row_blocks(a.nw * a.fov));
     const size_t sm = PS::row_smem_bytes(PS::ROWL);
     return half(a) ? launch_k(k_row_seed<LF, true>, g, RT, sm, a, s)
                    : launch_k(k_row_seed<LF, false>, g, RT, sm, a, s);
