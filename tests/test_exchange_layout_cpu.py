@@ -1,0 +1,75 @@
+"""The line DFT's exchange matrix (Line<P, Q, T> in csrc/dos_fft.cuh): entry
+(q, k1) lives at q * RP + k1 in the normal layout and at k1 * RP + q in the
+transposed one (RP = P + 1 for even P).  Step 1 of thread t writes the entries
+of its sub-DFTs q = t + T j; step 2 of thread t reads the entries of its
+columns k1 = t + T j.  The bulk passes drop the barrier between two line DFTs
+when the second writes in the other layout, which is safe exactly when every
+thread then overwrites only entries it read itself: these tests check that
+property for the square lines the kernels use it on, and that it fails for the
+non-square ones, where the kernels keep the barrier."""
+import pytest
+
+LINES = {16: (4, 4, 4), 32: (4, 8, 4), 64: (8, 8, 8), 128: (8, 16, 8), 200: (10, 20, 10),
+         256: (16, 16, 16), 400: (20, 20, 20), 512: (16, 32, 16)}
+
+
+def rp(P):
+    return P + 1 if P % 2 == 0 else P
+
+
+def step1_writes(P, Q, T, t, tr):
+    R = rp(P)
+    out = set()
+    for j in range(Q // T):
+        q = t + T * j
+        for k1 in range(P):
+            out.add(k1 * R + q if tr else q * R + k1)
+    return out
+
+
+def step2_reads(P, Q, T, t, tr):
+    R = rp(P)
+    out = set()
+    for j in range(P // T):
+        k1 = t + T * j
+        for q in range(Q):
+            out.add(k1 * R + q if tr else q * R + k1)
+    return out
+
+
+def thread_private(P, Q, T, first_tr):
+    """Second DFT (other layout) writes only what the same thread read in the
+    first DFT's step 2, for every thread."""
+    return all(step1_writes(P, Q, T, t, not first_tr) <= step2_reads(P, Q, T, t, first_tr)
+               for t in range(T))
+
+
+@pytest.mark.parametrize("m", [16, 64, 256, 400])
+def test_square_lines_alternating_layouts_are_thread_private(m):
+    P, Q, T = LINES[m]
+    assert P == Q == T
+    assert thread_private(P, Q, T, first_tr=False)   # normal then transposed
+    assert thread_private(P, Q, T, first_tr=True)    # transposed then normal
+    # and the transposed layout fits in the exchange buffer of Q * RP entries
+    assert max(max(step1_writes(P, Q, T, t, True)) for t in range(T)) < Q * rp(P)
+
+
+@pytest.mark.parametrize("m", [32, 128, 200, 512])
+def test_non_square_lines_need_the_barrier(m):
+    P, Q, T = LINES[m]
+    assert not (P == Q == T)
+    assert not thread_private(P, Q, T, first_tr=False)
+
+
+@pytest.mark.parametrize("m", sorted(LINES))
+def test_each_step_covers_the_matrix_once(m):
+    """Step 1 over all threads writes every entry exactly once, step 2 reads
+    every entry exactly once, in the normal layout and (square lines, the only
+    ones that use it) in the transposed one."""
+    P, Q, T = LINES[m]
+    for tr in ((False, True) if P == Q == T else (False,)):
+        w = [step1_writes(P, Q, T, t, tr) for t in range(T)]
+        r = [step2_reads(P, Q, T, t, tr) for t in range(T)]
+        assert sum(map(len, w)) == P * Q == len(set().union(*w))
+        assert sum(map(len, r)) == P * Q == len(set().union(*r))
+        assert set().union(*w) == set().union(*r)
