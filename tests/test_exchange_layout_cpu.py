@@ -73,3 +73,15 @@ def test_each_step_covers_the_matrix_once(m):
         assert sum(map(len, w)) == P * Q == len(set().union(*w))
         assert sum(map(len, r)) == P * Q == len(set().union(*r))
         assert set().union(*w) == set().union(*r)
+
+
+def test_table_matches_the_compiled_line_shapes():
+    import glob
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    found = {}
+    for f in glob.glob(os.path.join(root, "paper_2604_02624_gb300", "csrc", "pass_m*.cu")):
+        for m, p, q, t in re.findall(r"DOS_DEFINE_PASS_OPS\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),", open(f).read()):
+            found[int(m)] = (int(p), int(q), int(t))
+    assert found == LINES
