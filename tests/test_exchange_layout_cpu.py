@@ -85,3 +85,28 @@ def test_table_matches_the_compiled_line_shapes():
         for m, p, q, t in re.findall(r"DOS_DEFINE_PASS_OPS\((\d+),\s*(\d+),\s*(\d+),\s*(\d+),", open(f).read()):
             found[int(m)] = (int(p), int(q), int(t))
     assert found == LINES
+
+
+@pytest.mark.parametrize("m", sorted(LINES))
+def test_field_half_is_the_first_half_of_every_sub_dft(m):
+    """The halved (N <= M/2) line DFTs: thread t holds position t + T i in
+    r[i]; in step 1 the input pp of sub-DFT j is r[j + (Q/T) pp], in step 2
+    the output k2 of column k1 = t + T j lands in r[j + (P/T) k2] at position
+    k1 + P k2.  Positions below M/2 (the field half) are exactly i < E/2, the
+    first P/2 inputs of each first-step sub-DFT and the first Q/2 outputs of
+    each second-step one, for every thread."""
+    P, Q, T = LINES[m]
+    M, E = P * Q, P * Q // T
+    QJ, PJ = Q // T, P // T
+    for t in range(T):
+        for j in range(QJ):
+            for pp in range(P):
+                i = j + QJ * pp
+                x = t + T * i
+                assert (x < M // 2) == (pp < P // 2) == (i < E // 2)
+        for j in range(PJ):
+            k1 = t + T * j
+            for k2 in range(Q):
+                i = j + PJ * k2
+                assert t + T * i == k1 + P * k2
+                assert (k1 + P * k2 < M // 2) == (k2 < Q // 2) == (i < E // 2)
