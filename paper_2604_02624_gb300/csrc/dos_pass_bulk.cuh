@@ -1,23 +1,26 @@
 // dos_pass_bulk.cuh - the multi-pass row and column passes with bulk-async prefetch.
 //
 // Same arithmetic as dos_pass.cuh; what changes is how the input reaches the
-// block.  Blocks are persistent over several work items and the bulk-copy
-// engine (cp.async.bulk global -> shared, completion counted in bytes on an
+// block.  Blocks loop over several work items and the bulk-copy engine
+// (cp.async.bulk global -> shared, completion counted in bytes on an
 // mbarrier) fetches the next item while the block computes the current one:
-//   column pass : item = a tile of COLL columns of one channel; one tensor
-//                 copy (TMA) of the box {COLL columns, N rows} of the spectra;
+//   column pass : item = a tile of COLL columns of one channel (persistent
+//                 blocks); one tensor copy (TMA) of the box {COLL columns,
+//                 input rows} of the spectra;
 //   row passes  : item = the block's RL rows of the next channel of its chunk;
-//                 one cp.async.bulk of M * 8 bytes per row (rows padded in
-//                 shared memory against bank conflicts).
-// One staging buffer per block suffices: the item is moved from the stage to
+//                 one cp.async.bulk per row (rows padded in shared memory
+//                 against bank conflicts): spectra rows, the rows of the
+//                 input-field table in the first forward pass, and spectra
+//                 plus checkpoint rows in the adjoint pass.
+// One staging buffer per input suffices: the item is moved from the stage to
 // registers and the next copy is issued at the first block barrier after
 // that (the one inside the item's first line DFT), so the copy overlaps most
 // of the item's DFT / modulation / DFT / store.
 // Every wait is bounded (one second of global time): when it expires the
 // block issues no further copy, leaves its loop, waits once more (bounded)
-// for the copy it was waiting for (its only one in flight) and sets *err.  PassArgs::stall (fault injection
-// for tests) makes the blocks announce their bytes without copying them, so
-// that the first wait of every block expires.
+// for the copy it was waiting for (its only one in flight) and sets *err.
+// PassArgs::stall (fault injection for tests) makes the blocks announce their
+// bytes without copying them, so that the first wait of every block expires.
 #pragma once
 
 #include <cuda.h>
@@ -209,7 +212,9 @@ struct PassBulk {
 
   // Rows [blockIdx.x * RL, +RL) of the channels of chunk blockIdx.y.
   //   ADJ false : forward layer pass (as Pass::row_fwd), FLAG = save the checkpoint
-  //   ADJ true  : adjoint layer pass (as Pass::row_adj), FLAG = first layer
+  //   ADJ true  : adjoint layer pass (as Pass::row_adj), FLAG = first layer; it
+  //               runs only for odd N (the checkpoint rows are then not 16-byte
+  //               multiples and are read directly), row_adj_staged otherwise
   template <bool ADJ, bool FLAG>
   __device__ static void row(const PassArgs& a) {
     extern __shared__ __align__(16) float2 smem[];
