@@ -35,13 +35,14 @@ sys.path.insert(0, ROOT)
 # the bench scales them to the launch's channels.  An entry must be removed
 # (traffic reported as null) when its kernel changes.
 TRAFFIC_PER_CHANNEL = {
-    # TMA column pass with packed butterflies: forward 1.4017 MB (gaps 1..K-1) and
-    # 1.0758 MB (last gap, field-of-view output rows); adjoint 0.9168 MB (first
-    # gap, field-of-view input rows) and 1.4020 MB (the other K - 1 gaps)
-    ("column_bulk", 200, 400, "column_forward"): ((4 * 1.401686e6 + 1.075750e6) / 5,
-                                                  "profiles/column_pass_bulk_batched.md"),
-    ("column_bulk", 200, 400, "column_adjoint"): ((0.916752e6 + 4 * 1.401998e6) / 5,
-                                                  "profiles/column_pass_bulk_batched.md"),
+    # TMA column pass with packed butterflies, all ten column launches of one step
+    # captured: forward 1.4013 / 1.3898 / 1.3909 / 1.3905 MB and 1.0654 MB (last gap,
+    # field-of-view output rows); adjoint 0.9047 MB (first gap, field-of-view
+    # input rows) and 1.3905 / 1.3901 / 1.3913 / 1.3902 MB
+    ("column_bulk", 200, 400, "column_forward"): ((1.401272e6 + 1.389845e6 + 1.390920e6 + 1.390511e6
+                                                   + 1.065403e6) / 5, "profiles/column_pass_bulk_batched.md"),
+    ("column_bulk", 200, 400, "column_adjoint"): ((0.904732e6 + 1.390524e6 + 1.390091e6 + 1.391332e6
+                                                   + 1.390215e6) / 5, "profiles/column_pass_bulk_batched.md"),
 }
 
 
