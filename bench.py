@@ -337,8 +337,10 @@ def run_ours(a):
         # only the F field-of-view rows
         "column_forward": nw * ((K - 1) * (16 * n * m + 8 * hs * hs) + (8 * F * m + 8 * n * m + 8 * hs * hs)) / K,
         "column_adjoint": nw * ((K - 1) * (16 * n * m + 8 * hs * hs) + (8 * F * m + 8 * n * m + 8 * hs * hs)) / K,
-        "row_forward": nw * (16 * n * m + 8 * n * n),
-        "row_adjoint": nw * (16 * n * m + 8 * n * n),
+        # the first forward row pass reads the v1 table (N x N) instead of
+        # spectra; layer 1's adjoint row pass writes no spectra back
+        "row_forward": nw * ((K - 1) * (16 * n * m + 8 * n * n) + (8 * n * n + 8 * n * m)) / K,
+        "row_adjoint": nw * ((K - 1) * (16 * n * m + 8 * n * n) + (8 * n * m + 8 * n * n)) / K,
         # fused sweeps: checkpoints, transfer table, output field / seed
         "fused_forward": nw * (8 * K * n * n + 8 * hs * hs + 12 * F * F),
         "fused_adjoint": nw * (8 * K * n * n + 8 * hs * hs + 12 * F * F),
