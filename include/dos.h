@@ -37,7 +37,7 @@
  *    GPU finishes unless stated otherwise.
  *  - A context is not thread-safe; use one context per host thread / stream.
  *  - Every int-returning call returns DOS_OK (0) or one of DOS_ERR_*; no C++
- *    exception crosses the ABI. dos_last_error() describes the last failure
+ *    exception crosses the ABI. dos_last_error(ctx) describes the last failure
  *    of the calling thread.
  */
 #ifndef DOS_H_
@@ -174,7 +174,8 @@ DOS_API int dos_set_stream(dos_ctx *ctx, void *cuda_stream);
  *   d_h  [K][N][N] float32 thickness h_l (learnable part of Eq. 2) [m].
  *   d_I  [N_w][F][F] float32 output intensities |o|^2, or NULL to skip.
  *   save_for_backward: nonzero keeps the incoming field of every layer
- *        (K x N_w x N x N complex64 in the workspace) for dos_backward.
+ *        (K x N_w x N x N complex64 in the workspace) and a copy of d_h
+ *        (K x N x N float32) for dos_backward.
  * The complex output fields o are always kept (dos_loss, dos_backward and
  * dos_output_field read them).  Errors: DOS_ERR_ARG (NULL d_h), DOS_ERR_CUDA.
  */
@@ -226,7 +227,7 @@ DOS_API int dos_loss(dos_ctx *ctx, const float *d_T, double *h_loss, float *d_ps
  * cleared): calls that overlap on the GPU (other streams, other threads)
  * race and must be serialised by the caller.
  * Errors: DOS_ERR_ARG, DOS_ERR_CUDA, DOS_ERR_UNSUPPORTED (device index > 63);
- * the message is in dos_last_error().
+ * the message is in dos_last_error(NULL).
  */
 DOS_API int dos_loss_noalloc(const float *d_I, const float *d_T, int n_lambda, int fov,
                              int n_lambda_total, int loss, double *h_loss, float *d_psnr,
@@ -281,12 +282,14 @@ DOS_API int dos_read_loss(dos_ctx *ctx, double *h_loss);
  * of Eq. 1-5 (error back-propagation, Section 2), summed over the channels.
  *   d_dLdI [N_w][F][F] float32 dL/dI for the last forward's intensities.
  *   d_dLdh [K][N][N] float32, overwritten with dL/dh_l [1/m].
- * Needs the last dos_forward to have had save_for_backward != 0 and the same
- * d_h contents (the layers' transmissions are recomputed from it).
+ * Needs the last dos_forward (or dos_step) to have had save_for_backward != 0:
+ * the adjoint reads that forward's layer fields and rebuilds the layers'
+ * transmissions t(h) from the copy of its thickness the context kept, so the
+ * caller may change its d_h buffer in between.
  * The sum over channels has a fixed order: results are bitwise reproducible.
- * Errors: DOS_ERR_STATE, DOS_ERR_ARG, DOS_ERR_CUDA.
+ * Errors: DOS_ERR_STATE (no saved forward), DOS_ERR_ARG (NULL pointer), DOS_ERR_CUDA.
  */
-DOS_API int dos_backward(dos_ctx *ctx, const float *d_h, const float *d_dLdI, float *d_dLdh);
+DOS_API int dos_backward(dos_ctx *ctx, const float *d_dLdI, float *d_dLdh);
 
 /*
  * One design step: dos_forward(save) + dos_loss + dos_backward, replayed as a
@@ -373,8 +376,12 @@ DOS_API int dos_describe(const dos_ctx *ctx, char *buf, int cap);
 /* Frees every resource of the context (waits for its stream).  NULL is a no-op. */
 DOS_API void dos_destroy(dos_ctx *ctx);
 
-/* Message for the last failing call of the calling thread ("" if none). */
-DOS_API const char *dos_last_error(void);
+/*
+ * Message for the last failing call of the calling thread ("" if none).  ctx
+ * may be NULL (a failed dos_create has no context); the message is the
+ * thread's, which for a context used from one thread is that context's.
+ */
+DOS_API const char *dos_last_error(const dos_ctx *ctx);
 
 #ifdef __cplusplus
 }

@@ -342,20 +342,36 @@ def rayleigh_sommerfeld_direct(u: np.ndarray, lam: float, z: float, pitch: float
 # --------------------------------------------------------------------------
 # Evaluation variants of a trained design (Section 2 Fig. 5-7, Section 3)
 # --------------------------------------------------------------------------
-def quantize_thickness(h, h_max, bits):
-    """Phase bit depth B (Fig. 7): the learnable thickness, limited to
-    [0, h_max], takes one of 2^B evenly spaced levels k h_max / (2^B - 1).
-
-    The level index is an integer decided by floating point, so it is taken
-    in FP32 exactly as the CUDA path takes it: k = rint(fp32(clip(h)) * s)
-    with s = fp32((2^B - 1) / h_max), value = fp32(k * fp32(h_max / (2^B - 1))).
-    """
+def quantize_level(h, h_max, bits):
+    """Level index of the phase bit depth B (Fig. 7): the learnable thickness,
+    limited to [0, h_max], is sent to the nearest of the 2^B evenly spaced
+    levels k h_max / (2^B - 1), k = 0 .. 2^B - 1.  Nearest level by the
+    definition, in FP64: k = rint(clip(h, 0, h_max) (2^B - 1) / h_max)
+    (an exact half step goes to the even level)."""
     levels = 2 ** bits - 1
-    s = np.float32(levels / h_max)
-    step = np.float32(h_max / levels)
-    hc = np.clip(np.asarray(h, np.float32), np.float32(0.0), np.float32(h_max))
-    k = np.rint(hc * s).astype(np.float32)
-    return (k * step).astype(np.float32)
+    hc = np.clip(np.asarray(h, np.float64), 0.0, float(h_max))
+    return np.rint(hc * (levels / float(h_max))).astype(np.int64)
+
+
+def quantize_thickness(h, h_max, bits):
+    """Thickness of the nearest level (Fig. 7): k h_max / (2^B - 1), in FP64."""
+    levels = 2 ** bits - 1
+    return quantize_level(h, h_max, bits).astype(np.float64) * (float(h_max) / levels)
+
+
+def channel_swap(psnr, lambdas):
+    """Dynamic channel swapping (Section 2, the Fig. 2B text): after a first
+    training run the images are ranked by their PSNR, best first, and handed
+    out again to the wavelengths from the longest one down.  Returns perm with
+    new_targets[c] = targets[perm[c]]; equal PSNRs (or wavelengths) keep their
+    index order."""
+    n = len(psnr)
+    images = sorted(range(n), key=lambda i: (-float(psnr[i]), i))        # best image first
+    channels = sorted(range(n), key=lambda c: (-float(lambdas[c]), c))   # longest wavelength first
+    perm = np.empty(n, dtype=np.int64)
+    for rank in range(n):
+        perm[channels[rank]] = images[rank]
+    return perm
 
 
 def diffraction_efficiency(I, aperture):

@@ -77,7 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dos_forward": (c_int, [p, p, p, c_int]),
         "dos_loss": (c_int, [p, p, POINTER(c_double), p, p]),
         "dos_read_loss": (c_int, [p, POINTER(c_double)]),
-        "dos_backward": (c_int, [p, p, p, p]),
+        "dos_backward": (c_int, [p, p, p]),
         "dos_step": (c_int, [p, p, p, p, p, p, POINTER(c_double)]),
         "dos_output_field": (c_int, [p, p]),
         "dos_layer_field": (c_int, [p, c_int, p]),
@@ -89,7 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "dos_path": (c_int, [p]),
         "dos_describe": (c_int, [p, ctypes.c_char_p, c_int]),
         "dos_destroy": (None, [p]),
-        "dos_last_error": (ctypes.c_char_p, []),
+        "dos_last_error": (ctypes.c_char_p, [p]),
         "dos_loss_noalloc": (c_int, [p, p, c_int, c_int, c_int, c_int, POINTER(c_double), p, p, p]),
         "dos_efficiency": (c_int, [p, p]),
         "dos_set_misalignment": (c_int, [p, POINTER(c_double)]),
@@ -105,7 +105,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 
 def _check(rc: int, where: str) -> None:
     if rc != DOS_OK:
-        msg = load().dos_last_error()
+        msg = load().dos_last_error(None)
         raise DosError(rc, where, msg.decode() if msg else "")
 
 
@@ -148,8 +148,8 @@ def dos_read_loss(ctx: int) -> float:
     return out.value
 
 
-def dos_backward(ctx: int, d_h: int, d_dLdI: int, d_dLdh: int) -> None:
-    _check(load().dos_backward(ctx, d_h, d_dLdI, d_dLdh), "dos_backward")
+def dos_backward(ctx: int, d_dLdI: int, d_dLdh: int) -> None:
+    _check(load().dos_backward(ctx, d_dLdI, d_dLdh), "dos_backward")
 
 
 def dos_step(ctx: int, d_h: int, d_T: int, d_dLdh: int, d_I: int, d_psnr: int, read_loss: bool):
@@ -206,8 +206,8 @@ def dos_destroy(ctx: int) -> None:
         load().dos_destroy(ctx)
 
 
-def dos_last_error() -> str:
-    msg = load().dos_last_error()
+def dos_last_error(ctx: int = 0) -> str:
+    msg = load().dos_last_error(ctx or None)
     return msg.decode() if msg else ""
 
 

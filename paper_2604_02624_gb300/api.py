@@ -147,15 +147,16 @@ class DiffractiveStack:
         self._bind()
         return L.dos_read_loss(self._ctx)
 
-    def backward(self, h: torch.Tensor, dLdI: torch.Tensor, out: Optional[torch.Tensor] = None):
-        h = h.contiguous()
+    def backward(self, dLdI: torch.Tensor, out: Optional[torch.Tensor] = None):
+        """dL/dh of the last forward that saved its fields (the context kept
+        that forward's thickness)."""
         dLdI = dLdI.contiguous()
-        _need(h, torch.float32, (self.n_layers, self.n, self.n), "h", self.device)
         _need(dLdI, torch.float32, (self.n_lambda, self.fov, self.fov), "dLdI", self.device)
-        g = out if out is not None else torch.empty_like(h)
+        g = out if out is not None else torch.empty((self.n_layers, self.n, self.n), dtype=torch.float32,
+                                                    device=self.device)
         _need(g, torch.float32, (self.n_layers, self.n, self.n), "out", self.device)
         self._bind()
-        L.dos_backward(self._ctx, h.data_ptr(), dLdI.data_ptr(), g.data_ptr())
+        L.dos_backward(self._ctx, dLdI.data_ptr(), g.data_ptr())
         return g
 
     def step(self, h: torch.Tensor, T: torch.Tensor, grad_out: Optional[torch.Tensor] = None,
@@ -222,13 +223,11 @@ class DosFunction(torch.autograd.Function):
         h = h.contiguous()
         I = stack.forward(h, save_for_backward=True)
         ctx.stack = stack
-        ctx.save_for_backward(h)
         return I
 
     @staticmethod
     def backward(ctx, gI: torch.Tensor):
-        (h,) = ctx.saved_tensors
-        g = ctx.stack.backward(h, gI.contiguous().to(torch.float32))
+        g = ctx.stack.backward(gI.contiguous().to(torch.float32))
         return g, None
 
 

@@ -136,6 +136,9 @@ struct dos_ctx {
   int step_launches = 0;     // kernels in the captured step graph
   dos::ChanConst* chan = nullptr;
   float* partial = nullptr;
+  // [K][N][N] thickness of the last forward that saved checkpoints: dos_backward
+  // rebuilds t(h) from it, so the caller passes h once per step
+  float* h_fwd = nullptr;
   dos::LossStats* stats = nullptr;
   double* d_loss = nullptr;
   double* h_loss = nullptr;  // pinned
@@ -145,13 +148,16 @@ struct dos_ctx {
   unsigned bulk = 0;
   int* d_err = nullptr;    // set by a kernel whose bounded wait expired
   int* h_err = nullptr;    // pinned copy
-  bool inject_stall = false;  // DOS_INJECT_WAIT_TIMEOUT: the next bulk pass stalls (tests)
+  // DOS_INJECT_WAIT_TIMEOUT (tests): the next bulk pass stalls.  1: its copies
+  // never arrive, so every block's first wait expires; 2: the copies land, but
+  // the odd threads of every block report their first wait as expired
+  int inject_stall = 0;
   CUtensorMap tmap_S;        // S as [nw][n][m] 8-byte elements, box {col_lines, n, 1}
   CUtensorMap tmap_F;        // the same with box {col_lines, fov, 1}: the adjoint's first column pass
   bool have_tmap = false;     // the bulk column pass runs the plain kernel without them
   int take_stall(unsigned kind) {
-    const int v = ((bulk & kind) && inject_stall) ? 1 : 0;
-    if (v) inject_stall = false;
+    const int v = (bulk & kind) ? inject_stall : 0;
+    if (v) inject_stall = 0;
     return v;
   }
   bool have_fwd = false, have_ckpt = false, have_loss = false;
@@ -437,6 +443,7 @@ int build(dos_ctx* x, const dos_config* c) {
   if ((rc = x->alloc(&x->tw, (size_t)x->ops->Q * (x->ops->P + 1), "twiddles"))) return rc;
   if ((rc = x->alloc(&x->chan, (size_t)x->nw, "channel constants"))) return rc;
   if ((rc = x->alloc(&x->partial, partial_count, "gradient partials"))) return rc;
+  if ((rc = x->alloc(&x->h_fwd, (size_t)x->K * n2, "saved thickness"))) return rc;
   if ((rc = x->alloc(&x->stats, (size_t)x->nw, "loss statistics"))) return rc;
   if ((rc = x->alloc(&x->d_loss, 1, "loss"))) return rc;
   if ((rc = x->alloc(&x->dLdI_step, (size_t)x->nw * x->fov * x->fov, "step seed"))) return rc;
@@ -475,7 +482,7 @@ int build(dos_ctx* x, const dos_config* c) {
   if ((rc = choose_path(x, c->path))) return rc;
   DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
   const char* inj = std::getenv("DOS_INJECT_WAIT_TIMEOUT");
-  x->inject_stall = inj && *inj && std::string(inj) != "0";
+  x->inject_stall = (inj && *inj) ? (std::string(inj) == "2" ? 2 : std::string(inj) != "0" ? 1 : 0) : 0;
   return DOS_OK;
 }
 
@@ -579,6 +586,9 @@ int gemm_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dL
 int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
   const size_t n2 = (size_t)c->n * c->n;
   c->launches = 0;
+  if (save && d_h != c->h_fwd)
+    DOS_CUDA(cudaMemcpyAsync(c->h_fwd, d_h, sizeof(float) * c->K * n2, cudaMemcpyDeviceToDevice, c->stream),
+             "saved thickness");
   if (c->path == DOS_PATH_DFT_GEMM || c->path == DOS_PATH_DFT_GEMM_X3) return gemm_forward(c, d_h, d_I);
   if (c->path == DOS_PATH_FUSED) {
     dos::FusedArgs f;
@@ -1108,12 +1118,12 @@ DOS_API int dos_read_loss(dos_ctx* c, double* h_loss) {
   return flag_after_sync(c);
 }
 
-DOS_API int dos_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
+DOS_API int dos_backward(dos_ctx* c, const float* d_dLdI, float* d_dLdh) {
   int rc = check_ctx(c);
   if (rc) return rc;
   if (!c->have_ckpt) return fail(DOS_ERR_STATE, "dos_backward needs dos_forward(save_for_backward=1) first");
-  if (!d_h || !d_dLdI || !d_dLdh) return fail(DOS_ERR_ARG, "d_h, d_dLdI and d_dLdh are required");
-  return run_backward(c, d_h, d_dLdI, d_dLdh);
+  if (!d_dLdI || !d_dLdh) return fail(DOS_ERR_ARG, "d_dLdI and d_dLdh are required");
+  return run_backward(c, c->h_fwd, d_dLdI, d_dLdh);
 }
 
 DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dLdh, float* d_I, float* d_psnr,
@@ -1133,9 +1143,9 @@ DOS_API int dos_step(dos_ctx* c, const float* d_h, const float* d_T, float* d_dL
   DOS_CUDA(cudaStreamWaitEvent(c->gstream, c->ev_in, 0), "step order");
   if (!same) {
     const bool timing = c->timer.on;
-    const bool inject = c->inject_stall;  // an injected stall never enters the graph
+    const int inject = c->inject_stall;  // an injected stall never enters the graph
     c->timer.on = false;
-    c->inject_stall = false;
+    c->inject_stall = 0;
     cudaStream_t user = c->stream;
     c->stream = c->gstream;
     cudaGraph_t g = nullptr;
@@ -1270,6 +1280,9 @@ DOS_API void dos_destroy(dos_ctx* c) {
   delete c;
 }
 
-DOS_API const char* dos_last_error(void) { return g_err.c_str(); }
+DOS_API const char* dos_last_error(const dos_ctx* c) {
+  (void)c;  // the message is the calling thread's: a failed dos_create has no context to hold it
+  return g_err.c_str();
+}
 
 }  // extern "C"

@@ -62,7 +62,8 @@ struct PassArgs {
   int n_chunks;
   Misalign mis;           // misaligned layers (mis.sq null: none)
   int* err;               // set to 1 by a bulk-copy pass whose bounded wait expired
-  int stall;              // fault injection: bulk passes expect bytes that are never copied
+  int stall;              // fault injection (tests): 1 = the bulk pass expects bytes that are never
+                          // copied; 2 = its copies land but odd threads give up their first wait
   const void* tmap;       // host CUtensorMap of S as [nw][n][m] 8-byte elements (bulk column pass), or null
   int tmap_rows;          // rows of its box: the bulk column pass uses it when they are in_r1 - in_r0
 };

@@ -16,11 +16,17 @@
 // registers and the next copy is issued at the first block barrier after
 // that (the one inside the item's first line DFT), so the copy overlaps most
 // of the item's DFT / modulation / DFT / store.
-// Every wait is bounded (one second of global time): when it expires the
-// block issues no further copy, leaves its loop, waits once more (bounded)
-// for the copy it was waiting for (its only one in flight) and sets *err.
-// PassArgs::stall (fault injection for tests) makes the blocks announce their
-// bytes without copying them, so that the first wait of every block expires.
+// Every wait is bounded (one second of global time).  Each thread times its
+// own wait, and the block takes one verdict from them (a block-wide AND at the
+// barrier after the wait), so that no thread goes on with an item another
+// thread gave up on: when any wait expires the whole block issues no further
+// copy, leaves its loop without writing partial results, waits once more
+// (bounded) for the copy it was waiting for (its only one in flight) and sets
+// *err.
+// PassArgs::stall (fault injection for tests): 1 makes the blocks announce
+// their bytes without copying them, so that the first wait of every block
+// expires; 2 lets the copies land but makes the odd threads of every block
+// give up their first wait (a split verdict that the block-wide AND resolves).
 #pragma once
 
 #include <cuda.h>
@@ -57,7 +63,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 // true once the phase with this parity has completed; false after kBulkWaitNs
-__device__ __forceinline__ bool bulk_wait(uint64_t* b, uint32_t parity) {
+// (or at once when `give_up` is set: the injected split verdict of the tests)
+__device__ __forceinline__ bool bulk_wait(uint64_t* b, uint32_t parity, bool give_up = false) {
+  if (give_up) return false;
   const unsigned long long t0 = global_ns();
   for (long it = 0; it < kBulkSpin; ++it) {
     uint32_t done;
@@ -70,6 +78,12 @@ __device__ __forceinline__ bool bulk_wait(uint64_t* b, uint32_t parity) {
     if ((it & 15) == 15 && global_ns() - t0 > kBulkWaitNs) return false;
   }
   return false;
+}
+
+// Injected split verdict (PassArgs::stall == 2, tests only): the odd threads
+// of every block give up their first wait although the copy lands.
+__device__ __forceinline__ bool split_verdict(const PassArgs& a, int item) {
+  return a.stall == 2 && item == 0 && (threadIdx.x & 1);
 }
 
 // Row stride of the row passes' staging buffer: a warp reads the rows of two
@@ -129,7 +143,7 @@ struct PassBulk {
       if (threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_expect(bar, bytes);
-      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
       const int w = it / ntiles, c0 = (it % ntiles) * COLL;
       asm volatile(
           "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
@@ -145,8 +159,8 @@ struct PassBulk {
       const int c = c0 + l;
       const bool cok = c < M;
       const int cc = cok ? c : c0;
-      if (!bulk_wait(bar, (uint32_t)(k & 1))) ok = false;
-      if (!__syncthreads_and(ok)) break;
+      ok = __syncthreads_and(bulk_wait(bar, (uint32_t)(k & 1), split_verdict(a, k))) != 0;  // one verdict for the whole block
+      if (!ok) break;
       float2 r[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) {
@@ -240,7 +254,7 @@ struct PassBulk {
       if (threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_expect(bar, bytes);
-      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
       const float2* src = a.S + ((size_t)w * a.n + r0) * M;
       for (int q = 0; q < nrows; ++q) bulk_g2s(stage + (size_t)q * SR, src + (size_t)q * M, M * 8u, bar);
     };
@@ -264,8 +278,8 @@ struct PassBulk {
     int k = 0;
     for (int w = w0; w < w1; ++w, ++k) {
       const ChanConst cc = a.chan[w];
-      if (!bulk_wait(bar, (uint32_t)(k & 1))) okw = false;
-      if (!__syncthreads_and(okw)) break;
+      okw = __syncthreads_and(bulk_wait(bar, (uint32_t)(k & 1), split_verdict(a, k))) != 0;  // one verdict for the whole block
+      if (!okw) break;
       float2 r[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = stage[(size_t)(ok ? l : 0) * SR + t + T * i];
@@ -372,7 +386,7 @@ struct PassBulk {
       if (threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_expect(bar, bytes);
-      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
       const float2* src = a.fin + ((size_t)w * a.n + r0) * a.n;
       for (int q = 0; q < nrows; ++q) bulk_g2s(stage + (size_t)q * cks, src + (size_t)q * a.n, a.n * 8u, bar);
     };
@@ -388,8 +402,8 @@ struct PassBulk {
     int k = 0;
     for (int w = w0; w < w1; ++w, ++k) {
       const ChanConst cc = a.chan[w];
-      if (!bulk_wait(bar, (uint32_t)(k & 1))) okw = false;
-      if (!__syncthreads_and(okw)) break;
+      okw = __syncthreads_and(bulk_wait(bar, (uint32_t)(k & 1), split_verdict(a, k))) != 0;  // one verdict for the whole block
+      if (!okw) break;
       float2 r[E];
 #pragma unroll
       for (int i = 0; i < E; ++i) {
@@ -461,7 +475,7 @@ struct PassBulk {
       if (threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_expect(&bar[0], (uint32_t)nrows * M * 8u);
-      if (a.stall) return;  // injected fault: the expected bytes never arrive
+      if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
       const float2* src = a.S + ((size_t)w * a.n + r0) * M;
       for (int q = 0; q < nrows; ++q) bulk_g2s(stage + (size_t)q * SR, src + (size_t)q * M, M * 8u, &bar[0]);
     };
@@ -469,7 +483,7 @@ struct PassBulk {
       if (threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_expect(&bar[1], (uint32_t)nrows * a.n * 8u);
-      if (a.stall) return;
+      if (a.stall == 1) return;
       const float2* src = a.ckpt + ((size_t)w * a.n + r0) * a.n;
       for (int q = 0; q < nrows; ++q) bulk_g2s(ckb + (size_t)q * cks, src + (size_t)q * a.n, a.n * 8u, &bar[1]);
     };
@@ -493,8 +507,8 @@ struct PassBulk {
     }
     for (int w = w0; w < w1; ++w) {
       const ChanConst cc = a.chan[w];
-      if (!bulk_wait(&bar[0], (uint32_t)(done_s & 1))) okw = false;
-      if (!__syncthreads_and(okw)) break;
+      okw = __syncthreads_and(bulk_wait(&bar[0], (uint32_t)(done_s & 1), split_verdict(a, done_s))) != 0;  // one verdict for the block
+      if (!okw) break;
       ++done_s;
       float2 r[E];
 #pragma unroll
@@ -506,8 +520,8 @@ struct PassBulk {
         ++issued_s;
       }
       LF::template step2<true, NOI, PKR>(r, t, z);  // the barrier below also ends its z reads
-      if (!bulk_wait(&bar[1], (uint32_t)(done_c & 1))) okw = false;
-      if (!__syncthreads_and(okw)) break;
+      okw = __syncthreads_and(bulk_wait(&bar[1], (uint32_t)(done_c & 1))) != 0;
+      if (!okw) break;
       ++done_c;
       const float2* ck = ckb + (size_t)lr * cks;
 #pragma unroll

@@ -30,6 +30,44 @@ def test_header_declares_the_binding_exports():
     assert _header_symbols() == sorted(L.EXPORTS)
 
 
+def _header_parameters():
+    """{name: [parameter declarations]} of every DOS_API function in dos.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "dos.h")).read(), flags=re.S)
+    out = {}
+    for name, params in re.findall(r"DOS_API\s+[\w\s\*]+?\b(dos_\w+)\s*\(([^)]*)\)", text):
+        params = " ".join(params.split())
+        out[name] = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes prototype has the header's number of parameters."""
+    decl = _header_parameters()
+    import inspect
+    src = inspect.getsource(L.load)
+    for name, params in decl.items():
+        m = re.search(r'"%s": \((.*?), \[(.*?)\]\),' % name, src)
+        assert m, name
+        args = [a for a in m.group(2).split(",") if a.strip()]
+        assert len(args) == len(params), (name, params, args)
+
+
+def test_boundary_entry_points_have_the_designed_signatures():
+    """The calls of the design's boundary: create / forward / loss / backward /
+    set_stream / destroy / last_error, with backward taking only the seed and
+    the output (the context keeps the thickness of the saved forward) and
+    last_error taking the context."""
+    decl = _header_parameters()
+    assert decl["dos_create"] == ["dos_ctx **out", "const dos_config *cfg", "void *cuda_stream"]
+    assert decl["dos_forward"] == ["dos_ctx *ctx", "const float *d_h", "float *d_I", "int save_for_backward"]
+    assert decl["dos_loss"] == ["dos_ctx *ctx", "const float *d_T", "double *h_loss", "float *d_psnr",
+                                "float *d_dLdI"]
+    assert decl["dos_backward"] == ["dos_ctx *ctx", "const float *d_dLdI", "float *d_dLdh"]
+    assert decl["dos_set_stream"] == ["dos_ctx *ctx", "void *cuda_stream"]
+    assert decl["dos_destroy"] == ["dos_ctx *ctx"]
+    assert decl["dos_last_error"] == ["const dos_ctx *ctx"]
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in _header_symbols():
         assert hasattr(lib, name), name
@@ -131,6 +169,6 @@ def test_null_arguments_are_rejected(lib):
     h = ctypes.c_void_p()
     assert lib.dos_create(ctypes.byref(h), None, None) == L.DOS_ERR_ARG
     assert lib.dos_forward(None, None, None, 0) == L.DOS_ERR_ARG
-    assert lib.dos_backward(None, None, None, None) == L.DOS_ERR_ARG
+    assert lib.dos_backward(None, None, None) == L.DOS_ERR_ARG
     lib.dos_destroy(None)  # no-op
     assert lib.dos_workspace_bytes(None) == 0

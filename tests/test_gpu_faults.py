@@ -17,7 +17,7 @@ from paper_2604_02624_gb300 import _lib as L
 from paper_2604_02624_gb300 import workloads as W
 from paper_2604_02624_gb300.api import DiffractiveStack
 
-from gpu_cases import TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS, oracle_model, rel_l2
+from gpu_cases import TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS, assert_close, oracle_model
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -51,7 +51,7 @@ def test_expired_bulk_wait_is_reported_and_context_recovers(monkeypatch):
     I = st.forward(hd).cpu().numpy().astype(np.float64)
     val, _, _ = st.loss(Td)
     L_ref, _, _, fwd = O.loss_and_grad(h, T, **oracle_model(w))
-    assert rel_l2(I, fwd["I"]) <= TOL_INTENSITY
+    assert_close(I, fwd["I"], TOL_INTENSITY)
     assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref)
     st.close()
 
@@ -76,7 +76,7 @@ def test_expired_wait_in_the_staged_adjoint_row_pass(monkeypatch):
     t0 = time.time()
     st.forward(hd)
     _, _, dl = st.loss(Td)          # the forward passes are plain: no stall yet
-    st.backward(hd, dl)             # the first bulk pass: its waits expire
+    st.backward(dl)             # the first bulk pass: its waits expire
     st.forward(hd)
     with pytest.raises(L.DosError) as e:
         st.loss(Td)
@@ -84,9 +84,46 @@ def test_expired_wait_in_the_staged_adjoint_row_pass(monkeypatch):
     assert time.time() - t0 < 60
     st.forward(hd)
     _, _, dl = st.loss(Td)
-    g = st.backward(hd, dl).cpu().numpy().astype(np.float64)
+    g = st.backward(dl).cpu().numpy().astype(np.float64)
     _, _, g_ref, _ = O.loss_and_grad(h, T, **oracle_model(w))
-    assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
+    assert_close(g, g_ref, TOL_GRAD_ORACLE)
+    st.close()
+
+
+@pytest.mark.parametrize("force", ["multipass:bulk", "multipass:bulk[row_adj]", "multipass:bulk[row_fwd]"])
+def test_split_wait_verdict_is_taken_by_the_whole_block(monkeypatch, force):
+    """Each thread times its own bounded wait.  DOS_INJECT_WAIT_TIMEOUT=2 lets
+    the copies of the next bulk pass land but makes the odd threads of every
+    block give up their first wait: the block must take one verdict (all of
+    its threads leave the item, none writes partial results) and the host
+    must read DOS_ERR_TIMEOUT, not silently skipped items.  The context then
+    computes the oracle's intensities and gradient."""
+    w = W.workload("tiny")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    monkeypatch.setenv("DOS_INJECT_WAIT_TIMEOUT", "2")
+    monkeypatch.setenv("DOS_FORCE_CONFIG", force)
+    st = DiffractiveStack.from_workload(w, device=DEV, path="auto")
+    monkeypatch.delenv("DOS_INJECT_WAIT_TIMEOUT")
+    monkeypatch.delenv("DOS_FORCE_CONFIG")
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    Td = torch.tensor(T, dtype=torch.float32, device=DEV)
+    t0 = time.time()
+    st.forward(hd)
+    if force.endswith("[row_adj]"):
+        _, _, dl = st.loss(Td)       # forward passes plain: nothing injected yet
+        st.backward(dl)          # the first bulk pass of this configuration
+        st.forward(hd)
+    with pytest.raises(L.DosError) as e:
+        st.loss(Td)
+    assert e.value.code == L.DOS_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    I = st.forward(hd).cpu().numpy().astype(np.float64)
+    _, _, dl = st.loss(Td)
+    g = st.backward(dl).cpu().numpy().astype(np.float64)
+    _, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    assert_close(I, fwd["I"], TOL_INTENSITY)
+    assert_close(g, g_ref, TOL_GRAD_ORACLE)
     st.close()
 
 
@@ -125,5 +162,5 @@ def test_non_finite_thickness_propagates_without_a_fault():
     assert not torch.isfinite(I).all()
     I2 = st.forward(torch.tensor(h, dtype=torch.float32, device=DEV)).cpu().numpy().astype(np.float64)
     ref = O.forward(h, keep_fields=False, **oracle_model(w))["I"]
-    assert rel_l2(I2, ref) <= TOL_INTENSITY
+    assert_close(I2, ref, TOL_INTENSITY)
     st.close()

@@ -11,7 +11,7 @@ from paper_2604_02624_gb300 import _lib as L
 from paper_2604_02624_gb300 import workloads as W
 from paper_2604_02624_gb300.api import DiffractiveStack, detuning_psnr, quantize_thickness
 
-from gpu_cases import TOL_INTENSITY, oracle_model, rel_l2
+from gpu_cases import TOL_INTENSITY, assert_close, oracle_model
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -27,12 +27,32 @@ def _built():
 
 
 @pytest.mark.parametrize("bits", [1, 4, 6, 8, 16])
-def test_quantisation_is_bit_exact(bits):
+def test_quantisation_matches_the_fp64_definition(bits):
+    """The kernel decides the level k in FP32 (dos.h); the oracle by the
+    definition in FP64.  The integer levels must agree on every element except
+    where the exact h (2^B - 1) / h_max lies within the kernel's FP32 rounding
+    of a half-integer (the two FP32 roundings of the scale and of the product,
+    each at most 2^-24 relative, move the product by at most 2^-23 of it);
+    those elements are counted and their number bounded by the band's
+    expected share, and there the kernel must pick one of the two neighbours.
+    Values are the level's thickness rounded to FP32."""
     rng = np.random.default_rng(bits)
     hmax = 664.5e-9
+    levels = 2 ** bits - 1
     h = rng.uniform(-0.2 * hmax, 1.2 * hmax, 100003).astype(np.float32)
-    q = quantize_thickness(torch.tensor(h, device=DEV), hmax, bits).cpu().numpy()
-    assert np.array_equal(q, O.quantize_thickness(h, hmax, bits))
+    q = quantize_thickness(torch.tensor(h, device=DEV), hmax, bits).cpu().numpy().astype(np.float64)
+    k_ref = O.quantize_level(h, hmax, bits)
+    step = hmax / levels
+    k_gpu = np.rint(q / step).astype(np.int64)
+    # the stored value is the level's thickness up to FP32 rounding (two roundings)
+    assert np.all(np.abs(q - k_gpu * step) <= 2.0 ** -23 * np.maximum(k_gpu * step, step))
+    x = np.clip(h.astype(np.float64), 0.0, hmax) * (levels / hmax)
+    band = 2.0 ** -23 * np.abs(x) + 1e-12
+    tie = np.abs(x - np.floor(x) - 0.5) <= band
+    assert np.array_equal(k_gpu[~tie], k_ref[~tie])
+    assert np.all(np.abs(k_gpu[tie] - x[tie]) <= 0.5 + band[tie])
+    expected = h.size * 2.0 * 2.0 ** -23 * levels
+    assert np.count_nonzero(tie) <= 4 * expected + 8, np.count_nonzero(tie)
 
 
 def test_quantised_design_forward_matches_oracle():
@@ -42,7 +62,7 @@ def test_quantised_design_forward_matches_oracle():
     st = DiffractiveStack.from_workload(w, device=DEV)
     I = st.forward(hq)
     ref = O.forward(hq.cpu().numpy().astype(np.float64), **oracle_model(w))
-    assert rel_l2(I.cpu().numpy().astype(np.float64), ref["I"]) <= TOL_INTENSITY
+    assert_close(I.cpu().numpy().astype(np.float64), ref["I"], TOL_INTENSITY)
     st.close()
 
 
@@ -54,7 +74,7 @@ def test_efficiency_matches_oracle(path):
     st.forward(torch.tensor(h, dtype=torch.float32, device=DEV))
     eta = st.efficiency().cpu().numpy().astype(np.float64)
     ref = O.diffraction_efficiency(O.forward(h, keep_fields=False, **oracle_model(w))["I"], w.aperture)
-    assert rel_l2(eta, ref) <= TOL_INTENSITY
+    assert_close(eta, ref, TOL_INTENSITY)
     st.close()
 
 
@@ -96,13 +116,65 @@ def test_fine_tune_after_channel_swap_lowers_the_loss():
     st.close()
 
 
+def test_channel_swap_from_gpu_psnr_matches_the_oracle():
+    """NEXT-3 on the GPU against the oracle: the per-channel PSNRs of the
+    first design (64 channels of the 5-layer batched geometry) give the same
+    reassignment of images to wavelengths as the oracle's PSNRs (index work:
+    bit-exact, except inside groups of PSNRs closer than the PSNR tolerance,
+    where only the group's image set must agree); then one fine-tuning step
+    on the swapped targets: its loss, and the gradient at the thickness the
+    Adam step produced, against the FP64 oracle on the same swapped targets."""
+    from gpu_cases import TOL_GRAD_ORACLE, TOL_LOSS
+    from paper_2604_02624_gb300.design import channel_swap, fine_tune
+    wb = W.workload("batched")
+    idx = W.subset_indices(wb.n_lambda, 64)
+    w = wb.subset(idx)
+    h = W.thickness(w, 0)
+    T = W.targets(wb, 1)[idx]
+    model = oracle_model(w)
+    st = DiffractiveStack.from_workload(w, device=DEV, loss="mse_scaled", path="multipass_bulk")
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    Td = torch.tensor(T, dtype=torch.float32, device=DEV)
+    st.forward(hd)
+    _, psnr, _ = st.loss(Td)
+    psnr = psnr.cpu().numpy().astype(np.float64)
+    fwd = O.forward(h, keep_fields=False, **model)
+    psnr_ref = O.mse_loss(fwd["I"], T, scaled=True)[1]
+    assert np.max(np.abs(psnr - psnr_ref)) <= 1e-3
+    perm = channel_swap(psnr, w.lambdas)
+    perm_ref = O.channel_swap(psnr_ref, w.lambdas)
+    ranked = np.sort(psnr_ref)[::-1]
+    close = np.abs(np.diff(ranked)) <= 2e-3
+    if not close.any():
+        assert np.array_equal(perm, perm_ref)
+    else:  # near-ties: the same images per group of equal rank
+        order = np.argsort(-w.lambdas, kind="stable")
+        starts = np.concatenate(([0], np.nonzero(~close)[0] + 1))
+        ends = np.concatenate((starts[1:], [len(ranked)]))
+        for a, b in zip(starts, ends):
+            assert set(perm[order[a:b]]) == set(perm_ref[order[a:b]])
+    Ts = T[perm_ref]
+    Tsd = torch.tensor(Ts, dtype=torch.float32, device=DEV)
+    h1, losses = fine_tune(st, hd, Tsd, steps=1, lr=1e-2, h_max=664.5e-9)
+    L0_ref = O.mse_loss(fwd["I"], Ts, scaled=True)[0]
+    assert abs(losses[0] - L0_ref) <= TOL_LOSS * abs(L0_ref)
+    h1n = h1.cpu().numpy().astype(np.float64)
+    assert np.all(h1n >= 0) and np.all(h1n <= 664.5e-9 * (1 + 1e-6))
+    g1 = torch.empty_like(hd)
+    L1, _ = st.step(h1, Tsd, grad_out=g1, read=True)
+    L1_ref, _, g1_ref, _ = O.loss_and_grad(h1n, Ts, scaled=True, **model)
+    assert abs(L1 - L1_ref) <= TOL_LOSS * abs(L1_ref)
+    assert_close(g1.cpu().numpy().astype(np.float64), g1_ref, TOL_GRAD_ORACLE, "gradient after one step")
+    st.close()
+
+
 # ------------------------------------------------------------ misaligned layers (NEXT-4)
 DISP = np.array([[31e-9, -17e-9, 90e-9], [-12e-9, 44e-9, -150e-9]])
 
 
 @pytest.mark.parametrize("path", ["multipass", "multipass_bulk", "fused", "dft_gemm"])
 def test_misaligned_layers_match_oracle(path):
-    from gpu_cases import TOL_FIELD, TOL_GRAD_ORACLE, split_bound, TOL_GRAD_FD
+    from gpu_cases import SPLIT_TARGET, TOL_FIELD, TOL_GRAD_ORACLE
     w = W.workload("small")
     h = W.thickness(w, 0)
     T = W.targets(w, 1)
@@ -112,20 +184,16 @@ def test_misaligned_layers_match_oracle(path):
     I = st.forward(hd)
     o = st.output_field()
     _, _, dl = st.loss(torch.tensor(T, dtype=torch.float32, device=DEV))
-    g = st.backward(hd, dl).cpu().numpy().astype(np.float64)
+    g = st.backward(dl).cpu().numpy().astype(np.float64)
     L_ref, _, g_ref, fwd = O.loss_and_grad(h, T, displacements=DISP, **oracle_model(w))
-    e_o = rel_l2(o.cpu().numpy().astype(np.complex128), fwd["o"])
-    if path == "dft_gemm":
-        assert e_o <= split_bound(4 * (w.n_layers + 1))
-        assert rel_l2(g, g_ref) <= TOL_GRAD_FD
-    else:
-        assert e_o <= TOL_FIELD
-        assert rel_l2(g, g_ref) <= TOL_GRAD_ORACLE
+    split = path == "dft_gemm"
+    assert_close(o.cpu().numpy().astype(np.complex128), fwd["o"], SPLIT_TARGET if split else TOL_FIELD, "field")
+    assert_close(g, g_ref, SPLIT_TARGET if split else TOL_GRAD_ORACLE, "gradient")
     # back to the aligned design
     st.set_misalignment(None)
     I0 = st.forward(hd).cpu().numpy().astype(np.float64)
     ref0 = O.forward(h, keep_fields=False, **oracle_model(w))["I"]
-    assert rel_l2(I0, ref0) <= (split_bound(12, True) if path == "dft_gemm" else TOL_INTENSITY)
+    assert_close(I0, ref0, SPLIT_TARGET if split else TOL_INTENSITY, "intensity")
     st.close()
 
 
@@ -143,7 +211,7 @@ def test_graph_step_follows_misalignment_changes():
         st.forward(h)
         L_ref, _, dl = st.loss(T)
         assert val == L_ref
-        assert torch.equal(g, st.backward(h, dl))
+        assert torch.equal(g, st.backward(dl))
     st.close()
 
 
@@ -165,14 +233,14 @@ def test_detector_pixels_loss_psnr_and_gradient(path, b, loss):
     Td = torch.tensor(T, device=DEV)
     st.forward(hd)
     val, psnr, dl = st.loss(Td)
-    g = st.backward(hd, dl).clone()
+    g = st.backward(dl).clone()
     scaled = loss == "mse_scaled"
     L_ref, psnr_ref, g_ref, fwd = O.loss_and_grad(h, T, scaled=scaled, detector_bin=b, **oracle_model(w))
     _, _, dl_ref = O.mse_loss(fwd["I"], T, scaled, b)
     assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref)
     assert np.max(np.abs(psnr.cpu().numpy() - psnr_ref)) <= 1e-3
-    assert rel_l2(dl.cpu().numpy().astype(np.float64), dl_ref) <= TOL_INTENSITY
-    assert rel_l2(g.cpu().numpy().astype(np.float64), g_ref) <= TOL_GRAD_ORACLE
+    assert_close(dl.cpu().numpy().astype(np.float64), dl_ref, TOL_INTENSITY)
+    assert_close(g.cpu().numpy().astype(np.float64), g_ref, TOL_GRAD_ORACLE)
     gs = torch.empty_like(g)
     val2, _ = st.step(hd, Td, grad_out=gs, read=True)
     assert val2 == val and torch.equal(gs, g)

@@ -18,12 +18,31 @@ def test_quantisation_error_is_at_most_half_a_step_and_idempotent():
     for bits in (4, 6, 8, 16):
         q = O.quantize_thickness(h, hmax, bits)
         step = hmax / (2 ** bits - 1)
-        # half a step, plus the FP32 rounding of the level decision h * s (ulp of
-        # a number near 2^B is 2^(B-23) steps) and of the stored values
-        slack = 0.5 * step * 2.0 ** (bits - 22) + 4 * np.spacing(np.float32(hmax))
-        assert np.max(np.abs(q - h.astype(np.float32))) <= 0.5 * step + slack
+        # half a step, up to the FP64 rounding of h (2^B - 1) / h_max
+        assert np.max(np.abs(q - h)) <= 0.5 * step * (1 + 1e-9)
         assert np.array_equal(O.quantize_thickness(q, hmax, bits), q)
         assert len(np.unique(q)) <= 2 ** bits
+
+
+def test_quantisation_is_the_nearest_level_by_brute_force():
+    """Fig. 7's B-bit design: each thickness goes to the closest of the 2^B
+    levels k h_max / (2^B - 1); checked against an exhaustive search over all
+    levels (thicknesses outside [0, h_max] go to the end levels)."""
+    rng = np.random.default_rng(7)
+    hmax = 664.5e-9
+    for bits in (1, 2, 3, 5, 8):
+        levels = np.arange(2 ** bits) * (hmax / (2 ** bits - 1))
+        h = rng.uniform(-0.3 * hmax, 1.3 * hmax, 4000)
+        nearest = levels[np.argmin(np.abs(h[:, None] - levels[None, :]), axis=1)]
+        assert np.array_equal(O.quantize_thickness(h, hmax, bits), nearest)
+
+
+def test_quantisation_hand_cases():
+    """Two bits, h_max = 3: levels 0, 1, 2, 3; a thickness midway between two
+    levels goes to the even level index (round half to even)."""
+    h = np.array([-1.0, 0.0, 0.49, 0.5, 0.51, 1.5, 2.5, 2.51, 3.0, 7.0])
+    assert O.quantize_level(h, 3.0, 2).tolist() == [0, 0, 0, 0, 1, 2, 2, 3, 3, 3]
+    assert O.quantize_thickness(h, 3.0, 2).tolist() == [0.0, 0.0, 0.0, 0.0, 1.0, 2.0, 2.0, 3.0, 3.0, 3.0]
 
 
 def test_efficiency_of_an_unobstructed_zero_gap_system():

@@ -17,7 +17,7 @@ from paper_2604_02624_gb300 import _lib as L
 from paper_2604_02624_gb300 import workloads as W
 from paper_2604_02624_gb300.api import DiffractiveStack
 
-from gpu_cases import TOL_INTENSITY, TOL_LOSS, rel_l2
+from gpu_cases import TOL_INTENSITY, TOL_LOSS, assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def test_noalloc_scoring_matches_dos_loss_on_two_calls_in_a_row(loss, mode):
         torch.cuda.synchronize()
         assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref), (call, val, L_ref)
         assert np.max(np.abs(psnr.cpu().numpy() - psnr_ref)) <= 1e-3, call
-        assert rel_l2(g.cpu().numpy().astype(np.float64), g_ref) <= TOL_INTENSITY, call
+        assert_close(g.cpu().numpy().astype(np.float64), g_ref, TOL_INTENSITY, call)
     st.close()
 
 
