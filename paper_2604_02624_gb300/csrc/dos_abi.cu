@@ -152,8 +152,9 @@ struct dos_ctx {
   // never arrive, so every block's first wait expires; 2: the copies land, but
   // the odd threads of every block report their first wait as expired
   int inject_stall = 0;
-  CUtensorMap tmap_S;        // S as [nw][n][m] 8-byte elements, box {col_lines, n, 1}
-  CUtensorMap tmap_F;        // the same with box {col_lines, fov, 1}: the adjoint's first column pass
+  CUtensorMap tmap_S;        // S as [nw][n][m] 8-byte elements, box {col_group, n, 1}
+  CUtensorMap tmap_F;        // the same with box {col_group, fov, 1}: the adjoint's first column pass
+  CUtensorMap tmap_H;        // transfer tables as [slots * nw][hs][hs], box {h_box_cols, h_box_rows, 1}
   bool have_tmap = false;     // the bulk column pass runs the plain kernel without them
   int take_stall(unsigned kind) {
     const int v = (bulk & kind) ? inject_stall : 0;
@@ -247,6 +248,7 @@ struct dos_ctx {
     a.err = d_err;
     a.tmap = have_tmap ? &tmap_S : nullptr;
     a.tmap_rows = n;
+    a.hmap = have_tmap ? &tmap_H : nullptr;
     return a;
   }
 };
@@ -298,10 +300,12 @@ int validate(const dos_config* c) {
 
 int choose_path(dos_ctx* x, int requested);
 
-// Tensor map of the row spectra S for the bulk column pass: [nw][n][m]
-// elements of 8 bytes (complex64 moved as opaque 64-bit words), box
-// {col_lines columns, n rows, 1 channel} (tmap_S) or {col_lines, fov, 1}
-// (tmap_F), columns past m read as zeros.
+// Tensor maps of the bulk column pass (elements of 8 bytes: complex64 moved as
+// opaque 64-bit words): the row spectra S as [nw][n][m], box {col_group
+// columns, n rows, 1 channel} (tmap_S) or {col_group, fov, 1} (tmap_F); the
+// transfer tables as [slots * nw][hs][hs] (rows of hs = m/2 + 2 entries, a
+// 16-byte multiple), box {h_box_cols, h_box_rows, 1} (tmap_H); rows past the
+// table read as zeros.
 // A driver without the entry point leaves the plain column kernel in use.
 int make_spectra_map(dos_ctx* x) {
   x->have_tmap = false;
@@ -319,13 +323,24 @@ int make_spectra_map(dos_ctx* x) {
   const int box_rows[2] = {x->n, x->fov};
   CUtensorMap* maps[2] = {&x->tmap_S, &x->tmap_F};
   for (int i = 0; i < 2; ++i) {  // both are encoded, also when fov == n
-    const cuuint32_t box[3] = {(cuuint32_t)x->ops->col_lines, (cuuint32_t)box_rows[i], 1};
+    const cuuint32_t box[3] = {(cuuint32_t)x->ops->col_group, (cuuint32_t)box_rows[i], 1};
     const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
         maps[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, x->S, dims, strides, box, estr,
         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
       return fail(DOS_ERR_CUDA, "cuTensorMapEncodeTiled(row spectra) failed: " + std::to_string((int)r));
+  }
+  {
+    const cuuint64_t hdims[3] = {(cuuint64_t)x->hs, (cuuint64_t)x->hs, (cuuint64_t)x->n_slots * x->nw};
+    const cuuint64_t hstrides[2] = {(cuuint64_t)x->hs * 8, (cuuint64_t)x->hs * x->hs * 8};
+    const cuuint32_t hbox[3] = {(cuuint32_t)x->ops->h_box_cols, (cuuint32_t)x->ops->h_box_rows, 1};
+    const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
+        &x->tmap_H, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, x->Hq, hdims, hstrides, hbox, estr,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(DOS_ERR_CUDA, "cuTensorMapEncodeTiled(transfer tables) failed: " + std::to_string((int)r));
   }
   x->have_tmap = true;
   return DOS_OK;
@@ -341,7 +356,9 @@ int build(dos_ctx* x, const dos_config* c) {
   x->ap = c->aperture ? c->aperture : c->fov;
   x->of = (c->n - c->fov) / 2;
   x->oa = (c->n - x->ap) / 2;
-  x->hs = c->m / 2 + 1;
+  // quadrant tables (H depends on fx^2, fy^2): M/2 + 1 frequencies per axis,
+  // stored with pitch M/2 + 2 so that a row is a 16-byte multiple (tensor copies)
+  x->hs = c->m / 2 + 2;
   x->pitch = c->pitch;
   x->n_med = c->n_medium;
   x->h_base = c->h_base;
@@ -433,12 +450,12 @@ int build(dos_ctx* x, const dos_config* c) {
     DOS_CUDA(dos::launch_build_dft(x->gp, x->stream), "DFT matrices");
   }
   if ((rc = x->alloc(&x->S, (size_t)x->nw * x->n * x->m, "row spectra"))) return rc;
-  if ((rc = make_spectra_map(x))) return rc;
   if ((rc = x->alloc(&x->ckpt, (size_t)x->K * x->nw * n2, "layer checkpoints"))) return rc;
   if (!x->fcands.empty() && (rc = x->alloc(&x->ckt, (size_t)x->K * x->nw * n2, "transmission checkpoints")))
     return rc;
   if ((rc = x->alloc(&x->o, (size_t)x->nw * x->fov * x->fov, "output field"))) return rc;
   if ((rc = x->alloc(&x->Hq, (size_t)x->n_slots * x->nw * x->hs * x->hs, "transfer tables"))) return rc;
+  if ((rc = make_spectra_map(x))) return rc;
   if ((rc = x->alloc(&x->arow, (size_t)x->m, "aperture spectrum"))) return rc;
   if ((rc = x->alloc(&x->tw, (size_t)x->ops->Q * (x->ops->P + 1), "twiddles"))) return rc;
   if ((rc = x->alloc(&x->chan, (size_t)x->nw, "channel constants"))) return rc;
@@ -656,6 +673,7 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
                 "forward row pass");
     }
     a.Hq = c->hq_slot(l);
+    a.hmap_z0 = c->gap_slot[l] * c->nw;
     a.mis = c->gap_mis(l);
     a.in_r0 = 0;
     a.in_r1 = c->n;
@@ -723,6 +741,7 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
   ++c->launches;
   for (int l = c->K; l >= 1; --l) {
     a.Hq = c->hq_slot(l);
+    a.hmap_z0 = c->gap_slot[l] * c->nw;
     a.mis = c->gap_mis(l);
     a.in_r0 = l == c->K ? c->of : 0;
     a.in_r1 = l == c->K ? c->of + c->fov : c->n;

@@ -3,10 +3,15 @@
 // Two levels:
 //  * dft<N, INV, NZ, NO>(x): an N-point DFT held entirely in one thread's
 //    registers, natural order in and out, built at compile time from radix
-//    2/3/4/5 butterflies by Cooley-Tukey splitting. Twiddles are compile-time
-//    constants (cos/sin of rational turns evaluated by a constexpr series), so
-//    they become instruction immediates. NZ leading inputs may be non-zero,
-//    NO leading outputs are needed: zero-padding and cropping prune work.
+//    2/3/4/5 butterflies.  Composite sizes split by Good-Thomas (prime factor
+//    algorithm: coprime factors, index maps by the Chinese remainder theorem,
+//    no twiddles between the stages) or by Cooley-Tukey, whichever a
+//    compile-time operation count finds cheaper (20 = 4 x 5 goes Good-Thomas).
+//    Twiddles are compile-time constants (cos/sin of rational turns evaluated
+//    by a constexpr series), so they become instruction immediates. NZ
+//    leading inputs may be non-zero, NO leading outputs are needed:
+//    zero-padding and cropping prune work, tracked as bit masks through the
+//    splits.
 //  * Line<P, Q, T>::fft: an M = P*Q point DFT shared by T threads, one shared
 //    memory exchange. Thread t holds x[t + T*i] in r[i] on input *and* output,
 //    so an inverse followed by a forward transform (crop -> modulate -> pad of
@@ -103,23 +108,164 @@ constexpr double cos_turn(long k, long n) {
 // sin(2 pi k / n) = cos(2 pi (4k - n) / (4n))
 constexpr double sin_turn(long k, long n) { return cos_turn(4 * k - n, 4 * n); }
 
-constexpr int cdiv_clamp(int num, int den, int hi) {
-  return num <= 0 ? 0 : ((num + den - 1) / den < hi ? (num + den - 1) / den : hi);
-}
 constexpr int first_factor(int n) {
   return n % 4 == 0 && n != 4 ? 4 : n % 5 == 0 && n != 5 ? 5 : n % 3 == 0 && n != 3 ? 3 : 2;
 }
 constexpr bool is_base(int n) { return n == 2 || n == 3 || n == 4 || n == 5; }
 constexpr int butterfly_cost(int n) { return n == 2 ? 4 : n == 3 ? 16 : n == 4 ? 16 : 36; }
-// instruction estimate of a direct sum with NZ inputs and NO outputs
-constexpr int direct_cost(int n, int nz, int no) {
+
+// ---- pruning masks: bit i of an input mask = input i may be non-zero; bit k
+// of an output mask = output k is needed (N <= 64)
+using mask_t = unsigned long long;
+constexpr mask_t lead_mask(int n) { return n <= 0 ? 0ull : n >= 64 ? ~0ull : ((1ull << n) - 1ull); }
+constexpr bool has(mask_t m, int i) { return ((m >> i) & 1ull) != 0; }
+constexpr int popcount(mask_t m) {
   int c = 0;
-  for (int k = 0; k < no; ++k)
-    for (int j = 1; j < nz; ++j) {
-      const int e = (j * k) % n;
-      c += 2 + ((e == 0 || 2 * e == n || 4 * e == n || 4 * e == 3 * n) ? 0 : 4);
-    }
+  for (; m; m >>= 1) c += (int)(m & 1ull);
   return c;
+}
+constexpr int lowest(mask_t m) {
+  int i = 0;
+  while (m && !(m & 1ull)) m >>= 1, ++i;
+  return i;
+}
+// w^e is +-1 or +-j: a sign change or a swap, no arithmetic
+constexpr bool trivial_turn(long e, long n) {
+  e %= n;
+  return e == 0 || 2 * e == n || 4 * e == n || 4 * e == 3 * n;
+}
+constexpr int gcd(int a, int b) { return b == 0 ? a : gcd(b, a % b); }
+constexpr int inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return 1;
+}
+// Good-Thomas (prime factor) indexing of N = P1 P2 with gcd(P1, P2) = 1:
+// input n = (P2 i1 + P1 i2) mod N; output k with k = k1 (mod P1), k = k2 (mod P2)
+// (Chinese remainder theorem).  Then X[k] = sum_i1 w_P1^(k1 i1) sum_i2 w_P2^(k2 i2)
+// x[n]: two sets of short DFTs with no twiddle factors between them.
+constexpr int pfa_in_index(int P1, int P2, int i1, int i2) { return (P2 * i1 + P1 * i2) % (P1 * P2); }
+constexpr int pfa_out_index(int P1, int P2, int k1, int k2) {
+  return (k1 * P2 * inv_mod(P2 % P1, P1) + k2 * P1 * inv_mod(P1 % P2, P2)) % (P1 * P2);
+}
+// masks of the sub-DFTs.  PFA: stage 1 = P2-point DFTs over i2 (one per i1),
+// stage 2 = P1-point DFTs over i1 (one per k2).
+constexpr mask_t pfa_in1(int P1, int P2, mask_t im, int i1) {
+  mask_t m = 0;
+  for (int i2 = 0; i2 < P2; ++i2)
+    if (has(im, pfa_in_index(P1, P2, i1, i2))) m |= 1ull << i2;
+  return m;
+}
+constexpr mask_t pfa_out1(int P1, int P2, mask_t om) {
+  mask_t m = 0;
+  for (int k = 0; k < P1 * P2; ++k)
+    if (has(om, k)) m |= 1ull << (k % P2);
+  return m;
+}
+constexpr mask_t pfa_in2(int P1, int P2, mask_t im) {
+  mask_t m = 0;
+  for (int i1 = 0; i1 < P1; ++i1)
+    if (pfa_in1(P1, P2, im, i1)) m |= 1ull << i1;
+  return m;
+}
+constexpr mask_t pfa_out2(int P1, int P2, mask_t om, int k2) {
+  mask_t m = 0;
+  for (int k1 = 0; k1 < P1; ++k1)
+    if (has(om, pfa_out_index(P1, P2, k1, k2))) m |= 1ull << k1;
+  return m;
+}
+// Cooley-Tukey N = A B: input n = B a + b, output k = k1 + A k2; stage 1 =
+// A-point DFTs over a (one per b), twiddles w_N^(b k1), stage 2 = B-point DFTs
+// over b (one per k1).
+constexpr mask_t ct_in1(int A, int B, mask_t im, int b) {
+  mask_t m = 0;
+  for (int a = 0; a < A; ++a)
+    if (has(im, B * a + b)) m |= 1ull << a;
+  return m;
+}
+constexpr mask_t ct_out1(int A, int B, mask_t om) {
+  mask_t m = 0;
+  for (int k = 0; k < A * B; ++k)
+    if (has(om, k)) m |= 1ull << (k % A);
+  return m;
+}
+constexpr mask_t ct_in2(int A, int B, mask_t im) {
+  mask_t m = 0;
+  for (int b = 0; b < B; ++b)
+    if (ct_in1(A, B, im, b)) m |= 1ull << b;
+  return m;
+}
+constexpr mask_t ct_out2(int A, int B, mask_t om, int k1) {
+  mask_t m = 0;
+  for (int k2 = 0; k2 < B; ++k2)
+    if (has(om, k1 + A * k2)) m |= 1ull << k2;
+  return m;
+}
+
+// ---- plans: the cheapest way (estimated scalar FP32 instructions) to
+// compute the needed outputs of an N-point DFT from its non-zero inputs
+enum PlanKind : int { kNone, kZero, kOne, kDirect, kButterfly, kPfa, kCt };
+struct Plan {
+  int cost, kind, p1;
+};
+// X[k] = sum over inputs of x[j] w^(jk) for the needed k
+constexpr int direct_cost(int n, mask_t im, mask_t om) {
+  const int j0 = lowest(im);
+  int c = 0;
+  for (int k = 0; k < n; ++k) {
+    if (!has(om, k)) continue;
+    c += trivial_turn((long)j0 * k, n) ? 0 : 4;
+    for (int j = j0 + 1; j < n; ++j)
+      if (has(im, j)) c += 2 + (trivial_turn((long)j * k, n) ? 0 : 4);
+  }
+  return c;
+}
+constexpr Plan plan(int n, mask_t im, mask_t om) {
+  im &= lead_mask(n);
+  om &= lead_mask(n);
+  if (n == 1 || om == 0) return Plan{0, kNone, 0};
+  if (im == 0) return Plan{0, kZero, 0};
+  if (popcount(im) == 1) {
+    const int j = lowest(im);
+    int c = 0;
+    for (int k = 0; k < n; ++k)
+      if (has(om, k) && !trivial_turn((long)j * k, n)) c += 4;
+    return Plan{c, kOne, 0};
+  }
+  if (is_base(n)) {
+    const bool full = im == lead_mask(n) && om == lead_mask(n);
+    const int d = full ? 1 << 30 : direct_cost(n, im, om);
+    return d < butterfly_cost(n) ? Plan{d, kDirect, 0} : Plan{butterfly_cost(n), kButterfly, 0};
+  }
+  Plan best{1 << 30, kCt, 0};
+  // Good-Thomas splits (both orders of every coprime factor pair)
+  for (int p1 = 2; p1 < n; ++p1) {
+    if (n % p1 != 0 || gcd(p1, n / p1) != 1) continue;
+    const int p2 = n / p1;
+    const mask_t om1 = pfa_out1(p1, p2, om), im2 = pfa_in2(p1, p2, im);
+    int c = 0;
+    for (int i1 = 0; i1 < p1; ++i1) c += plan(p2, pfa_in1(p1, p2, im, i1), om1).cost;
+    for (int k2 = 0; k2 < p2; ++k2)
+      if (has(om1, k2)) c += plan(p1, im2, pfa_out2(p1, p2, om, k2)).cost;
+    if (c < best.cost) best = Plan{c, kPfa, p1};
+  }
+  // Cooley-Tukey split with twiddles
+  {
+    const int a = first_factor(n), b = n / a;
+    const mask_t om1 = ct_out1(a, b, om), im2 = ct_in2(a, b, im);
+    int c = 0;
+    for (int bb = 0; bb < b; ++bb) {
+      const mask_t m = ct_in1(a, b, im, bb);
+      if (!m) continue;
+      c += plan(a, m, om1).cost;
+      for (int k1 = 0; k1 < a; ++k1)
+        if (has(om1, k1) && !trivial_turn((long)bb * k1, n)) c += 4;
+    }
+    for (int k1 = 0; k1 < a; ++k1)
+      if (has(om1, k1)) c += plan(b, im2, ct_out2(a, b, om, k1)).cost;
+    if (c < best.cost) best = Plan{c, kCt, a};
+  }
+  return best;
 }
 }  // namespace ct
 
@@ -210,74 +356,135 @@ DOS_HD void bfly5(float2* x) {
   x[3] = csub(a2, jb2);
 }
 
-// Direct sum X[k] = sum_{n < NZ} x[n] w^{nk} for k < NO (small pruned cases).
-template <int N, bool INV, int NZ, int NO>
+// Direct sum X[k] = sum over the non-zero inputs j of x[j] w^(jk), needed k only.
+template <int N, bool INV, ct::mask_t IM, ct::mask_t OM>
 DOS_HD void dft_direct(float2* x) {
-  float2 out[NO];
-  static_for<0, NO>([&](auto kk) {
+  constexpr int j0 = ct::lowest(IM);
+  float2 out[N];
+  static_for<0, N>([&](auto kk) {
     constexpr int k = kk;
-    float2 acc = x[0];
-    static_for<1, NZ>([&](auto jj) {
-      constexpr int j = jj;
-      acc = cadd(acc, twiddle<N, (long)j * k, INV>(x[j]));
-    });
-    out[k] = acc;
+    if constexpr (ct::has(OM, k)) {
+      float2 acc = twiddle<N, (long)j0 * k, INV>(x[j0]);
+      static_for<j0 + 1, N>([&](auto jj) {
+        constexpr int j = jj;
+        if constexpr (ct::has(IM, j)) acc = cadd(acc, twiddle<N, (long)j * k, INV>(x[j]));
+      });
+      out[k] = acc;
+    }
   });
-  static_for<0, NO>([&](auto k) { x[k] = out[k]; });
+  static_for<0, N>([&](auto kk) {
+    if constexpr (ct::has(OM, kk)) x[kk] = out[kk];
+  });
+}
+
+// N-point DFT in registers, natural order in and out: only the inputs in IM
+// are read (the others are zero), only the outputs in OM are produced (the
+// others are left undefined).  The split is chosen at compile time by
+// ct::plan: a radix-2/3/4/5 butterfly or a direct sum for the base sizes, and
+// for composite sizes the cheaper of the Good-Thomas splits (coprime factors,
+// no twiddles between the stages) and a Cooley-Tukey split (with twiddles).
+template <int N, bool INV, ct::mask_t IM, ct::mask_t OM, bool PK = false>
+DOS_HD void dftm(float2* x) {
+  constexpr ct::Plan pl = ct::plan(N, IM, OM);
+  constexpr ct::mask_t im = IM & ct::lead_mask(N), om = OM & ct::lead_mask(N);
+  if constexpr (pl.kind == ct::kNone) {
+    return;
+  } else if constexpr (pl.kind == ct::kZero) {
+    static_for<0, N>([&](auto k) {
+      if constexpr (ct::has(om, k)) x[k] = czero();
+    });
+  } else if constexpr (pl.kind == ct::kOne) {
+    constexpr int j = ct::lowest(im);
+    const float2 v = x[j];
+    static_for<0, N>([&](auto kk) {
+      constexpr int k = kk;
+      if constexpr (ct::has(om, k)) x[k] = twiddle<N, (long)j * k, INV>(v);
+    });
+  } else if constexpr (pl.kind == ct::kDirect) {
+    dft_direct<N, INV, im, om>(x);
+  } else if constexpr (pl.kind == ct::kButterfly) {
+    static_for<0, N>([&](auto j) {
+      if constexpr (!ct::has(im, j)) x[j] = czero();
+    });
+    constexpr bool pk = PK && im == ct::lead_mask(N);  // zero inputs fold only in scalar form
+    if constexpr (N == 2) bfly2<INV, pk>(x);
+    else if constexpr (N == 3) bfly3<INV, pk>(x);
+    else if constexpr (N == 4) bfly4<INV, pk>(x);
+    else bfly5<INV, pk>(x);
+  } else if constexpr (pl.kind == ct::kPfa) {
+    constexpr int P1 = pl.p1, P2 = N / P1;
+    constexpr ct::mask_t OM1 = ct::pfa_out1(P1, P2, om), IM2 = ct::pfa_in2(P1, P2, im);
+    float2 y[N];  // y[i1 * P2 + k2]
+    static_for<0, P1>([&](auto ii) {
+      constexpr int i1 = ii;
+      constexpr ct::mask_t m = ct::pfa_in1(P1, P2, im, i1);
+      if constexpr (m != 0) {
+        float2 t[P2];
+        static_for<0, P2>([&](auto jj) {
+          constexpr int i2 = jj;
+          if constexpr (ct::has(m, i2)) t[i2] = x[ct::pfa_in_index(P1, P2, i1, i2)];
+        });
+        dftm<P2, INV, m, OM1, PK>(t);
+        static_for<0, P2>([&](auto kk) {
+          if constexpr (ct::has(OM1, kk)) y[i1 * P2 + kk] = t[kk];
+        });
+      }
+    });
+    static_for<0, P2>([&](auto kk) {
+      constexpr int k2 = kk;
+      if constexpr (ct::has(OM1, k2)) {
+        constexpr ct::mask_t o2 = ct::pfa_out2(P1, P2, om, k2);
+        float2 t[P1];
+        static_for<0, P1>([&](auto ii) {
+          if constexpr (ct::has(IM2, ii)) t[ii] = y[ii * P2 + k2];
+        });
+        dftm<P1, INV, IM2, o2, PK>(t);
+        static_for<0, P1>([&](auto k1) {
+          if constexpr (ct::has(o2, k1)) x[ct::pfa_out_index(P1, P2, k1, k2)] = t[k1];
+        });
+      }
+    });
+  } else {
+    constexpr int A = pl.p1, B = N / A;
+    constexpr ct::mask_t OM1 = ct::ct_out1(A, B, om), IM2 = ct::ct_in2(A, B, im);
+    float2 y[N];  // y[b * A + k1]
+    static_for<0, B>([&](auto bb) {
+      constexpr int b = bb;
+      constexpr ct::mask_t m = ct::ct_in1(A, B, im, b);
+      if constexpr (m != 0) {
+        float2 t[A];
+        static_for<0, A>([&](auto aa) {
+          if constexpr (ct::has(m, aa)) t[aa] = x[B * aa + b];
+        });
+        dftm<A, INV, m, OM1, PK>(t);
+        static_for<0, A>([&](auto kk) {
+          constexpr int k1 = kk;
+          if constexpr (ct::has(OM1, k1)) y[b * A + k1] = twiddle<N, (long)b * k1, INV>(t[k1]);
+        });
+      }
+    });
+    static_for<0, A>([&](auto kk) {
+      constexpr int k1 = kk;
+      if constexpr (ct::has(OM1, k1)) {
+        constexpr ct::mask_t o2 = ct::ct_out2(A, B, om, k1);
+        float2 t[B];
+        static_for<0, B>([&](auto bb) {
+          if constexpr (ct::has(IM2, bb)) t[bb] = y[bb * A + k1];
+        });
+        dftm<B, INV, IM2, o2, PK>(t);
+        static_for<0, B>([&](auto k2) {
+          if constexpr (ct::has(o2, k2)) x[k1 + A * k2] = t[k2];
+        });
+      }
+    });
+  }
 }
 
 // N-point DFT in registers; only x[0..NZ) are read, only X[0..NO) are produced.
 template <int N, bool INV, int NZ = N, int NO = N, bool PK = false>
 DOS_HD void dft(float2* x) {
-  static_assert(NZ >= 0 && NZ <= N && NO >= 0 && NO <= N, "bad pruning");
-  if constexpr (N == 1 || NO == 0) {
-    return;
-  } else if constexpr (NZ == 0) {
-    static_for<0, NO>([&](auto k) { x[k] = czero(); });
-  } else if constexpr (NZ == 1) {
-    static_for<1, NO>([&](auto k) { x[k] = x[0]; });
-  } else if constexpr (ct::is_base(N)) {
-    if constexpr ((NZ < N || NO < N) && ct::direct_cost(N, NZ, NO) < ct::butterfly_cost(N)) {
-      dft_direct<N, INV, NZ, NO>(x);
-    } else {
-      if constexpr (NZ < N) static_for<NZ, N>([&](auto k) { x[k] = czero(); });
-      constexpr bool pk = PK && NZ == N;  // zero inputs fold only in scalar form
-      if constexpr (N == 2) bfly2<INV, pk>(x);
-      else if constexpr (N == 3) bfly3<INV, pk>(x);
-      else if constexpr (N == 4) bfly4<INV, pk>(x);
-      else bfly5<INV, pk>(x);
-    }
-  } else {
-    // N = A*B; input n = B*a + b, output k = k1 + A*k2.
-    constexpr int A = ct::first_factor(N);
-    constexpr int B = N / A;
-    constexpr int NOA = NO < A ? NO : A;
-    constexpr int NZB = NZ < B ? NZ : B;
-    float2 y[N];
-    static_for<0, B>([&](auto bb) {
-      constexpr int b = bb;
-      constexpr int nza = ct::cdiv_clamp(NZ - b, B, A);
-      if constexpr (nza > 0) {
-        float2 t[A];
-        static_for<0, nza>([&](auto aa) { t[aa] = x[B * aa + b]; });
-        dft<A, INV, nza, NOA, PK>(t);
-        static_for<0, NOA>([&](auto kk) {
-          constexpr int k1 = kk;
-          y[b * A + k1] = twiddle<N, (long)b * k1, INV>(t[k1]);
-        });
-      }
-    });
-    static_for<0, NOA>([&](auto kk) {
-      constexpr int k1 = kk;
-      constexpr int nob = ct::cdiv_clamp(NO - k1, A, B);
-      if constexpr (nob > 0) {
-        float2 t[B];
-        static_for<0, NZB>([&](auto bb) { t[bb] = y[bb * A + k1]; });
-        dft<B, INV, NZB, nob, PK>(t);
-        static_for<0, nob>([&](auto k2) { x[k1 + A * k2] = t[k2]; });
-      }
-    });
-  }
+  static_assert(NZ >= 0 && NZ <= N && NO >= 0 && NO <= N && N <= 64, "bad pruning");
+  dftm<N, INV, ct::lead_mask(NZ), ct::lead_mask(NO), PK>(x);
 }
 
 // --------------------------------------------------- line FFT over T threads

@@ -66,6 +66,8 @@ struct PassArgs {
                           // copied; 2 = its copies land but odd threads give up their first wait
   const void* tmap;       // host CUtensorMap of S as [nw][n][m] 8-byte elements (bulk column pass), or null
   int tmap_rows;          // rows of its box: the bulk column pass uses it when they are in_r1 - in_r0
+  const void* hmap;       // host CUtensorMap of the transfer tables as [slots * nw][hs][hs] 8-byte elements
+  int hmap_z0;            // its channel coordinate of this gap's table slot: slot * nw
 };
 
 // Kernel launchers of one padded size M (one translation unit per M).
@@ -86,6 +88,9 @@ struct PassOps {
   cudaError_t (*bulk_row_fwd)(const PassArgs&, bool save, cudaStream_t);
   cudaError_t (*bulk_row_adj)(const PassArgs&, bool first, cudaStream_t);
   cudaError_t (*bulk_row_first)(const PassArgs&, cudaStream_t);  // t(h) * field (fin) -> row spectra
+  // boxes of the bulk column pass's tensor copies: spectra {col_group, rows, 1},
+  // transfer table {h_box_cols, h_box_rows, 1}
+  int col_group, h_box_cols, h_box_rows;
 };
 
 const PassOps* pass_ops_for_m(int m);

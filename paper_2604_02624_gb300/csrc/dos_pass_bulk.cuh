@@ -4,9 +4,9 @@
 // block.  Blocks loop over several work items and the bulk-copy engine
 // (cp.async.bulk global -> shared, completion counted in bytes on an
 // mbarrier) fetches the next item while the block computes the current one:
-//   column pass : item = a tile of COLL columns of one channel (persistent
-//                 blocks); one tensor copy (TMA) of the box {COLL columns,
-//                 input rows} of the spectra;
+//   column pass : item = a mirrored pair of 8-column groups of one channel
+//                 (persistent blocks); tensor copies (TMA) of both groups'
+//                 input rows and of the transfer-table tile they share;
 //   row passes  : item = the block's RL rows of the next channel of its chunk;
 //                 one cp.async.bulk per row (rows padded in shared memory
 //                 against bank conflicts): spectra rows, the rows of the
@@ -105,115 +105,144 @@ struct PassBulk {
   static constexpr int SR = row_stage_stride(M);  // even: every staged row starts 16-byte aligned
   static_assert(SR % 2 == 0 && SR >= M, "staged rows must be 16-byte aligned and hold M values");
   static_assert(Pass<LF>::RZL >= LF::ZS, "exchange buffers must not overlap");
-  static_assert(Pass<LF>::COLL * 8 % 128 == 0, "a tensor copy into stage row in_r0 must start 128-byte aligned");
   static constexpr int CT = T * COLL, RT = T * RL;
-  static constexpr bool EARLY_H = E <= 20;  // registers allow the H values in flight
 
   // ------------------------------------------------------------ column pass
+  // An item is a mirrored pair of column groups of one channel: columns
+  // c0 .. c0+7 (lines 0-7) and M-c0-8 .. M-c0-1 (lines 8-15), c0 = 8 p for
+  // p < M/16.  H depends on |kx| only, and the two groups' |kx| are c0 .. c0+8,
+  // so one tile of 10 quadrant columns starting at x = c0 (even: a legal TMA
+  // start for 8-byte elements) serves all 16 columns.  Per item, four tensor
+  // copies: the two groups' input rows (box {8, in_r1 - in_r0, 1} of the row
+  // spectra, one dense [rows][8] block per group) and the H tile (two boxes
+  // {10, HR, 1} of the quadrant table, whose rows are 16-byte multiples: pitch
+  // M/2 + 2).  The spectra of the next item are fetched at the barrier inside
+  // the forward DFT (the stage has been read), the H tile of the next item at
+  // the barrier inside the inverse DFT (the tile has been read); both are
+  // waited for at the top of the item, with one block-wide verdict.
+  static constexpr int GW = Pass<LF>::COLL / 2;       // columns per group
+  static constexpr int HW = GW + 2;                   // quadrant columns per H tile (c0 .. c0+9)
+  static constexpr int HP = M / 2 + 2;                // quadrant pitch (rows and columns)
+  static constexpr int HR = ((HP / 2) + 7) / 8 * 8;   // rows per H box: two boxes cover the quadrant
+  static_assert(GW == 8 && HR <= 256, "column groups of 8, H boxes of at most 256 rows");
+  static_assert((HR * HW * 8) % 128 == 0, "the second H box must land 128-byte aligned");
+  // group stride in the stage (float2): whole 128-byte lines for any row count
+  __host__ __device__ static int col_group_stride(int rows) { return (rows + 1) / 2 * 2 * GW; }
   // dynamic shared memory (from a 128-byte aligned base):
-  //   stage[n][COLL] | exchange[COLL][ZL] | tw[ZS] | barrier
+  //   stage[2][rows][8] | H tile[2 HR][10] | exchange[COLL][ZL] | tw[ZS] | barrier[2]
   static size_t col_smem(int n) {
-    return 128 + sizeof(float2) * ((size_t)n * COLL + (size_t)COLL * ZL + LF::ZS) + sizeof(uint64_t);
+    return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + 2 * (size_t)HR * HW + (size_t)COLL * ZL +
+                                   LF::ZS) + 2 * sizeof(uint64_t);
   }
 
-  // The input rows [in_r0, in_r1) of every column tile (all N rows, or the
-  // field of view in the adjoint's first pass) are fetched by one tensor copy
-  // of the box {COLL columns, in_r1 - in_r0 rows, 1 channel} to their own rows
-  // of the stage (a row is COLL * 8 = 128 bytes, so every start stays 128-byte
-  // aligned); columns past M read as zeros.
   template <bool ADJ>
-  __device__ static void col(const PassArgs& a, const CUtensorMap* map) {
+  __device__ static void col(const PassArgs& a, const CUtensorMap* smap, const CUtensorMap* hmap) {
     extern __shared__ __align__(16) unsigned char col_raw[];
     float2* stage = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(col_raw) + 127) & ~uintptr_t(127));
-    float2* zb = stage + (size_t)a.n * COLL;
+    const int GS = col_group_stride(a.n);
+    float2* htile = stage + 2 * (size_t)GS;
+    float2* zb = htile + 2 * HR * HW;
     float2* tw = zb + (size_t)COLL * ZL;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);  // [0] spectra, [1] transfer-table tile
     const int l = threadIdx.x % COLL, t = threadIdx.x / COLL;
+    const int g = l / GW, lc = l % GW;
     float2* z = zb + l * ZL;
-    constexpr int ntiles = (M + COLL - 1) / COLL;
-    const int items = a.nw * ntiles;
-    const uint32_t bytes = (uint32_t)(COLL * 8) * (uint32_t)(a.in_r1 - a.in_r0);
+    constexpr int npairs = M / (2 * GW);
+    const int items = a.nw * npairs;
+    const uint32_t sbytes = 2u * GW * 8u * (uint32_t)(a.in_r1 - a.in_r0);
+    constexpr uint32_t hbytes = 2u * HW * HR * 8u;
     if (threadIdx.x == 0) {
-      bulk_bar_init(bar);
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+      bulk_bar_init(&bar[0]);
+      bulk_bar_init(&bar[1]);
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(smap)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(hmap)) : "memory");
     }
     for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
     __syncthreads();
-    auto fetch = [&](int it) {
-      if (threadIdx.x != 0) return;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bulk_expect(bar, bytes);
-      if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
-      const int w = it / ntiles, c0 = (it % ntiles) * COLL;
+    auto tensor_copy = [](float2* dst, const CUtensorMap* map, int x, int y, int zc, uint64_t* b) {
       asm volatile(
           "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-          "[%5];" ::"r"(sh_addr(stage + (size_t)a.in_r0 * COLL)),
-          "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(a.in_r0), "r"(w), "r"(sh_addr(bar))
+          "[%5];" ::"r"(sh_addr(dst)),
+          "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(zc), "r"(sh_addr(b))
           : "memory");
+    };
+    auto fetch_s = [&](int it) {
+      if (threadIdx.x != 0) return;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(&bar[0], sbytes);
+      if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
+      const int w = it / npairs, c0 = GW * (it % npairs);
+      tensor_copy(stage, smap, c0, a.in_r0, w, &bar[0]);
+      tensor_copy(stage + GS, smap, M - c0 - GW, a.in_r0, w, &bar[0]);
+    };
+    auto fetch_h = [&](int it) {
+      if (threadIdx.x != 0) return;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(&bar[1], hbytes);
+      if (a.stall == 1) return;
+      const int w = it / npairs, c0 = GW * (it % npairs);
+      tensor_copy(htile, hmap, c0, 0, a.hmap_z0 + w, &bar[1]);
+      tensor_copy(htile + HR * HW, hmap, c0, HR, a.hmap_z0 + w, &bar[1]);
     };
     bool ok = true;
     int k = 0;
-    if ((int)blockIdx.x < items) fetch(blockIdx.x);
+    if ((int)blockIdx.x < items) {
+      fetch_s(blockIdx.x);
+      fetch_h(blockIdx.x);
+    }
     for (int it = blockIdx.x; it < items; it += gridDim.x, ++k) {
-      const int w = it / ntiles, c0 = (it % ntiles) * COLL;
-      const int c = c0 + l;
-      const bool cok = c < M;
-      const int cc = cok ? c : c0;
-      ok = __syncthreads_and(bulk_wait(bar, (uint32_t)(k & 1), split_verdict(a, k))) != 0;  // one verdict for the whole block
+      const int w = it / npairs, c0 = GW * (it % npairs);
+      const int cc = g == 0 ? c0 + lc : M - c0 - GW + lc;  // this line's column
+      const int hc = g == 0 ? lc : GW - lc;                 // its |kx| - c0: the column in the H tile
+      const bool got = bulk_wait(&bar[0], (uint32_t)(k & 1), split_verdict(a, k)) &&
+                       bulk_wait(&bar[1], (uint32_t)(k & 1));
+      ok = __syncthreads_and(got) != 0;  // one verdict for the whole block
       if (!ok) break;
       float2 r[E];
+      const float2* sg = stage + (size_t)g * GS + lc - (ptrdiff_t)a.in_r0 * GW;  // row y at sg[y * GW]
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int row = t + T * i;
-        r[i] = (i < EF && row >= a.in_r0 && row < a.in_r1) ? stage[(size_t)row * COLL + l] : czero();
-      }
-      // transfer function of this column; with few elements per thread it is
-      // loaded before the forward DFT so that the loads overlap it
-      const float2* Hw = a.Hq + (size_t)w * a.hs * a.hs;
-      const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
-      const int bc = min(cc, M - cc);
-      float2 hv[EARLY_H ? E : 1];
-      if constexpr (EARLY_H) {
-#pragma unroll
-        for (int i = 0; i < E; ++i) {
-          const int kk = t + T * i;
-          hv[i] = __ldg(Hw + (size_t)min(kk, M - kk) * a.hs + bc);
-        }
+        r[i] = (i < EF && row >= a.in_r0 && row < a.in_r1) ? sg[row * GW] : czero();
       }
       LF::template step1<false, NZF, PKC>(r, t, z, tw);
-      __syncthreads();  // every thread is past its stage reads: the next item may land there
-      if (it + (int)gridDim.x < items) fetch(it + gridDim.x);
+      __syncthreads();  // every thread is past its stage reads: the next item's rows may land there
+      if (it + (int)gridDim.x < items) fetch_s(it + gridDim.x);
       LF::template step2<false, LF::Q, PKC>(r, t, z);
       // square lines: the inverse DFT below writes the exchange matrix in
       // the transposed layout, i.e. only what this thread just read
       if constexpr (!LF::SQUARE) __syncthreads();
+      // H(|ky|, |kx|) from the tile: |ky| = k below M/2 and M - k above, both
+      // affine in i at compile time
+      const float2* hlo = htile + t * HW + hc;
+      const float2* hhi = htile + (M - t) * HW + hc;
+      const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
-        float2 h;
-        if constexpr (EARLY_H) {
-          h = hv[i];
-        } else {
-          const int kk = t + T * i;
-          h = __ldg(Hw + (size_t)min(kk, M - kk) * a.hs + bc);
-        }
+        float2 h = i < E / 2 ? hlo[T * i * HW] : hhi[-T * i * HW];
         if (Sw) {
           const int kk = t + T * i;
-          h = cmul(h, misalign_factor(a.mis, kk, cc, M, Sw[(size_t)min(kk, M - kk) * a.hs + bc]));
+          h = cmul(h, misalign_factor(a.mis, kk, cc, M, Sw[(size_t)min(kk, M - kk) * a.hs + c0 + hc]));
         }
         r[i] = ADJ ? cmulc(r[i], h) : cmul(r[i], h);
       }
+      LF::template step1<true, LF::P, PKC, LF::SQUARE>(r, t, z, tw);
+      __syncthreads();  // every thread is past its reads of the H tile: the next item's may land there
+      if (it + (int)gridDim.x < items) fetch_h(it + gridDim.x);
       // no trailing barrier: the exchange buffer is next written after the
       // barrier at the top of the next item
-      LF::template fft<true, LF::P, NOI, false, PKC, LF::SQUARE>(r, t, z, tw);
+      LF::template step2<true, NOI, PKC, LF::SQUARE>(r, t, z);
       float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         const int row = t + T * i;
-        if (i < EF && cok && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
+        if (i < EF && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
       }
     }
     if (!ok && threadIdx.x == 0) {
-      (void)bulk_wait(bar, (uint32_t)(k & 1));  // a late copy lands (bounded) before the block leaves
+      // both copies of the item the block gave up on land (bounded) before it leaves
+      (void)bulk_wait(&bar[0], (uint32_t)(k & 1));
+      (void)bulk_wait(&bar[1], (uint32_t)(k & 1));
       atomicExch(a.err, 1);
     }
   }
@@ -587,8 +616,8 @@ __global__ void __launch_bounds__(LF::T * RL, LF::E <= 20 ? 3 : 1) k_row_adj_sta
 // DFT's barriers and dependencies (M = 512: 8.5 ms per launch with one)
 template <class LF, int RL, bool HALF, bool ADJ>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::COLL, 2)
-    k_col_bulk(PassArgs a, const __grid_constant__ CUtensorMap map) {
-  PassBulk<LF, RL, HALF>::template col<ADJ>(a, &map);
+    k_col_bulk(PassArgs a, const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap hmap) {
+  PassBulk<LF, RL, HALF>::template col<ADJ>(a, &smap, &hmap);
 }
 // the row passes: as many resident blocks as their shared memory allows
 template <class LF, int RL>
@@ -624,18 +653,23 @@ struct PassBulkLaunch {
   static bool half(const PassArgs& a) { return 2 * a.n <= LF::M; }
   template <bool H>
   static cudaError_t col_h(const PassArgs& a, bool adj, size_t sm, cudaStream_t s) {
-    const int items = a.nw * ((LF::M + PB::COLL - 1) / PB::COLL);
+    const int items = a.nw * (LF::M / PB::COLL);
     if (items == 0) return cudaSuccess;
     int n_slots = 0;
     auto kern = adj ? k_col_bulk<LF, RL, H, true> : k_col_bulk<LF, RL, H, false>;
     cudaError_t e = slots(kern, PB::CT, sm, &n_slots);
     if (e != cudaSuccess) return e;
-    kern<<<std::min(items, n_slots), PB::CT, sm, s>>>(a, *static_cast<const CUtensorMap*>(a.tmap));
+    kern<<<std::min(items, n_slots), PB::CT, sm, s>>>(a, *static_cast<const CUtensorMap*>(a.tmap),
+                                                     *static_cast<const CUtensorMap*>(a.hmap));
     return cudaGetLastError();
   }
+  // The tensor copies need maps whose boxes hold the input rows (at most 256)
+  // and the H tile, and M a multiple of 16 (whole mirrored pairs of 8-column
+  // groups); otherwise the plain kernel runs.
   static cudaError_t col(const PassArgs& a, bool adj, cudaStream_t s) {
     const size_t sm = PB::col_smem(a.n);
-    if (!a.tmap || a.tmap_rows != a.in_r1 - a.in_r0 || a.tmap_rows > 256 || sm > 227 * 1024)
+    if (!a.tmap || !a.hmap || a.tmap_rows != a.in_r1 - a.in_r0 || a.tmap_rows > 256 || LF::M % 16 != 0 ||
+        sm > 227 * 1024)
       return PassLaunch<LF>::col(a, adj, false, s);
     return half(a) ? col_h<true>(a, adj, sm, s) : col_h<false>(a, adj, sm, s);
   }
@@ -689,7 +723,8 @@ const PassOps* pass_ops_table() {
                             Pass<LF>::ROWL, Pass<LF>::COLL, &PL::col,    &PL::row_fwd,
                             &PL::row_out, &PL::row_seed,  &PL::row_adj,  &PL::row_in,
                             &PL::row_back, &PL::row_first, &PBL::col, &PBL::row_fwd,
-                            &PBL::row_adj, &PBL::row_first};
+                            &PBL::row_adj, &PBL::row_first, PassBulk<LF, RL>::GW, PassBulk<LF, RL>::HW,
+                            PassBulk<LF, RL>::HR};
   return &o;
 }
 
