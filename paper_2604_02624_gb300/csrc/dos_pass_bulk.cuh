@@ -117,43 +117,54 @@ struct PassBulk {
   // spectra, one dense [rows][8] block per group) and the H tile (two boxes
   // {10, HR, 1} of the quadrant table, whose rows are 16-byte multiples: pitch
   // M/2 + 2).  The spectra of the next item are fetched at the barrier inside
-  // the forward DFT (the stage has been read), the H tile of the next item at
-  // the barrier inside the inverse DFT (the tile has been read); both are
-  // waited for at the top of the item, with one block-wide verdict.
+  // the forward DFT (the stage has been read) and waited for at the top of the
+  // item, with one block-wide verdict; the H tile of the next item is fetched
+  // at the barrier inside the inverse DFT (the tile has been read) and waited
+  // for just before the H multiply, so its copy overlaps the forward DFT.  A
+  // thread whose H wait expires marks a shared flag (its item's results are
+  // then invalid, and reported so) that the next block-wide verdict reads.
   static constexpr int GW = Pass<LF>::COLL / 2;       // columns per group
   static constexpr int HW = GW + 2;                   // quadrant columns per H tile (c0 .. c0+9)
   static constexpr int HP = M / 2 + 2;                // quadrant pitch (rows and columns)
-  static constexpr int HR = ((HP / 2) + 7) / 8 * 8;   // rows per H box: two boxes cover the quadrant
+  // H boxes (at most 256 rows each): one of HP rows, or two of HR rows (a
+  // multiple of 8, so that the second lands 128-byte aligned)
+  static constexpr int NHB = HP <= 256 ? 1 : 2;
+  static constexpr int HR = NHB == 1 ? HP : ((HP + 1) / 2 + 7) / 8 * 8;
   static_assert(GW == 8 && HR <= 256, "column groups of 8, H boxes of at most 256 rows");
-  static_assert((HR * HW * 8) % 128 == 0, "the second H box must land 128-byte aligned");
+  static_assert(NHB == 1 || (HR * HW * 8) % 128 == 0, "the second H box must land 128-byte aligned");
   // group stride in the stage (float2): whole 128-byte lines for any row count
   __host__ __device__ static int col_group_stride(int rows) { return (rows + 1) / 2 * 2 * GW; }
   // dynamic shared memory (from a 128-byte aligned base):
-  //   stage[2][rows][8] | H tile[2 HR][10] | exchange[COLL][ZL] | tw[ZS] | barrier[2]
+  //   stage[2][rows][8] | H tile[NHB HR][10] | exchange[COLL][ZL] | tw[ZS] | barrier[2] | flag
   static size_t col_smem(int n) {
-    return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + 2 * (size_t)HR * HW + (size_t)COLL * ZL +
-                                   LF::ZS) + 2 * sizeof(uint64_t);
+    return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)NHB * HR * HW + (size_t)COLL * ZL +
+                                   LF::ZS) + 2 * sizeof(uint64_t) + sizeof(int);
   }
 
   template <bool ADJ>
   __device__ static void col(const PassArgs& a, const CUtensorMap* smap, const CUtensorMap* hmap) {
     extern __shared__ __align__(16) unsigned char col_raw[];
-    float2* stage = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(col_raw) + 127) & ~uintptr_t(127));
+    // 128-byte aligned start, by pointer arithmetic on the shared array: the
+    // compiler keeps seeing shared-memory pointers (an integer round trip
+    // would turn every access below into a generic one)
+    float2* stage = reinterpret_cast<float2*>(col_raw + ((128u - (sh_addr(col_raw) & 127u)) & 127u));
     const int GS = col_group_stride(a.n);
     float2* htile = stage + 2 * (size_t)GS;
-    float2* zb = htile + 2 * HR * HW;
+    float2* zb = htile + NHB * HR * HW;
     float2* tw = zb + (size_t)COLL * ZL;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);  // [0] spectra, [1] transfer-table tile
+    int* h_late = reinterpret_cast<int*>(bar + 2);              // an H wait of this block expired
     const int l = threadIdx.x % COLL, t = threadIdx.x / COLL;
     const int g = l / GW, lc = l % GW;
     float2* z = zb + l * ZL;
     constexpr int npairs = M / (2 * GW);
     const int items = a.nw * npairs;
     const uint32_t sbytes = 2u * GW * 8u * (uint32_t)(a.in_r1 - a.in_r0);
-    constexpr uint32_t hbytes = 2u * HW * HR * 8u;
+    constexpr uint32_t hbytes = (uint32_t)NHB * HW * HR * 8u;
     if (threadIdx.x == 0) {
       bulk_bar_init(&bar[0]);
       bulk_bar_init(&bar[1]);
+      *h_late = 0;
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(smap)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(hmap)) : "memory");
     }
@@ -182,7 +193,7 @@ struct PassBulk {
       if (a.stall == 1) return;
       const int w = it / npairs, c0 = GW * (it % npairs);
       tensor_copy(htile, hmap, c0, 0, a.hmap_z0 + w, &bar[1]);
-      tensor_copy(htile + HR * HW, hmap, c0, HR, a.hmap_z0 + w, &bar[1]);
+      if constexpr (NHB == 2) tensor_copy(htile + HR * HW, hmap, c0, HR, a.hmap_z0 + w, &bar[1]);
     };
     bool ok = true;
     int k = 0;
@@ -194,8 +205,8 @@ struct PassBulk {
       const int w = it / npairs, c0 = GW * (it % npairs);
       const int cc = g == 0 ? c0 + lc : M - c0 - GW + lc;  // this line's column
       const int hc = g == 0 ? lc : GW - lc;                 // its |kx| - c0: the column in the H tile
-      const bool got = bulk_wait(&bar[0], (uint32_t)(k & 1), split_verdict(a, k)) &&
-                       bulk_wait(&bar[1], (uint32_t)(k & 1));
+      // the spectra of this item, and no expired H wait in the previous one
+      const bool got = bulk_wait(&bar[0], (uint32_t)(k & 1), split_verdict(a, k)) && *h_late == 0;
       ok = __syncthreads_and(got) != 0;  // one verdict for the whole block
       if (!ok) break;
       float2 r[E];
@@ -214,6 +225,7 @@ struct PassBulk {
       if constexpr (!LF::SQUARE) __syncthreads();
       // H(|ky|, |kx|) from the tile: |ky| = k below M/2 and M - k above, both
       // affine in i at compile time
+      if (!bulk_wait(&bar[1], (uint32_t)(k & 1))) *h_late = 1;
       const float2* hlo = htile + t * HW + hc;
       const float2* hhi = htile + (M - t) * HW + hc;
       const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
@@ -228,7 +240,7 @@ struct PassBulk {
       }
       LF::template step1<true, LF::P, PKC, LF::SQUARE>(r, t, z, tw);
       __syncthreads();  // every thread is past its reads of the H tile: the next item's may land there
-      if (it + (int)gridDim.x < items) fetch_h(it + gridDim.x);
+      if (it + (int)gridDim.x < items && *h_late == 0) fetch_h(it + gridDim.x);
       // no trailing barrier: the exchange buffer is next written after the
       // barrier at the top of the next item
       LF::template step2<true, NOI, PKC, LF::SQUARE>(r, t, z);
@@ -240,9 +252,11 @@ struct PassBulk {
       }
     }
     if (!ok && threadIdx.x == 0) {
-      // both copies of the item the block gave up on land (bounded) before it leaves
+      // The copies in flight land (bounded) before the block leaves: the
+      // spectra of item k, and the H tile of item k (or, after an expired H
+      // wait in item k - 1, that tile: no further one was issued).
       (void)bulk_wait(&bar[0], (uint32_t)(k & 1));
-      (void)bulk_wait(&bar[1], (uint32_t)(k & 1));
+      (void)bulk_wait(&bar[1], (uint32_t)((*h_late ? k - 1 : k) & 1));
       atomicExch(a.err, 1);
     }
   }
