@@ -35,14 +35,22 @@ sys.path.insert(0, ROOT)
 # the bench scales them to the launch's channels.  An entry must be removed
 # (traffic reported as null) when its kernel changes.
 TRAFFIC_PER_CHANNEL = {
-    # TMA column pass with packed butterflies, all ten column launches of one step
-    # captured: forward 1.4013 / 1.3898 / 1.3909 / 1.3905 MB and 1.0654 MB (last gap,
-    # field-of-view output rows); adjoint 0.9047 MB (first gap, field-of-view
-    # input rows) and 1.3905 / 1.3901 / 1.3913 / 1.3902 MB
-    ("column_bulk", 200, 400, "column_forward"): ((1.401272e6 + 1.389845e6 + 1.390920e6 + 1.390511e6
-                                                   + 1.065403e6) / 5, "profiles/column_pass_bulk_batched.md"),
-    ("column_bulk", 200, 400, "column_adjoint"): ((0.904732e6 + 1.390524e6 + 1.390091e6 + 1.391332e6
-                                                   + 1.390215e6) / 5, "profiles/column_pass_bulk_batched.md"),
+    # one capture of every bulk pass of a step (dram__bytes_read + write per
+    # launch / 256 channels), each kind averaged over its five launches:
+    # forward column 1.3861 / 1.3858 / 1.3863 / 1.3858 MB and 1.0645 MB (last gap,
+    # field-of-view output rows); adjoint column 0.9063 MB (first gap, field-of-view
+    # input rows) and 1.3858 / 1.3860 / 1.3859 / 1.3862 MB; forward row 0.7382 MB
+    # (first pass, from the input-field table) and 1.3712 / 1.3719 / 1.3713 /
+    # 1.3711 MB; adjoint row 1.4254 / 1.4253 / 1.4266 / 1.4244 MB and 0.9883 MB
+    # (layer 1: no spectra written back)
+    ("column_bulk", 200, 400, "column_forward"): ((1.3861e6 + 1.3858e6 + 1.3863e6 + 1.3858e6 + 1.0645e6) / 5,
+                                                  "profiles/column_pass_bulk_batched.md"),
+    ("column_bulk", 200, 400, "column_adjoint"): ((0.9063e6 + 1.3858e6 + 1.3860e6 + 1.3859e6 + 1.3862e6) / 5,
+                                                  "profiles/column_pass_bulk_batched.md"),
+    ("row_bulk", 200, 400, "row_forward"): ((0.7382e6 + 1.3712e6 + 1.3719e6 + 1.3713e6 + 1.3711e6) / 5,
+                                            "profiles/row_passes_batched.md"),
+    ("row_bulk", 200, 400, "row_adjoint"): ((1.4254e6 + 1.4253e6 + 1.4266e6 + 1.4244e6 + 0.9883e6) / 5,
+                                            "profiles/row_passes_batched.md"),
 }
 
 
@@ -73,14 +81,18 @@ def step_bytes(n, m, K, F, nw, bin_=1):
 
 
 def kernel_family(detail, kind):
-    """Which kernel of a multi-pass kind ran: 'column_bulk' / 'column_plain'
-    for the column passes, from the configuration name dos_describe prints
-    (multipass, multipass:bulk or multipass:bulk[col+...])."""
+    """Which kernel of a multi-pass kind ran ('column_bulk' / 'column_plain',
+    'row_bulk' / 'row_plain'), from the configuration name dos_describe prints
+    (multipass, multipass:bulk or multipass:bulk[col+row_fwd+...])."""
     name = detail.split("|")[0].strip().split()[0].removeprefix("path=")
-    if not kind.startswith("column") or not name.startswith("multipass"):
+    if not name.startswith("multipass"):
         return None
-    bulk = name == "multipass:bulk" or (name.startswith("multipass:bulk[") and "col" in name)
-    return "column_bulk" if bulk else "column_plain"
+    tag = {"column_forward": "col", "column_adjoint": "col", "row_forward": "row_fwd",
+           "row_adjoint": "row_adj"}.get(kind)
+    if tag is None:
+        return None
+    bulk = name == "multipass:bulk" or (name.startswith("multipass:bulk[") and tag in name[15:].rstrip("]").split("+"))
+    return ("column_" if kind.startswith("column") else "row_") + ("bulk" if bulk else "plain")
 
 
 METRIC = "lambda-channel layer-propagations/s (fwd+adjoint, 4096 lambda)"

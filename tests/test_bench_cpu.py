@@ -15,7 +15,11 @@ def test_kernel_family_from_configuration_name():
     assert kf("path=multipass:bulk[col+row_fwd] | tuned", "column_adjoint") == "column_bulk"
     assert kf("path=multipass:bulk[row_fwd+row_adj] | tuned", "column_forward") == "column_plain"
     assert kf("path=multipass (DOS_FORCE_CONFIG)", "column_adjoint") == "column_plain"
-    assert kf("path=multipass:bulk[col] (DOS_FORCE_CONFIG)", "row_forward") is None
+    assert kf("path=multipass:bulk[col] (DOS_FORCE_CONFIG)", "row_forward") == "row_plain"
+    assert kf("path=multipass:bulk[row_fwd+row_adj] | tuned", "row_adjoint") == "row_bulk"
+    assert kf("path=multipass:bulk | tuned", "row_forward") == "row_bulk"
+    assert kf("path=multipass:bulk[col+row_fwd] | tuned", "row_adjoint") == "row_plain"
+    assert kf("path=multipass:bulk", "loss") is None
     assert kf("path=fused:C5:L16 threads=320 clusters=28 smem=1", "column_forward") is None
 
 
