@@ -132,12 +132,18 @@ struct PassBulk {
   static constexpr int HR = NHB == 1 ? HP : ((HP + 1) / 2 + 7) / 8 * 8;
   static_assert(GW == 8 && HR <= 256, "column groups of 8, H boxes of at most 256 rows");
   static_assert(NHB == 1 || (HR * HW * 8) % 128 == 0, "the second H box must land 128-byte aligned");
+  // The H tile is staged where the block still fits twice on an SM with it
+  // (M <= 400: 99.6 KB at N = 200); at M = 512 the exchange buffers alone take
+  // 70 KB, so the tile stays out and each thread reads its H values from the
+  // table (L2-resident per channel) at the multiply: 107 KB, two blocks per SM.
+  static constexpr bool STAGE_H = M <= 400;
+  static constexpr int HTILE = STAGE_H ? NHB * HR * HW : 0;  // float2 of the H tile in shared memory
   // group stride in the stage (float2): whole 128-byte lines for any row count
   __host__ __device__ static int col_group_stride(int rows) { return (rows + 1) / 2 * 2 * GW; }
   // dynamic shared memory (from a 128-byte aligned base):
   //   stage[2][rows][8] | H tile[NHB HR][10] | exchange[COLL][ZL] | tw[ZS] | barrier[2] | flag
   static size_t col_smem(int n) {
-    return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)NHB * HR * HW + (size_t)COLL * ZL +
+    return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)HTILE + (size_t)COLL * ZL +
                                    LF::ZS) + 2 * sizeof(uint64_t) + sizeof(int);
   }
 
@@ -150,7 +156,7 @@ struct PassBulk {
     float2* stage = reinterpret_cast<float2*>(col_raw + ((128u - (sh_addr(col_raw) & 127u)) & 127u));
     const int GS = col_group_stride(a.n);
     float2* htile = stage + 2 * (size_t)GS;
-    float2* zb = htile + NHB * HR * HW;
+    float2* zb = htile + HTILE;
     float2* tw = zb + (size_t)COLL * ZL;
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);  // [0] spectra, [1] transfer-table tile
     int* h_late = reinterpret_cast<int*>(bar + 2);              // an H wait of this block expired
@@ -187,7 +193,7 @@ struct PassBulk {
       tensor_copy(stage + GS, smap, M - c0 - GW, a.in_r0, w, &bar[0]);
     };
     auto fetch_h = [&](int it) {
-      if (threadIdx.x != 0) return;
+      if (!STAGE_H || threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bulk_expect(&bar[1], hbytes);
       if (a.stall == 1) return;
@@ -225,13 +231,18 @@ struct PassBulk {
       if constexpr (!LF::SQUARE) __syncthreads();
       // H(|ky|, |kx|) from the tile: |ky| = k below M/2 and M - k above, both
       // affine in i at compile time
-      if (!bulk_wait(&bar[1], (uint32_t)(k & 1))) *h_late = 1;
-      const float2* hlo = htile + t * HW + hc;
-      const float2* hhi = htile + (M - t) * HW + hc;
+      if (STAGE_H && !bulk_wait(&bar[1], (uint32_t)(k & 1))) *h_late = 1;
+      // the tile's rows (pitch HW), or the table's (pitch hs) when it is not staged
+      const int hpitch = STAGE_H ? HW : a.hs;
+      const float2* hbase = STAGE_H ? htile : a.Hq + (size_t)w * a.hs * a.hs + c0;
+      const float2* hlo = hbase + t * hpitch + hc;
+      const float2* hhi = hbase + (M - t) * hpitch + hc;
       const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
-        float2 h = i < E / 2 ? hlo[T * i * HW] : hhi[-T * i * HW];
+        float2 h;
+        if constexpr (STAGE_H) h = i < E / 2 ? hlo[T * i * HW] : hhi[-T * i * HW];
+        else h = i < E / 2 ? __ldg(hlo + (size_t)T * i * hpitch) : __ldg(hhi - (size_t)T * i * hpitch);
         if (Sw) {
           const int kk = t + T * i;
           h = cmul(h, misalign_factor(a.mis, kk, cc, M, Sw[(size_t)min(kk, M - kk) * a.hs + c0 + hc]));
@@ -256,7 +267,7 @@ struct PassBulk {
       // spectra of item k, and the H tile of item k (or, after an expired H
       // wait in item k - 1, that tile: no further one was issued).
       (void)bulk_wait(&bar[0], (uint32_t)(k & 1));
-      (void)bulk_wait(&bar[1], (uint32_t)((*h_late ? k - 1 : k) & 1));
+      if (STAGE_H) (void)bulk_wait(&bar[1], (uint32_t)((*h_late ? k - 1 : k) & 1));
       atomicExch(a.err, 1);
     }
   }
