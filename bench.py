@@ -107,6 +107,8 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--n-lambda", type=int, default=0,
+                   help="channels of the workload (0: its own count); smaller designs for profiling")
     p.add_argument("--path", default="auto")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -115,10 +117,10 @@ def _args():
     return p.parse_args()
 
 
-def _workload(name, rank, world):
+def _workload(name, rank, world, n_lambda=0):
     from paper_2604_02624_gb300 import sharding
     from paper_2604_02624_gb300 import workloads as W
-    w = W.workload(name)
+    w = W.workload(name, n_lambda=n_lambda) if n_lambda else W.workload(name)
     if world > 1:
         # weak scaling: the design holds world * N_w channels, rank r owns one shard
         nw = w.n_lambda
@@ -261,7 +263,7 @@ def run_reference(a):
     if rank != 0:
         return 0
     from paper_2604_02624_gb300 import workloads as W
-    w = _workload(a.workload, 0, 1)
+    w = _workload(a.workload, 0, 1, a.n_lambda)
     h = W.thickness(w, 0)
     T = W.targets(w, 1)
     pool = OraclePool(w, h, T)
@@ -304,7 +306,7 @@ def run_ours(a):
     from paper_2604_02624_gb300 import _lib as L
     from paper_2604_02624_gb300.api import DiffractiveStack
 
-    w = _workload(a.workload, rank, world)
+    w = _workload(a.workload, rank, world, a.n_lambda)
     h_np = W.thickness(w, 0)
     T_np = W.targets(w, 1)
     stack = DiffractiveStack.from_workload(w, device=dev, n_lambda_total=w.n_lambda * world,

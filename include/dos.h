@@ -220,8 +220,11 @@ DOS_API int dos_loss(dos_ctx *ctx, const float *d_T, double *h_loss, float *d_ps
  *   dos_loss (h_loss may be NULL; then the loss is not read back).
  *   cuda_stream  stream of the caller's device (NULL: legacy default stream).
  * The first call on each device (with that device current) looks up the
- * scratch address; make that first call before any stream capture.  Calls
- * allocate nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * scratch address, and so does the first call under another CUDA context of
+ * that device (a primary context recreated after cudaDeviceReset, a driver
+ * context the caller made current); make such a first call before any stream
+ * capture.  Calls allocate nothing: no cudaMalloc, cudaFree or allocating
+ * library routine.
  * Every call on a device shares the same scratch, which keeps the contents
  * of the last call (each call overwrites what it reads, nothing has to be
  * cleared): calls that overlap on the GPU (other streams, other threads)

@@ -8,6 +8,8 @@
 // serves them: the same statistics kernels, with their scratch in a
 // file-scope __device__ array of fixed size that every GPU loading this
 // library holds until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -90,12 +92,17 @@ __global__ void k_dldi_from_intensity(const float* __restrict__ I, const float* 
   dLdI[i] = (float)g;
 }
 
-// Device addresses of the scratch, looked up once per device with that
-// device current (host code cannot use the symbols' names as addresses).
+// Device addresses of the scratch, looked up with the device current (host
+// code cannot use the symbols' names as addresses).  The addresses belong to
+// the context the module was loaded in, so each device's entry remembers that
+// context's process-unique id and is looked up again under another one (a
+// primary context recreated after cudaDeviceReset, a caller's own driver
+// context).
 constexpr int kMaxDevices = 64;
 struct Scratch {
   LossStats* stats = nullptr;
   double* loss = nullptr;
+  unsigned long long ctx_id = 0;
 };
 Scratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
@@ -105,14 +112,45 @@ int na_fail(int code, const std::string& msg) {
   return code;
 }
 
+// Process-unique id of the calling thread's current context (cuCtxGetId,
+// found through the runtime's driver entry points); 0 when it cannot be told,
+// and then the addresses are looked up on every call.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(fn);
+    (void)cudaGetLastError();
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
 int scratch_for_current_device(Scratch* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(DOS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return na_fail(DOS_ERR_UNSUPPORTED, "device index beyond 63");
+  // 0 also when no context is current yet: the lookup below binds the
+  // runtime's context to the thread, and the entry records that one
+  const unsigned long long ctx_id = current_context_id();
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   Scratch& s = g_scratch[dev];
-  if (!s.stats) {
+  if (!s.stats || ctx_id == 0 || s.ctx_id != ctx_id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_stats);
     if (e != cudaSuccess)
@@ -123,6 +161,7 @@ int scratch_for_current_device(Scratch* out) {
       return na_fail(DOS_ERR_CUDA, std::string("cudaGetSymbolAddress(loss): ") + cudaGetErrorString(e));
     s.stats = static_cast<LossStats*>(p);
     s.loss = static_cast<double*>(q);
+    s.ctx_id = current_context_id();
   }
   *out = s;
   return DOS_OK;

@@ -56,6 +56,45 @@ def test_noalloc_scoring_matches_dos_loss_on_two_calls_in_a_row(loss, mode):
     st.close()
 
 
+def test_noalloc_sharded_normalisation_and_no_loss_readback():
+    """A shard of a larger design (n_lambda_total = 2 n_lambda) scores like
+    dos_loss of a context created with the same n_lambda_total; with h_loss
+    NULL the loss is not read back but PSNR and dL/dI are still written.
+    Around the calls neither torch's allocator nor the device's free memory
+    changes: the entry point allocates nothing."""
+    w = W.workload("small")
+    h = torch.tensor(W.thickness(w, 0), dtype=torch.float32, device=DEV)
+    T = torch.tensor(W.targets(w, 1), dtype=torch.float32, device=DEV)
+    total = 2 * w.n_lambda
+    st = DiffractiveStack.from_workload(w, device=DEV, n_lambda_total=total)
+    I = st.forward(h)
+    L_ref, psnr_ref, g_ref = st.loss(T)
+    psnr_ref = psnr_ref.cpu().numpy()
+    g_ref = g_ref.cpu().numpy().astype(np.float64)
+    stream = torch.cuda.current_stream(DEV).cuda_stream
+    psnr = torch.full((w.n_lambda,), float("nan"), device=DEV)
+    g = torch.full_like(T, float("nan"))
+    val = L.dos_loss_noalloc(I.data_ptr(), T.data_ptr(), w.n_lambda, w.fov, total, L.DOS_LOSS_MSE, True,
+                             psnr.data_ptr(), g.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert abs(val - L_ref) <= TOL_LOSS * abs(L_ref), (val, L_ref)
+    assert_close(g.cpu().numpy().astype(np.float64), g_ref, TOL_INTENSITY)
+    psnr.fill_(float("nan"))
+    g.fill_(float("nan"))
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated(DEV)
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    assert L.dos_loss_noalloc(I.data_ptr(), T.data_ptr(), w.n_lambda, w.fov, total, L.DOS_LOSS_MSE, False,
+                              psnr.data_ptr(), g.data_ptr(), stream) is None
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated(DEV) == alloc0
+    free1, _ = torch.cuda.mem_get_info(DEV)
+    assert free1 == free0
+    assert np.max(np.abs(psnr.cpu().numpy() - psnr_ref)) <= 1e-3
+    assert_close(g.cpu().numpy().astype(np.float64), g_ref, TOL_INTENSITY)
+    st.close()
+
+
 def test_noalloc_rejects_more_channels_than_its_scratch_holds():
     dummy = torch.zeros(4, device=DEV)
     with pytest.raises(L.DosError) as e:
