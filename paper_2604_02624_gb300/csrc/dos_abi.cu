@@ -18,6 +18,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <functional>
 #include <new>
 #include <sstream>
 #include <string>
@@ -146,6 +147,7 @@ struct dos_ctx {
   // multi-pass passes that run their bulk-async prefetching kernels
   // (DOS_PATH_MULTIPASS_BULK: all three; the autotuner may mix them per kind)
   unsigned bulk = 0;
+
   int* d_err = nullptr;    // set by a kernel whose bounded wait expired
   int* h_err = nullptr;    // pinned copy
   // DOS_INJECT_WAIT_TIMEOUT (tests): the next bulk pass stalls.  1: its copies
@@ -600,6 +602,139 @@ int gemm_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dL
 }
 
 // ------------------------------------------------------------ launch sequences
+// One kernel launch of a multi-pass sequence: its kind (for the per-kernel
+// timer), what it launches on a given stream, and a name for errors.
+struct Launch {
+  int kind;
+  std::function<cudaError_t(cudaStream_t)> go;
+  const char* what;
+};
+
+// The pass arguments of the channel range [w0, w1): every per-channel array
+// starts at channel w0, the tensor-map coordinates are offset by w0.
+dos::PassArgs range_args(const dos_ctx* c, int w0, int w1) {
+  dos::PassArgs a = c->base();
+  a.S = c->S + (size_t)w0 * c->n * c->m;
+  a.o = c->o + (size_t)w0 * c->fov * c->fov;
+  a.chan = c->chan + w0;
+  a.nw = w1 - w0;
+  a.n_chunks = (a.nw + c->chunk - 1) / c->chunk;
+  a.tmap_w0 = w0;
+  return a;
+}
+
+// transfer table and displacement table of gap g for the channels from w0
+const float2* range_hq(const dos_ctx* c, int g, int w0) { return c->hq_slot(g) + (size_t)w0 * c->hs * c->hs; }
+dos::Misalign range_mis(const dos_ctx* c, int g, int w0) {
+  dos::Misalign m = c->gap_mis(g);
+  if (m.sq) m.sq += (size_t)w0 * c->hs * c->hs;
+  return m;
+}
+
+// forward: [gap 0 column pass,] K x (row pass + column pass), output row pass
+std::vector<Launch> forward_launches(dos_ctx* c, const float* d_h, float* d_I, int save, int w0, int w1) {
+  const dos::PassOps* op = c->ops;
+  const size_t n2 = (size_t)c->n * c->n;
+  std::vector<Launch> L;
+  dos::PassArgs a = range_args(c, w0, w1);
+  if (!c->ckpt1_is_v1) {
+    // the aperture field has the separable spectrum Arow[ky] Arow[kx]
+    a.Hq = range_hq(c, 0, w0);
+    a.mis = range_mis(c, 0, w0);
+    a.out_r0 = 0;
+    a.out_r1 = c->n;
+    L.push_back({DOS_KERNEL_COLUMN_FORWARD, [op, a](cudaStream_t s) { return op->col(a, false, true, s); },
+                 "forward column pass (aperture)"});
+  }
+  for (int l = 1; l <= c->K; ++l) {
+    a.h = d_h + (size_t)(l - 1) * n2;
+    a.ckpt = c->ckpt + ((size_t)(l - 1) * c->nw + w0) * n2;
+    const bool brow = (c->bulk & kBulkRowFwd) != 0;
+    a.stall = c->take_stall(kBulkRowFwd);
+    if (l == 1 && c->ckpt1_is_v1) {
+      a.fin = c->v1 + (size_t)w0 * n2;
+      L.push_back({DOS_KERNEL_ROW_FORWARD,
+                   [op, a, brow](cudaStream_t s) { return brow ? op->bulk_row_first(a, s) : op->row_first(a, s); },
+                   "first row pass"});
+    } else {
+      const bool sv = save != 0;
+      L.push_back({DOS_KERNEL_ROW_FORWARD,
+                   [op, a, brow, sv](cudaStream_t s) { return brow ? op->bulk_row_fwd(a, sv, s) : op->row_fwd(a, sv, s); },
+                   "forward row pass"});
+    }
+    a.Hq = range_hq(c, l, w0);
+    a.hmap_z0 = c->gap_slot[l] * c->nw + w0;
+    a.mis = range_mis(c, l, w0);
+    a.in_r0 = 0;
+    a.in_r1 = c->n;
+    a.out_r0 = l == c->K ? c->of : 0;
+    a.out_r1 = l == c->K ? c->of + c->fov : c->n;
+    const bool bcol = (c->bulk & kBulkCol) != 0;
+    a.stall = c->take_stall(kBulkCol);
+    L.push_back({DOS_KERNEL_COLUMN_FORWARD,
+                 [op, a, bcol](cudaStream_t s) { return bcol ? op->bulk_col(a, false, s) : op->col(a, false, false, s); },
+                 "forward column pass"});
+  }
+  a.I = d_I ? d_I + (size_t)w0 * c->fov * c->fov : nullptr;
+  L.push_back({DOS_KERNEL_ROW_OUTPUT, [op, a](cudaStream_t s) { return op->row_out(a, s); }, "output row pass"});
+  return L;
+}
+
+// adjoint: seed row pass, K x (column pass with conj H + row pass); the
+// gradient partials of the range's chunks (the caller reduces them)
+std::vector<Launch> backward_launches(dos_ctx* c, const float* d_h, const float* d_dLdI, int w0, int w1) {
+  const dos::PassOps* op = c->ops;
+  const size_t n2 = (size_t)c->n * c->n;
+  std::vector<Launch> L;
+  dos::PassArgs a = range_args(c, w0, w1);
+  a.dLdI = d_dLdI + (size_t)w0 * c->fov * c->fov;
+  L.push_back({DOS_KERNEL_ROW_SEED, [op, a](cudaStream_t s) { return op->row_seed(a, s); }, "adjoint seed row pass"});
+  for (int l = c->K; l >= 1; --l) {
+    a.Hq = range_hq(c, l, w0);
+    a.hmap_z0 = c->gap_slot[l] * c->nw + w0;
+    a.mis = range_mis(c, l, w0);
+    a.in_r0 = l == c->K ? c->of : 0;
+    a.in_r1 = l == c->K ? c->of + c->fov : c->n;
+    a.tmap = !c->have_tmap ? nullptr : l == c->K ? &c->tmap_F : &c->tmap_S;
+    a.tmap_rows = l == c->K ? c->fov : c->n;
+    a.out_r0 = 0;
+    a.out_r1 = c->n;
+    const bool bcol = (c->bulk & kBulkCol) != 0;
+    a.stall = c->take_stall(kBulkCol);
+    L.push_back({DOS_KERNEL_COLUMN_ADJOINT,
+                 [op, a, bcol](cudaStream_t s) { return bcol ? op->bulk_col(a, true, s) : op->col(a, true, false, s); },
+                 "adjoint column pass"});
+    a.h = d_h + (size_t)(l - 1) * n2;
+    a.ckpt = (l == 1 && c->ckpt1_is_v1) ? c->v1 + (size_t)w0 * n2 : c->ckpt + ((size_t)(l - 1) * c->nw + w0) * n2;
+    a.partial = c->partial + ((size_t)(l - 1) * c->n_chunks + w0 / c->chunk) * n2;
+    const bool brow = (c->bulk & kBulkRowAdj) != 0;
+    const bool first = l == 1;
+    a.stall = c->take_stall(kBulkRowAdj);
+    L.push_back({DOS_KERNEL_ROW_ADJOINT,
+                 [op, a, brow, first](cudaStream_t s) { return brow ? op->bulk_row_adj(a, first, s) : op->row_adj(a, first, s); },
+                 "adjoint row pass"});
+  }
+  return L;
+}
+
+int enqueue(dos_ctx* c, const Launch& l, cudaStream_t s) {
+  c->timer.begin(l.kind, s);
+  const cudaError_t e = l.go(s);
+  c->timer.end(s);
+  DOS_CUDA(e, l.what);
+  return DOS_OK;
+}
+
+// The launches of one channel range, in order on the context's stream.
+int run_launches(dos_ctx* c, const std::vector<Launch>& L) {
+  c->launches = (int)L.size();
+  for (const Launch& l : L) {
+    const int rc = enqueue(c, l, c->stream);
+    if (rc) return rc;
+  }
+  return DOS_OK;
+}
+
 int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
   const size_t n2 = (size_t)c->n * c->n;
   c->launches = 0;
@@ -643,52 +778,10 @@ int run_forward(dos_ctx* c, const float* d_h, float* d_I, int save) {
     c->launches = 1;
     return DOS_OK;
   }
-  const dos::PassOps* op = c->ops;
-  dos::PassArgs a = c->base();
   // gap 0 is the create-time table v1 unless the layers are displaced (then the
-  // first gap depends on layer 1's displacement): the aperture field has the
-  // separable spectrum Arow[ky] Arow[kx]
+  // first gap depends on layer 1's displacement)
   c->ckpt1_is_v1 = c->v1 && !c->mis_on;
-  if (!c->ckpt1_is_v1) {
-    a.Hq = c->hq_slot(0);
-    a.mis = c->gap_mis(0);
-    a.out_r0 = 0;
-    a.out_r1 = c->n;
-    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD, op->col(a, false, true, c->stream), "forward column pass (aperture)");
-    ++c->launches;
-  }
-  for (int l = 1; l <= c->K; ++l) {
-    a.h = d_h + (size_t)(l - 1) * n2;
-    a.ckpt = c->ckpt + (size_t)(l - 1) * c->nw * n2;
-    if (l == 1 && c->ckpt1_is_v1) {
-      a.fin = c->v1;
-      a.stall = c->take_stall(kBulkRowFwd);
-      DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,
-                (c->bulk & kBulkRowFwd) ? op->bulk_row_first(a, c->stream) : op->row_first(a, c->stream),
-                "first row pass");
-    } else {
-      a.stall = c->take_stall(kBulkRowFwd);
-      DOS_TIMED(c, DOS_KERNEL_ROW_FORWARD,
-                (c->bulk & kBulkRowFwd) ? op->bulk_row_fwd(a, save != 0, c->stream) : op->row_fwd(a, save != 0, c->stream),
-                "forward row pass");
-    }
-    a.Hq = c->hq_slot(l);
-    a.hmap_z0 = c->gap_slot[l] * c->nw;
-    a.mis = c->gap_mis(l);
-    a.in_r0 = 0;
-    a.in_r1 = c->n;
-    a.out_r0 = l == c->K ? c->of : 0;
-    a.out_r1 = l == c->K ? c->of + c->fov : c->n;
-    a.stall = c->take_stall(kBulkCol);
-    DOS_TIMED(c, DOS_KERNEL_COLUMN_FORWARD,
-              (c->bulk & kBulkCol) ? op->bulk_col(a, false, c->stream) : op->col(a, false, false, c->stream),
-              "forward column pass");
-    c->launches += 2;
-  }
-  a.I = d_I;
-  DOS_TIMED(c, DOS_KERNEL_ROW_OUTPUT, op->row_out(a, c->stream), "output row pass");
-  ++c->launches;
-  return DOS_OK;
+  return run_launches(c, forward_launches(c, d_h, d_I, save, 0, c->nw));
 }
 
 int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLdh) {
@@ -734,34 +827,8 @@ int run_backward(dos_ctx* c, const float* d_h, const float* d_dLdI, float* d_dLd
     c->launches = 2;
     return DOS_OK;
   }
-  const dos::PassOps* op = c->ops;
-  dos::PassArgs a = c->base();
-  a.dLdI = d_dLdI;
-  DOS_TIMED(c, DOS_KERNEL_ROW_SEED, op->row_seed(a, c->stream), "adjoint seed row pass");
-  ++c->launches;
-  for (int l = c->K; l >= 1; --l) {
-    a.Hq = c->hq_slot(l);
-    a.hmap_z0 = c->gap_slot[l] * c->nw;
-    a.mis = c->gap_mis(l);
-    a.in_r0 = l == c->K ? c->of : 0;
-    a.in_r1 = l == c->K ? c->of + c->fov : c->n;
-    a.tmap = !c->have_tmap ? nullptr : l == c->K ? &c->tmap_F : &c->tmap_S;
-    a.tmap_rows = l == c->K ? c->fov : c->n;
-    a.out_r0 = 0;
-    a.out_r1 = c->n;
-    a.stall = c->take_stall(kBulkCol);
-    DOS_TIMED(c, DOS_KERNEL_COLUMN_ADJOINT,
-              (c->bulk & kBulkCol) ? op->bulk_col(a, true, c->stream) : op->col(a, true, false, c->stream),
-              "adjoint column pass");
-    a.h = d_h + (size_t)(l - 1) * n2;
-    a.ckpt = (l == 1 && c->ckpt1_is_v1) ? c->v1 : c->ckpt + (size_t)(l - 1) * c->nw * n2;
-    a.partial = c->partial + (size_t)(l - 1) * c->n_chunks * n2;
-    a.stall = c->take_stall(kBulkRowAdj);
-    DOS_TIMED(c, DOS_KERNEL_ROW_ADJOINT,
-              (c->bulk & kBulkRowAdj) ? op->bulk_row_adj(a, l == 1, c->stream) : op->row_adj(a, l == 1, c->stream),
-              "adjoint row pass");
-    c->launches += 2;
-  }
+  const int rc = run_launches(c, backward_launches(c, d_h, d_dLdI, 0, c->nw));
+  if (rc) return rc;
   DOS_TIMED(c, DOS_KERNEL_GRAD_REDUCE,
             dos::launch_grad_reduce(c->partial, d_dLdh, c->n_chunks, (size_t)c->K * n2, n2, c->stream),
             "gradient reduction");
@@ -778,14 +845,14 @@ constexpr int multipass_choice(unsigned mask) { return -1 - (int)mask; }
 unsigned choice_mask(int idx) { return (unsigned)(-1 - idx); }
 
 std::string choice_name(const dos_ctx* x, int idx) {
-  if (idx == kPlain) return "multipass";
-  if (idx == kBulk) return "multipass:bulk";
   if (idx < 0) {
-    const unsigned m = choice_mask(idx);
+    const unsigned b = choice_mask(idx);
+    if (b == 0) return "multipass";
+    if (b == kBulkAll) return "multipass:bulk";
     std::string s = "multipass:bulk[";
-    if (m & kBulkCol) s += "col";
-    if (m & kBulkRowFwd) s += std::string(s.back() == '[' ? "" : "+") + "row_fwd";
-    if (m & kBulkRowAdj) s += std::string(s.back() == '[' ? "" : "+") + "row_adj";
+    if (b & kBulkCol) s += "col";
+    if (b & kBulkRowFwd) s += std::string(s.back() == '[' ? "" : "+") + "row_fwd";
+    if (b & kBulkRowAdj) s += std::string(s.back() == '[' ? "" : "+") + "row_adj";
     return s + "]";
   }
   const dos::FusedOps* f = x->fcands[idx];

@@ -67,7 +67,8 @@ struct PassArgs {
   const void* tmap;       // host CUtensorMap of S as [nw][n][m] 8-byte elements (bulk column pass), or null
   int tmap_rows;          // rows of its box: the bulk column pass uses it when they are in_r1 - in_r0
   const void* hmap;       // host CUtensorMap of the transfer tables as [slots * nw][hs][hs] 8-byte elements
-  int hmap_z0;            // its channel coordinate of this gap's table slot: slot * nw
+  int hmap_z0;            // its channel coordinate of this gap's table slot and channel range: slot * nw + w0
+  int tmap_w0;            // channel coordinate of channel 0 of this range in the spectra maps
 };
 
 // Kernel launchers of one padded size M (one translation unit per M).

@@ -189,8 +189,8 @@ struct PassBulk {
       bulk_expect(&bar[0], sbytes);
       if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
       const int w = it / npairs, c0 = GW * (it % npairs);
-      tensor_copy(stage, smap, c0, a.in_r0, w, &bar[0]);
-      tensor_copy(stage + GS, smap, M - c0 - GW, a.in_r0, w, &bar[0]);
+      tensor_copy(stage, smap, c0, a.in_r0, a.tmap_w0 + w, &bar[0]);
+      tensor_copy(stage + GS, smap, M - c0 - GW, a.in_r0, a.tmap_w0 + w, &bar[0]);
     };
     auto fetch_h = [&](int it) {
       if (!STAGE_H || threadIdx.x != 0) return;
