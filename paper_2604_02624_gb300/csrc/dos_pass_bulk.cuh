@@ -140,11 +140,33 @@ struct PassBulk {
   static constexpr int HTILE = STAGE_H ? NHB * HR * HW : 0;  // float2 of the H tile in shared memory
   // group stride in the stage (float2): whole 128-byte lines for any row count
   __host__ __device__ static int col_group_stride(int rows) { return (rows + 1) / 2 * 2 * GW; }
+  // The two groups of an item share only the H tile: a group's 8 lines are
+  // held by warps of their own (thread = group g, line lc, element owner t:
+  // g = tid / GT, lc = tid % 8, t = (tid % GT) / 8), so the exchanges inside
+  // the line DFTs synchronise the group's warps on a named barrier, and only
+  // the top of an item is a block-wide barrier.  With GT not a multiple of the
+  // warp size (M = 200) the groups share warps and the block barrier serves.
+  static constexpr int GT = GW * T;                    // threads of a group
+  static constexpr bool GROUP_BARS = GT % 32 == 0;
+  // exchange-matrix stride between the lines (float2): at least ZS and 2 mod
+  // 16, which with a group warp's 8 lines x 4 consecutive element owners puts
+  // every exchange write and read (both layouts) on distinct bank pairs
+  static constexpr int ZLB = LF::ZS + ((2 - LF::ZS % 16) + 16) % 16;
+  __device__ static __forceinline__ void group_sync(int g) {
+    if constexpr (GROUP_BARS) {
+      // g is uniform over a warp; immediate barrier ids keep the count of
+      // barriers the kernel reserves at three
+      if (g == 0) asm volatile("bar.sync 1, %0;" ::"n"(GT) : "memory");
+      else asm volatile("bar.sync 2, %0;" ::"n"(GT) : "memory");
+    } else {
+      __syncthreads();
+    }
+  }
   // dynamic shared memory (from a 128-byte aligned base):
-  //   stage[2][rows][8] | H tile[NHB HR][10] | exchange[COLL][ZL] | tw[ZS] | barrier[2] | flag
+  //   stage[2][rows][8] | H tile[NHB HR][10] | exchange[COLL][ZLB] | tw[ZS] | barrier[3] | flag
   static size_t col_smem(int n) {
-    return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)HTILE + (size_t)COLL * ZL +
-                                   LF::ZS) + 2 * sizeof(uint64_t) + sizeof(int);
+    return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)HTILE + (size_t)COLL * ZLB +
+                                   LF::ZS) + 3 * sizeof(uint64_t) + sizeof(int);
   }
 
   template <bool ADJ>
@@ -157,19 +179,21 @@ struct PassBulk {
     const int GS = col_group_stride(a.n);
     float2* htile = stage + 2 * (size_t)GS;
     float2* zb = htile + HTILE;
-    float2* tw = zb + (size_t)COLL * ZL;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);  // [0] spectra, [1] transfer-table tile
-    int* h_late = reinterpret_cast<int*>(bar + 2);              // an H wait of this block expired
-    const int l = threadIdx.x % COLL, t = threadIdx.x / COLL;
-    const int g = l / GW, lc = l % GW;
-    float2* z = zb + l * ZL;
+    float2* tw = zb + (size_t)COLL * ZLB;
+    // [0], [1] spectra of group 0, 1; [2] transfer-table tile
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    int* h_late = reinterpret_cast<int*>(bar + 3);  // an H wait of this block expired
+    const int g = threadIdx.x / GT, lc = threadIdx.x % GW, t = (threadIdx.x % GT) / GW;
+    const bool leader = threadIdx.x % GT == 0;  // issues the group's copies
+    float2* z = zb + (g * GW + lc) * ZLB;
     constexpr int npairs = M / (2 * GW);
     const int items = a.nw * npairs;
-    const uint32_t sbytes = 2u * GW * 8u * (uint32_t)(a.in_r1 - a.in_r0);
+    const uint32_t sbytes = GW * 8u * (uint32_t)(a.in_r1 - a.in_r0);
     constexpr uint32_t hbytes = (uint32_t)NHB * HW * HR * 8u;
     if (threadIdx.x == 0) {
       bulk_bar_init(&bar[0]);
       bulk_bar_init(&bar[1]);
+      bulk_bar_init(&bar[2]);
       *h_late = 0;
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(smap)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(hmap)) : "memory");
@@ -183,38 +207,37 @@ struct PassBulk {
           "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(zc), "r"(sh_addr(b))
           : "memory");
     };
-    auto fetch_s = [&](int it) {
-      if (threadIdx.x != 0) return;
+    // the input rows of group gg of item it (its leader)
+    auto fetch_s = [&](int it, int gg) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bulk_expect(&bar[0], sbytes);
+      bulk_expect(&bar[gg], sbytes);
       if (a.stall == 1) return;  // injected fault: the expected bytes never arrive
       const int w = it / npairs, c0 = GW * (it % npairs);
-      tensor_copy(stage, smap, c0, a.in_r0, a.tmap_w0 + w, &bar[0]);
-      tensor_copy(stage + GS, smap, M - c0 - GW, a.in_r0, a.tmap_w0 + w, &bar[0]);
+      tensor_copy(stage + gg * GS, smap, gg == 0 ? c0 : M - c0 - GW, a.in_r0, a.tmap_w0 + w, &bar[gg]);
     };
+    // the H tile of item it (thread 0)
     auto fetch_h = [&](int it) {
-      if (!STAGE_H || threadIdx.x != 0) return;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bulk_expect(&bar[1], hbytes);
+      bulk_expect(&bar[2], hbytes);
       if (a.stall == 1) return;
       const int w = it / npairs, c0 = GW * (it % npairs);
-      tensor_copy(htile, hmap, c0, 0, a.hmap_z0 + w, &bar[1]);
-      if constexpr (NHB == 2) tensor_copy(htile + HR * HW, hmap, c0, HR, a.hmap_z0 + w, &bar[1]);
+      tensor_copy(htile, hmap, c0, 0, a.hmap_z0 + w, &bar[2]);
+      if constexpr (NHB == 2) tensor_copy(htile + HR * HW, hmap, c0, HR, a.hmap_z0 + w, &bar[2]);
     };
     bool ok = true;
     int k = 0;
-    if ((int)blockIdx.x < items) {
-      fetch_s(blockIdx.x);
-      fetch_h(blockIdx.x);
-    }
+    if ((int)blockIdx.x < items && leader) fetch_s(blockIdx.x, g);
     for (int it = blockIdx.x; it < items; it += gridDim.x, ++k) {
       const int w = it / npairs, c0 = GW * (it % npairs);
       const int cc = g == 0 ? c0 + lc : M - c0 - GW + lc;  // this line's column
       const int hc = g == 0 ? lc : GW - lc;                 // its |kx| - c0: the column in the H tile
-      // the spectra of this item, and no expired H wait in the previous one
-      const bool got = bulk_wait(&bar[0], (uint32_t)(k & 1), split_verdict(a, k)) && *h_late == 0;
+      // this group's input rows, and no expired H wait in the previous item
+      const bool got = bulk_wait(&bar[g], (uint32_t)(k & 1), split_verdict(a, k)) && *h_late == 0;
       ok = __syncthreads_and(got) != 0;  // one verdict for the whole block
       if (!ok) break;
+      // every thread is past the previous item's H multiply: this item's tile
+      // may land (it is waited for just before the multiply)
+      if (STAGE_H && threadIdx.x == 0) fetch_h(it);
       float2 r[E];
       const float2* sg = stage + (size_t)g * GS + lc - (ptrdiff_t)a.in_r0 * GW;  // row y at sg[y * GW]
 #pragma unroll
@@ -223,15 +246,15 @@ struct PassBulk {
         r[i] = (i < EF && row >= a.in_r0 && row < a.in_r1) ? sg[row * GW] : czero();
       }
       LF::template step1<false, NZF, PKC>(r, t, z, tw);
-      __syncthreads();  // every thread is past its stage reads: the next item's rows may land there
-      if (it + (int)gridDim.x < items) fetch_s(it + gridDim.x);
+      group_sync(g);  // the group is past its stage reads: its next rows may land there
+      if (leader && it + (int)gridDim.x < items) fetch_s(it + gridDim.x, g);
       LF::template step2<false, LF::Q, PKC>(r, t, z);
       // square lines: the inverse DFT below writes the exchange matrix in
       // the transposed layout, i.e. only what this thread just read
-      if constexpr (!LF::SQUARE) __syncthreads();
+      if constexpr (!LF::SQUARE) group_sync(g);
       // H(|ky|, |kx|) from the tile: |ky| = k below M/2 and M - k above, both
       // affine in i at compile time
-      if (STAGE_H && !bulk_wait(&bar[1], (uint32_t)(k & 1))) *h_late = 1;
+      if (STAGE_H && !bulk_wait(&bar[2], (uint32_t)(k & 1))) *h_late = 1;
       // the tile's rows (pitch HW), or the table's (pitch hs) when it is not staged
       const int hpitch = STAGE_H ? HW : a.hs;
       const float2* hbase = STAGE_H ? htile : a.Hq + (size_t)w * a.hs * a.hs + c0;
@@ -250,8 +273,7 @@ struct PassBulk {
         r[i] = ADJ ? cmulc(r[i], h) : cmul(r[i], h);
       }
       LF::template step1<true, LF::P, PKC, LF::SQUARE>(r, t, z, tw);
-      __syncthreads();  // every thread is past its reads of the H tile: the next item's may land there
-      if (it + (int)gridDim.x < items && *h_late == 0) fetch_h(it + gridDim.x);
+      group_sync(g);
       // no trailing barrier: the exchange buffer is next written after the
       // barrier at the top of the next item
       LF::template step2<true, NOI, PKC, LF::SQUARE>(r, t, z);
@@ -263,11 +285,12 @@ struct PassBulk {
       }
     }
     if (!ok && threadIdx.x == 0) {
-      // The copies in flight land (bounded) before the block leaves: the
-      // spectra of item k, and the H tile of item k (or, after an expired H
-      // wait in item k - 1, that tile: no further one was issued).
+      // The copies in flight land (bounded) before the block leaves: both
+      // groups' rows of item k, and after an expired H wait in item k - 1
+      // that tile (no tile of item k was issued).
       (void)bulk_wait(&bar[0], (uint32_t)(k & 1));
-      if (STAGE_H) (void)bulk_wait(&bar[1], (uint32_t)((*h_late ? k - 1 : k) & 1));
+      (void)bulk_wait(&bar[1], (uint32_t)(k & 1));
+      if (STAGE_H && *h_late) (void)bulk_wait(&bar[2], (uint32_t)((k - 1) & 1));
       atomicExch(a.err, 1);
     }
   }
