@@ -250,7 +250,7 @@ struct dos_ctx {
     a.err = d_err;
     a.tmap = have_tmap ? &tmap_S : nullptr;
     a.tmap_rows = n;
-    a.hmap = have_tmap ? &tmap_H : nullptr;
+    a.hmap = (have_tmap && ops->h_box_cols > 0) ? &tmap_H : nullptr;
     return a;
   }
 };
@@ -306,8 +306,8 @@ int choose_path(dos_ctx* x, int requested);
 // opaque 64-bit words): the row spectra S as [nw][n][m], box {col_group
 // columns, n rows, 1 channel} (tmap_S) or {col_group, fov, 1} (tmap_F); the
 // transfer tables as [slots * nw][hs][hs] (rows of hs = m/2 + 2 entries, a
-// 16-byte multiple), box {h_box_cols, h_box_rows, 1} (tmap_H); rows past the
-// table read as zeros.
+// 16-byte multiple), box {h_box_cols, h_box_rows, 1} (tmap_H: whole table rows,
+// the quadrant being symmetric), when the column kernel stages an H tile.
 // A driver without the entry point leaves the plain column kernel in use.
 int make_spectra_map(dos_ctx* x) {
   x->have_tmap = false;
@@ -333,7 +333,7 @@ int make_spectra_map(dos_ctx* x) {
     if (r != CUDA_SUCCESS)
       return fail(DOS_ERR_CUDA, "cuTensorMapEncodeTiled(row spectra) failed: " + std::to_string((int)r));
   }
-  {
+  if (x->ops->h_box_cols > 0) {  // the column kernel of this size stages an H tile
     const cuuint64_t hdims[3] = {(cuuint64_t)x->hs, (cuuint64_t)x->hs, (cuuint64_t)x->n_slots * x->nw};
     const cuuint64_t hstrides[2] = {(cuuint64_t)x->hs * 8, (cuuint64_t)x->hs * x->hs * 8};
     const cuuint32_t hbox[3] = {(cuuint32_t)x->ops->h_box_cols, (cuuint32_t)x->ops->h_box_rows, 1};

@@ -90,7 +90,7 @@ struct PassOps {
   cudaError_t (*bulk_row_adj)(const PassArgs&, bool first, cudaStream_t);
   cudaError_t (*bulk_row_first)(const PassArgs&, cudaStream_t);  // t(h) * field (fin) -> row spectra
   // boxes of the bulk column pass's tensor copies: spectra {col_group, rows, 1},
-  // transfer table {h_box_cols, h_box_rows, 1}
+  // transfer table {h_box_cols, h_box_rows, 1} (h_box_cols 0: no staged H tile)
   int col_group, h_box_cols, h_box_rows;
 };
 

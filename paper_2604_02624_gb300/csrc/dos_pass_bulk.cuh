@@ -111,33 +111,34 @@ struct PassBulk {
   // An item is a mirrored pair of column groups of one channel: columns
   // c0 .. c0+7 (lines 0-7) and M-c0-8 .. M-c0-1 (lines 8-15), c0 = 8 p for
   // p < M/16.  H depends on |kx| only, and the two groups' |kx| are c0 .. c0+8,
-  // so one tile of 10 quadrant columns starting at x = c0 (even: a legal TMA
-  // start for 8-byte elements) serves all 16 columns.  Per item, four tensor
-  // copies: the two groups' input rows (box {8, in_r1 - in_r0, 1} of the row
-  // spectra, one dense [rows][8] block per group) and the H tile (two boxes
-  // {10, HR, 1} of the quadrant table, whose rows are 16-byte multiples: pitch
-  // M/2 + 2).  The spectra of the next item are fetched at the barrier inside
-  // the forward DFT (the stage has been read) and waited for at the top of the
-  // item, with one block-wide verdict; the H tile of the next item is fetched
-  // at the barrier inside the inverse DFT (the tile has been read) and waited
-  // for just before the H multiply, so its copy overlaps the forward DFT.  A
-  // thread whose H wait expires marks a shared flag (its item's results are
-  // then invalid, and reported so) that the next block-wide verdict reads.
+  // so one tile of 10 |kx| values (c0 .. c0+9) serves all 16 columns.  The
+  // quadrant table is symmetric, H(|ky|, |kx|) = H(|kx|, |ky|) (the setup forms
+  // q = k^2 - (fx^2 + fy^2), the same in either order), so the tile is fetched
+  // as the table's rows c0 .. c0+9, all M/2 + 2 entries each (box {M/2+2, 10,
+  // 1}; a row is a 16-byte multiple), and held as tile[|kx| - c0][|ky|]: then
+  // the 16 reads of a half-warp (8 lines x 2 element owners) fall on distinct
+  // bank pairs.  Per item, three tensor copies: the two groups' input rows (box
+  // {8, in_r1 - in_r0, 1} of the row spectra, one dense [rows][8] block per
+  // group) and the H tile.  The spectra of the next item are fetched at the
+  // barrier inside the forward DFT (the stage has been read) and waited for at
+  // the top of the item, with one block-wide verdict; the H tile of an item is
+  // fetched at its top (every thread is past the previous item's multiply)
+  // and waited for just before the H multiply, so its copy overlaps the
+  // forward DFT.  A thread whose H wait expires marks a shared flag (its
+  // item's results are then invalid, and reported so) that the next
+  // block-wide verdict reads.
   static constexpr int GW = Pass<LF>::COLL / 2;       // columns per group
-  static constexpr int HW = GW + 2;                   // quadrant columns per H tile (c0 .. c0+9)
+  static constexpr int HW = GW + 2;                   // |kx| values per H tile (c0 .. c0+9)
   static constexpr int HP = M / 2 + 2;                // quadrant pitch (rows and columns)
-  // H boxes (at most 256 rows each): one of HP rows, or two of HR rows (a
-  // multiple of 8, so that the second lands 128-byte aligned)
-  static constexpr int NHB = HP <= 256 ? 1 : 2;
-  static constexpr int HR = NHB == 1 ? HP : ((HP + 1) / 2 + 7) / 8 * 8;
-  static_assert(GW == 8 && HR <= 256, "column groups of 8, H boxes of at most 256 rows");
-  static_assert(NHB == 1 || (HR * HW * 8) % 128 == 0, "the second H box must land 128-byte aligned");
+  static_assert(GW == 8, "column groups of 8");
   // The H tile is staged where the block still fits twice on an SM with it
-  // (M <= 400: 99.6 KB at N = 200); at M = 512 the exchange buffers alone take
-  // 70 KB, so the tile stays out and each thread reads its H values from the
-  // table (L2-resident per channel) at the multiply: 107 KB, two blocks per SM.
+  // and a table row fits one box (M <= 400: 100.8 KB at N = 200); at M = 512
+  // the exchange buffers alone take 70 KB, so the tile stays out and each
+  // thread reads its H values from the table (L2-resident per channel) at the
+  // multiply: 107 KB, two blocks per SM.
   static constexpr bool STAGE_H = M <= 400;
-  static constexpr int HTILE = STAGE_H ? NHB * HR * HW : 0;  // float2 of the H tile in shared memory
+  static_assert(!STAGE_H || HP <= 256, "a staged H tile row is one box row (at most 256 entries)");
+  static constexpr int HTILE = STAGE_H ? HW * HP : 0;  // float2 of the H tile in shared memory
   // group stride in the stage (float2): whole 128-byte lines for any row count
   __host__ __device__ static int col_group_stride(int rows) { return (rows + 1) / 2 * 2 * GW; }
   // The two groups of an item share only the H tile: a group's 8 lines are
@@ -163,7 +164,7 @@ struct PassBulk {
     }
   }
   // dynamic shared memory (from a 128-byte aligned base):
-  //   stage[2][rows][8] | H tile[NHB HR][10] | exchange[COLL][ZLB] | tw[ZS] | barrier[3] | flag
+  //   stage[2][rows][8] | H tile[10][M/2+2] | exchange[COLL][ZLB] | tw[ZS] | barrier[3] | flag
   static size_t col_smem(int n) {
     return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)HTILE + (size_t)COLL * ZLB +
                                    LF::ZS) + 3 * sizeof(uint64_t) + sizeof(int);
@@ -189,7 +190,7 @@ struct PassBulk {
     constexpr int npairs = M / (2 * GW);
     const int items = a.nw * npairs;
     const uint32_t sbytes = GW * 8u * (uint32_t)(a.in_r1 - a.in_r0);
-    constexpr uint32_t hbytes = (uint32_t)NHB * HW * HR * 8u;
+    constexpr uint32_t hbytes = (uint32_t)HW * HP * 8u;
     if (threadIdx.x == 0) {
       bulk_bar_init(&bar[0]);
       bulk_bar_init(&bar[1]);
@@ -221,8 +222,7 @@ struct PassBulk {
       bulk_expect(&bar[2], hbytes);
       if (a.stall == 1) return;
       const int w = it / npairs, c0 = GW * (it % npairs);
-      tensor_copy(htile, hmap, c0, 0, a.hmap_z0 + w, &bar[2]);
-      if constexpr (NHB == 2) tensor_copy(htile + HR * HW, hmap, c0, HR, a.hmap_z0 + w, &bar[2]);
+      tensor_copy(htile, hmap, 0, c0, a.hmap_z0 + w, &bar[2]);
     };
     bool ok = true;
     int k = 0;
@@ -255,17 +255,17 @@ struct PassBulk {
       // H(|ky|, |kx|) from the tile: |ky| = k below M/2 and M - k above, both
       // affine in i at compile time
       if (STAGE_H && !bulk_wait(&bar[2], (uint32_t)(k & 1))) *h_late = 1;
-      // the tile's rows (pitch HW), or the table's (pitch hs) when it is not staged
-      const int hpitch = STAGE_H ? HW : a.hs;
-      const float2* hbase = STAGE_H ? htile : a.Hq + (size_t)w * a.hs * a.hs + c0;
-      const float2* hlo = hbase + t * hpitch + hc;
-      const float2* hhi = hbase + (M - t) * hpitch + hc;
+      // tile[hc][|ky|] (pitch HP), or the table's H(|ky|, c0 + hc) (pitch hs)
+      // when the tile is not staged
+      const float2* hlo = STAGE_H ? htile + hc * HP + t : a.Hq + (size_t)w * a.hs * a.hs + (size_t)t * a.hs + c0 + hc;
+      const float2* hhi = STAGE_H ? htile + hc * HP + (M - t)
+                                  : a.Hq + (size_t)w * a.hs * a.hs + (size_t)(M - t) * a.hs + c0 + hc;
       const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         float2 h;
-        if constexpr (STAGE_H) h = i < E / 2 ? hlo[T * i * HW] : hhi[-T * i * HW];
-        else h = i < E / 2 ? __ldg(hlo + (size_t)T * i * hpitch) : __ldg(hhi - (size_t)T * i * hpitch);
+        if constexpr (STAGE_H) h = i < E / 2 ? hlo[T * i] : hhi[-T * i];
+        else h = i < E / 2 ? __ldg(hlo + (size_t)T * i * a.hs) : __ldg(hhi - (size_t)T * i * a.hs);
         if (Sw) {
           const int kk = t + T * i;
           h = cmul(h, misalign_factor(a.mis, kk, cc, M, Sw[(size_t)min(kk, M - kk) * a.hs + c0 + hc]));
@@ -707,8 +707,9 @@ struct PassBulkLaunch {
     auto kern = adj ? k_col_bulk<LF, RL, H, true> : k_col_bulk<LF, RL, H, false>;
     cudaError_t e = slots(kern, PB::CT, sm, &n_slots);
     if (e != cudaSuccess) return e;
+    // (without a staged tile the H map is not read: the spectra map stands in)
     kern<<<std::min(items, n_slots), PB::CT, sm, s>>>(a, *static_cast<const CUtensorMap*>(a.tmap),
-                                                     *static_cast<const CUtensorMap*>(a.hmap));
+                                                     *static_cast<const CUtensorMap*>(a.hmap ? a.hmap : a.tmap));
     return cudaGetLastError();
   }
   // The tensor copies need maps whose boxes hold the input rows (at most 256)
@@ -716,7 +717,8 @@ struct PassBulkLaunch {
   // groups); otherwise the plain kernel runs.
   static cudaError_t col(const PassArgs& a, bool adj, cudaStream_t s) {
     const size_t sm = PB::col_smem(a.n);
-    if (!a.tmap || !a.hmap || a.tmap_rows != a.in_r1 - a.in_r0 || a.tmap_rows > 256 || LF::M % 16 != 0 ||
+    if (!a.tmap || (PB::STAGE_H && !a.hmap) || a.tmap_rows != a.in_r1 - a.in_r0 || a.tmap_rows > 256 ||
+        LF::M % 16 != 0 ||
         sm > 227 * 1024)
       return PassLaunch<LF>::col(a, adj, false, s);
     return half(a) ? col_h<true>(a, adj, sm, s) : col_h<false>(a, adj, sm, s);
@@ -771,8 +773,8 @@ const PassOps* pass_ops_table() {
                             Pass<LF>::ROWL, Pass<LF>::COLL, &PL::col,    &PL::row_fwd,
                             &PL::row_out, &PL::row_seed,  &PL::row_adj,  &PL::row_in,
                             &PL::row_back, &PL::row_first, &PBL::col, &PBL::row_fwd,
-                            &PBL::row_adj, &PBL::row_first, PassBulk<LF, RL>::GW, PassBulk<LF, RL>::HW,
-                            PassBulk<LF, RL>::HR};
+                            &PBL::row_adj, &PBL::row_first, PassBulk<LF, RL>::GW,
+                            PassBulk<LF, RL>::STAGE_H ? PassBulk<LF, RL>::HP : 0, PassBulk<LF, RL>::HW};
   return &o;
 }
 

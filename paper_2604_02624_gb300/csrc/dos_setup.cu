@@ -27,7 +27,9 @@ __global__ void k_htable(float2* __restrict__ Hq, const double* __restrict__ lam
   const double fa = a * df;
   for (int b = threadIdx.x; b < hs; b += blockDim.x) {
     const double fb = b * df;
-    const double q = k2 - fa * fa - fb * fb;
+    // fx^2 + fy^2 first: the table is exactly symmetric, H(a, b) = H(b, a)
+    // (the bulk column pass reads a quadrant column as a table row)
+    const double q = k2 - (fa * fa + fb * fb);
     float2 h;
     if (q >= 0.0) {
       const double cyc = z * sqrt(q);
