@@ -353,8 +353,11 @@ struct PassBulk {
     bool okw = true;
     if (w0 < w1) fetch(w0);
     int k = 0;
+    // the next channel's constants are loaded one iteration ahead
+    ChanConst cnext = a.chan[w0 < w1 ? w0 : 0];
     for (int w = w0; w < w1; ++w, ++k) {
-      const ChanConst cc = a.chan[w];
+      const ChanConst cc = cnext;
+      if (w + 1 < w1) cnext = a.chan[w + 1];
       okw = __syncthreads_and(bulk_wait(bar, (uint32_t)(k & 1), split_verdict(a, k))) != 0;  // one verdict for the whole block
       if (!okw) break;
       float2 r[E];
@@ -477,8 +480,11 @@ struct PassBulk {
     bool okw = true;
     if (w0 < w1) fetch(w0);
     int k = 0;
+    // the next channel's constants are loaded one iteration ahead
+    ChanConst cnext = a.chan[w0 < w1 ? w0 : 0];
     for (int w = w0; w < w1; ++w, ++k) {
-      const ChanConst cc = a.chan[w];
+      const ChanConst cc = cnext;
+      if (w + 1 < w1) cnext = a.chan[w + 1];
       okw = __syncthreads_and(bulk_wait(bar, (uint32_t)(k & 1), split_verdict(a, k))) != 0;  // one verdict for the whole block
       if (!okw) break;
       float2 r[E];
