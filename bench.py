@@ -80,6 +80,17 @@ def step_bytes(n, m, K, F, nw, bin_=1):
     return {"design": nw * (fwd + loss + adj), "ideal": nw * (K + 1) * 40 * n * n}
 
 
+def method_bytes_per_launch(kind, nw, n, K):
+    """The method's algorithmic bytes credited to one launch of a kernel kind
+    (SURVEY §8(d)): 16 N^2 B per forward layer-propagation (read v, write
+    v_next) and 24 N^2 B per adjoint one (read a and the checkpoint, write
+    a_prev), complex64; a multi-pass launch advances every channel by one
+    propagation, a fused sweep through all of its gaps."""
+    return {"column_forward": nw * 16 * n * n, "row_forward": nw * 16 * n * n,
+            "column_adjoint": nw * 24 * n * n, "row_adjoint": nw * 24 * n * n,
+            "fused_forward": nw * (K + 1) * 16 * n * n, "fused_adjoint": nw * K * 24 * n * n}.get(kind)
+
+
 def kernel_family(detail, kind):
     """Which kernel of a multi-pass kind ran ('column_bulk' / 'column_plain',
     'row_bulk' / 'row_plain'), from the configuration name dos_describe prints
@@ -391,9 +402,7 @@ def run_ours(a):
     # a and the checkpoint, write a_prev).  A multi-pass launch advances every
     # channel by one propagation and is credited that propagation's bytes; a
     # fused sweep advances every channel through all its gaps.
-    method = {"column_forward": nw * 16 * n * n, "row_forward": nw * 16 * n * n,
-              "column_adjoint": nw * 24 * n * n, "row_adjoint": nw * 24 * n * n,
-              "fused_forward": nw * (K + 1) * 16 * n * n, "fused_adjoint": nw * K * 24 * n * n}.get(dom)
+    method = method_bytes_per_launch(dom, nw, n, K)
     # what the multi-pass design itself must move per launch (every channel once)
     algo = {
         # the last forward column pass writes, and the adjoint's first reads,

@@ -41,3 +41,22 @@ def test_step_bytes_structure():
     assert b3["design"] - b2["design"] == 7 * per_layer
     assert b3["ideal"] == 7 * 4 * 40 * n * n
     assert bench.step_bytes(n, m, 5, F, 14)["design"] == 2 * bench.step_bytes(n, m, 5, F, 7)["design"]
+
+
+def test_roofline_bytes_are_the_methods():
+    """roofline.frac's numerator can be recomputed from SURVEY §8(d) alone:
+    16 N^2 bytes per forward and 24 N^2 per adjoint layer-propagation, times
+    the channels a launch advances; the whole step is (K + 1) * 40 N^2 per
+    channel, which is step_bytes' "ideal"."""
+    mb = bench.method_bytes_per_launch
+    n, K, nw = 200, 5, 4096
+    assert mb("column_forward", nw, n, K) == 16 * n * n * nw == 2_621_440_000
+    assert mb("column_adjoint", nw, n, K) == 24 * n * n * nw
+    assert mb("row_forward", nw, n, K) == mb("column_forward", nw, n, K)
+    assert mb("fused_forward", nw, n, K) + mb("fused_adjoint", nw, n, K) == \
+        nw * (K * 40 + 16) * n * n
+    # forward and adjoint launches of a multi-pass step add up to the step's
+    # algorithmic bytes once the adjoint's missing gap 0 is accounted for
+    per_step = (K + 1) * mb("column_forward", nw, n, K) + K * mb("column_adjoint", nw, n, K)
+    assert per_step + mb("column_adjoint", nw, n, K) == bench.step_bytes(n, 400, K, 50, nw)["ideal"]
+    assert mb("loss", nw, n, K) is None
