@@ -121,9 +121,25 @@ __device__ __forceinline__ void split_store8(const Parts& P, size_t at, const fl
   if (P.k > 2) *reinterpret_cast<uint4*>(P.p[2] + at) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
 }
 
+// Transfer-function values of accumulator row r = (w, kx), columns cb ..
+// cb+31 = sixteen ky (spectrum epilogue): loaded before the accumulator is,
+// so that the table's latency overlaps the tensor-memory load
+__device__ __forceinline__ void spectrum_h(const GemmArgs& g, int r, int cb, float2 (&hv)[16]) {
+  const int m = g.m, w = r / m, kx = r - w * m;
+  const int bx = min(kx, m - kx);
+  const float2* Hw = g.Hq + (size_t)w * g.hs * g.hs;
+  const int ky0 = cb >> 1;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int ky = ky0 + q;
+    hv[q] = ky < m ? __ldg(Hw + (size_t)min(ky, m - ky) * g.hs + bx) : make_float2(0.f, 0.f);
+  }
+}
+
 // accumulator row r, columns cb .. cb+31 (values v) -> the destination of MODE
+// (hv: the spectrum epilogue's transfer-function values, from spectrum_h)
 template <int MODE>
-__device__ __forceinline__ void epilogue(const GemmArgs& g, int r, int cb, const float* v) {
+__device__ __forceinline__ void epilogue(const GemmArgs& g, int r, int cb, const float* v, const float2 (&hv)[16]) {
   if constexpr (MODE == GEMM_OUT_ROWS) {
     const int k = r >> 1, p = r & 1;
     if (g.nj % 8 == 0) {
@@ -147,7 +163,6 @@ __device__ __forceinline__ void epilogue(const GemmArgs& g, int r, int cb, const
     // row r = (w, kx); columns 2ky + {0, 1}: sixteen spectrum values
     const int m = g.m, w = r / m, kx = r - w * m;
     const int bx = min(kx, m - kx);
-    const float2* Hw = g.Hq + (size_t)w * g.hs * g.hs;
     const float* Sw = g.mis.sq ? g.mis.sq + (size_t)w * g.hs * g.hs : nullptr;
     const int ky0 = cb >> 1;  // multiple of 16
     if (ky0 >= m) return;
@@ -157,11 +172,10 @@ __device__ __forceinline__ void epilogue(const GemmArgs& g, int r, int cb, const
       const int ky = ky0 + q;
       float2 val = make_float2(0.f, 0.f);
       if (ky < m) {
-        const size_t qi = (size_t)min(ky, m - ky) * g.hs + bx;
-        float2 hv = Hw[qi];
-        if (Sw) hv = cmul(hv, misalign_factor(g.mis, ky, kx, m, Sw[qi]));
+        float2 h = hv[q];
+        if (Sw) h = cmul(h, misalign_factor(g.mis, ky, kx, m, Sw[(size_t)min(ky, m - ky) * g.hs + bx]));
         const float2 b = make_float2(v[2 * q], v[2 * q + 1]);
-        val = g.adj ? cmulc(b, hv) : cmul(b, hv);
+        val = g.adj ? cmulc(b, h) : cmul(b, h);
       }
       re[q] = val.x;
       im[q] = val.y;
@@ -328,6 +342,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const __grid_consta
       const int r = mt * GTM + q * 32 + lane;  // accumulator row of this thread
 #pragma unroll 1
       for (int c0 = part * (GTN / 4); c0 < (part + 1) * (GTN / 4); c0 += 32) {
+        float2 hv[16];
+        if constexpr (MODE == GEMM_OUT_SPECTRUM) {
+          if (r < g.vrows) spectrum_h(g, r, nt * GTN + c0, hv);
+        }
         uint32_t u[32];
         const uint32_t addr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * GTN + c0);
         asm volatile(
@@ -343,7 +361,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const __grid_consta
           float v[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(u[j]);
-          epilogue<MODE>(g, r, nt * GTN + c0, v);
+          epilogue<MODE>(g, r, nt * GTN + c0, v, hv);
         }
       }
       // this warp is done with the accumulator
