@@ -484,8 +484,8 @@ int build(dos_ctx* x, const dos_config* c) {
                                 x->n_med, x->pitch, x->m, x->hs, x->evan, x->stream),
              "transfer tables");
   DOS_CUDA(dos::launch_arow(x->arow, x->m, x->oa, x->ap, x->stream), "aperture spectrum");
-  const int RP = x->ops->P % 2 == 0 ? x->ops->P + 1 : x->ops->P;
-  DOS_CUDA(dos::launch_twiddles(x->tw, x->ops->P, x->ops->Q, RP, x->m, x->stream), "twiddles");
+  const int TWP = x->ops->P + (x->ops->P & 1);  // even pitch (Line::TWP): pairs are 16-byte loads
+  DOS_CUDA(dos::launch_twiddles(x->tw, x->ops->P, x->ops->Q, TWP, x->m, x->stream), "twiddles");
   if (!gemm) {
     // v1: the aperture's separable spectrum through gap 0, inverse row DFT, crop
     if ((rc = x->alloc(&x->v1, (size_t)x->nw * n2, "input field"))) return rc;

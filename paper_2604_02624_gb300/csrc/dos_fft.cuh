@@ -491,7 +491,8 @@ DOS_HD void dft(float2* x) {
 // M = P*Q points shared by T threads (T | P, T | Q). Thread t holds element
 // t + T*i in r[i], i < M/T, both before and after the transform.
 // z: this line's exchange buffer (ZS float2 in shared memory).
-// tw: shared table tw[q*RP + k1] = exp(-2 pi j q k1 / M) (forward sign).
+// tw: shared table tw[q*TWP + k1] = exp(-2 pi j q k1 / M) (forward sign), 16-byte
+// aligned, read two twiddles at a time.
 // Every thread of the block must call fft() the same number of times (it
 // contains two block-wide barriers).
 template <int P_, int Q_, int T_>
@@ -500,7 +501,11 @@ struct Line {
   static constexpr int QJ = Q / T, PJ = P / T;
   static constexpr int RP = (P % 2 == 0) ? P + 1 : P;  // odd pitch: conflict-free columns
   static constexpr int ZS = Q * RP;
+  // twiddle table pitch: even, so that twiddles k1 and k1 + 1 (k1 even) are
+  // one 16-byte load; TWS entries in all (at most ZS)
+  static constexpr int TWP = P + (P & 1), TWS = Q * TWP;
   static_assert(P % T == 0 && Q % T == 0, "T must divide P and Q");
+  static_assert(TWS <= ZS, "the twiddle table fits the space kernels reserve for it");
   // TR: the exchange matrix stored transposed (entry (q, k1) at k1 * RP + q).
   // For a square line (P = Q = T) step 1 of thread t writes exactly the
   // entries that step 2 of thread t read in the other layout, so two line
@@ -519,13 +524,21 @@ struct Line {
       static_for<0, NZP>([&](auto pp) { a[pp] = r[j + QJ * pp]; });
       dft<P, INV, NZP, P, PK>(a);
       const int q = t + T * j;
-      const float2* twq = tw + q * RP;
+      const float4* twq = reinterpret_cast<const float4*>(tw + q * TWP);  // twiddle pairs
       float2* zq = TR ? z + q : z + q * RP;
       constexpr int ZK = TR ? RP : 1;  // stride of k1
       zq[0] = a[0];
-      static_for<1, P>([&](auto kk) {
-        const float2 w = twq[kk];
-        zq[kk * ZK] = INV ? cmulc(a[kk], w) : cmul(a[kk], w);
+      static_for<0, (P + 1) / 2>([&](auto pp) {
+        constexpr int k0 = 2 * pp, k1 = 2 * pp + 1;
+        const float4 w = twq[pp];
+        if constexpr (k0 > 0) {
+          const float2 w0 = make_float2(w.x, w.y);
+          zq[k0 * ZK] = INV ? cmulc(a[k0], w0) : cmul(a[k0], w0);
+        }
+        if constexpr (k1 < P) {
+          const float2 w1 = make_float2(w.z, w.w);
+          zq[k1 * ZK] = INV ? cmulc(a[k1], w1) : cmul(a[k1], w1);
+        }
       });
     });
   }

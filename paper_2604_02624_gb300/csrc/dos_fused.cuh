@@ -101,7 +101,11 @@ struct Fused {
 
   static size_t smem_bytes(int n) {
     const int R = (n + C - 1) / C;
-    return sizeof(float2) * ((size_t)R * ZS + (size_t)LINES * ZL + ZS);
+    return sizeof(float2) * (tw_offset(R) + ZS);
+  }
+  // the twiddle table starts on a 16-byte boundary (Line reads it in pairs)
+  __host__ __device__ static constexpr size_t tw_offset(int R) {
+    return ((size_t)R * ZS + (size_t)LINES * ZL + 1) & ~(size_t)1;
   }
 
   struct Sm {
@@ -112,13 +116,13 @@ struct Fused {
   };
 
   __device__ static Sm carve(const FusedArgs& a) {
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     Sm s;
     s.R = (a.n + C - 1) / C;
     s.sp = smem;
     s.colz = smem + (size_t)s.R * ZS;
-    s.tw = s.colz + (size_t)LINES * ZL;
-    for (int i = threadIdx.x; i < ZS; i += NT) s.tw[i] = a.tw[i];
+    s.tw = smem + tw_offset(s.R);
+    for (int i = threadIdx.x; i < LF::TWS; i += NT) s.tw[i] = a.tw[i];
     __syncthreads();
     return s;
   }

@@ -106,7 +106,7 @@ cudaError_t launch_htable(float2* Hq, const double* d_lambda, int nw, double z, 
 cudaError_t launch_arow(float2* arow, int m, int offset, int width, cudaStream_t s);
 cudaError_t launch_sqtable(float* sq, const double* d_lambda, int nw, double n_medium, double pitch, int m, int hs,
                            cudaStream_t s);
-cudaError_t launch_twiddles(float2* tw, int P, int Q, int RP, int m, cudaStream_t s);
+cudaError_t launch_twiddles(float2* tw, int P, int Q, int TWP, int m, cudaStream_t s);
 cudaError_t launch_chan(ChanConst* chan, const double* d_lambda, const double* d_nidx,
                         const double* d_kappa, int nw, double n_medium, double h_base,
                         cudaStream_t s);

@@ -77,14 +77,14 @@ struct Pass {
   static constexpr size_t row_smem_bytes(int lines) { return sizeof(float2) * (LF::ZS + (size_t)lines * RZL); }
 
   __device__ static __forceinline__ void load_tw(float2* tw, const float2* g) {
-    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = g[i];
+    for (int i = threadIdx.x; i < LF::TWS; i += blockDim.x) tw[i] = g[i];
     __syncthreads();
   }
 
   // ------------------------------------------------------------ column pass
   template <bool ADJ, bool APERTURE>
   __device__ static void col(const PassArgs& a) {
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     float2* tw = smem;
     const int l = threadIdx.x % COLL;
     const int t = threadIdx.x / COLL;
@@ -136,7 +136,7 @@ struct Pass {
     float2* tw;
   };
   __device__ static __forceinline__ RowCtx row_ctx(const PassArgs& a) {
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(16) float2 smem[];
     RowCtx rc;
     rc.l = threadIdx.x / T;
     rc.t = threadIdx.x % T;

@@ -42,6 +42,9 @@ constexpr unsigned long long kBulkWaitNs = 1000000000ull;  // bounded wait: one 
 constexpr long kBulkSpin = 1L << 30;                        // and an iteration cap behind it
 
 __device__ __forceinline__ uint32_t sh_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// First 16-byte boundary at or after p: the line DFTs read the twiddle table
+// in 16-byte pairs (the layouts reserve one extra float2 for the shift).
+__device__ __forceinline__ float2* tw_align(float2* p) { return p + ((sh_addr(p) >> 3) & 1u); }
 
 __device__ __forceinline__ void bulk_bar_init(uint64_t* b) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(b)));
@@ -167,7 +170,7 @@ struct PassBulk {
   //   stage[2][rows][8] | H tile[10][M/2+2] | exchange[COLL][ZLB] | tw[ZS] | barrier[3] | flag
   static size_t col_smem(int n) {
     return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)HTILE + (size_t)COLL * ZLB +
-                                   LF::ZS) + 3 * sizeof(uint64_t) + sizeof(int);
+                                   LF::ZS + 1) + 3 * sizeof(uint64_t) + sizeof(int);
   }
 
   template <bool ADJ>
@@ -180,7 +183,7 @@ struct PassBulk {
     const int GS = col_group_stride(a.n);
     float2* htile = stage + 2 * (size_t)GS;
     float2* zb = htile + HTILE;
-    float2* tw = zb + (size_t)COLL * ZLB;
+    float2* tw = tw_align(zb + (size_t)COLL * ZLB);
     // [0], [1] spectra of group 0, 1; [2] transfer-table tile
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
     int* h_late = reinterpret_cast<int*>(bar + 3);  // an H wait of this block expired
@@ -199,7 +202,7 @@ struct PassBulk {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(smap)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(hmap)) : "memory");
     }
-    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    for (int i = threadIdx.x; i < LF::TWS; i += blockDim.x) tw[i] = a.tw[i];
     __syncthreads();
     auto tensor_copy = [](float2* dst, const CUtensorMap* map, int x, int y, int zc, uint64_t* b) {
       asm volatile(
@@ -298,7 +301,7 @@ struct PassBulk {
   // ------------------------------------------------------------- row passes
   // dynamic shared memory: stage[RL][SR] | exchange[RL][RZL] | tw[ZS] | barrier
   static size_t row_smem() {
-    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * RZL + LF::ZS) + sizeof(uint64_t);
+    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * RZL + LF::ZS + 1) + sizeof(uint64_t);
   }
 
   // Rows [blockIdx.x * RL, +RL) of the channels of chunk blockIdx.y.
@@ -311,7 +314,7 @@ struct PassBulk {
     extern __shared__ __align__(16) float2 smem[];
     float2* stage = smem;
     float2* zb = stage + (size_t)RL * SR;
-    float2* tw = zb + (size_t)RL * RZL;
+    float2* tw = tw_align(zb + (size_t)RL * RZL);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
     const int l = threadIdx.x / T, t = threadIdx.x % T;
     float2* z = zb + l * RZL;
@@ -324,7 +327,7 @@ struct PassBulk {
     const int w1 = min(a.nw, w0 + a.chunk);
     const uint32_t bytes = (uint32_t)nrows * M * 8u;
     if (threadIdx.x == 0) bulk_bar_init(bar);
-    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    for (int i = threadIdx.x; i < LF::TWS; i += blockDim.x) tw[i] = a.tw[i];
     __syncthreads();
     // thread 0 copies the block's rows of channel w, one bulk copy (M * 8 bytes) per row
     auto fetch = [&](int w) {
@@ -438,7 +441,7 @@ struct PassBulk {
   // of the input-field table v1 (fin) staged by bulk copies.  Needs N even.
   // dynamic shared memory: stage[RL][cks] | exchange[RL][RZL] | tw[ZS] | barrier
   static size_t first_smem(int n) {
-    return sizeof(float2) * ((size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS) + sizeof(uint64_t);
+    return sizeof(float2) * ((size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS + 1) + sizeof(uint64_t);
   }
 
   __device__ static void row_first_staged(const PassArgs& a) {
@@ -446,7 +449,7 @@ struct PassBulk {
     const int cks = ck_stride(a.n);
     float2* stage = smem;
     float2* zb = stage + (size_t)RL * cks;
-    float2* tw = zb + (size_t)RL * RZL;
+    float2* tw = tw_align(zb + (size_t)RL * RZL);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
     const int l = threadIdx.x / T, t = threadIdx.x % T;
     float2* z = zb + l * RZL;
@@ -460,7 +463,7 @@ struct PassBulk {
     const int w1 = min(a.nw, w0 + a.chunk);
     const uint32_t bytes = (uint32_t)nrows * a.n * 8u;
     if (threadIdx.x == 0) bulk_bar_init(bar);
-    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    for (int i = threadIdx.x; i < LF::TWS; i += blockDim.x) tw[i] = a.tw[i];
     __syncthreads();
     auto fetch = [&](int w) {
       if (threadIdx.x != 0) return;
@@ -523,7 +526,7 @@ struct PassBulk {
   // few rows per block three blocks fit on an SM.  Needs N even.
   // dynamic shared memory: stage[RL][SR] | ck[RL][cks] | exchange[RL][RZL] | tw[ZS] | barrier[2]
   static size_t adj_staged_smem(int n) {
-    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS) +
+    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS + 1) +
            2 * sizeof(uint64_t);
   }
 
@@ -534,7 +537,7 @@ struct PassBulk {
     float2* stage = smem;
     float2* ckb = stage + (size_t)RL * SR;
     float2* zb = ckb + (size_t)RL * cks;
-    float2* tw = zb + (size_t)RL * RZL;
+    float2* tw = tw_align(zb + (size_t)RL * RZL);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);  // [0] spectra rows, [1] checkpoint rows
     const int l = threadIdx.x / T, t = threadIdx.x % T;
     float2* z = zb + l * RZL;
@@ -550,7 +553,7 @@ struct PassBulk {
       bulk_bar_init(&bar[0]);
       bulk_bar_init(&bar[1]);
     }
-    for (int i = threadIdx.x; i < LF::ZS; i += blockDim.x) tw[i] = a.tw[i];
+    for (int i = threadIdx.x; i < LF::TWS; i += blockDim.x) tw[i] = a.tw[i];
     __syncthreads();
     // thread 0 copies the block's rows of channel w: spectra (M * 8 bytes a
     // row) into the stage, checkpoint (N * 8 bytes a row) into ck

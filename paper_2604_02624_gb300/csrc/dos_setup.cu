@@ -95,10 +95,10 @@ cudaError_t launch_arow(float2* arow, int m, int offset, int width, cudaStream_t
 }
 
 // tw[q*RP + k] = exp(-2 pi j q k / m) for q < Q, k < P; padding entries zero.
-__global__ void k_twiddles(float2* __restrict__ tw, int P, int Q, int RP, int m) {
+__global__ void k_twiddles(float2* __restrict__ tw, int P, int Q, int TWP, int m) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Q * RP) return;
-  const int q = i / RP, k = i % RP;
+  if (i >= Q * TWP) return;
+  const int q = i / TWP, k = i % TWP;
   float2 v = make_float2(0.f, 0.f);
   if (k < P) {
     const long e = ((long)q * k) % m;
@@ -109,9 +109,9 @@ __global__ void k_twiddles(float2* __restrict__ tw, int P, int Q, int RP, int m)
   tw[i] = v;
 }
 
-cudaError_t launch_twiddles(float2* tw, int P, int Q, int RP, int m, cudaStream_t s) {
-  const int n = Q * RP;
-  k_twiddles<<<(n + 127) / 128, 128, 0, s>>>(tw, P, Q, RP, m);
+cudaError_t launch_twiddles(float2* tw, int P, int Q, int TWP, int m, cudaStream_t s) {
+  const int n = Q * TWP;
+  k_twiddles<<<(n + 127) / 128, 128, 0, s>>>(tw, P, Q, TWP, m);
   return cudaGetLastError();
 }
 

@@ -96,7 +96,7 @@ static void check_line(unsigned seed) {
   for (int q = 0; q < Q; ++q)
     for (int k1 = 0; k1 < P; ++k1) {
       const cd w = w_turn((long)q * k1, M, false);
-      tw[q * LF::RP + k1] = make_float2((float)w.real(), (float)w.imag());
+      tw[q * LF::TWP + k1] = make_float2((float)w.real(), (float)w.imag());
     }
   std::mt19937 rng(seed);
   std::normal_distribution<double> nd;
