@@ -515,9 +515,15 @@ struct Line {
   // Step 1: the Q/T sub-DFTs of length P owned by thread t (q = t + T*j),
   // twiddled and written to the exchange matrix z[q][k1].
   // NZP: leading non-zero inputs of each sub-DFT (zero padding).
-  template <bool INV, int NZP = P, bool PK = false, bool TR = false>
+  // ZR: pitch of the exchange matrix (RP, or an even pitch for kernels whose
+  // lines are laid out so that 16-byte accesses are conflict-free: then a
+  // thread's entries k1, k1 + 1 (k1 even) of a row are one 16-byte store, and
+  // in step 2 of the transposed layout q, q + 1 are one 16-byte load).
+  template <bool INV, int NZP = P, bool PK = false, bool TR = false, int ZR = RP>
   DOS_HD static void step1(const float2 (&r)[E], int t, float2* z, const float2* tw) {
     static_assert(!TR || SQUARE, "the transposed exchange is for square lines");
+    static_assert(ZR >= P && (!TR || ZR >= Q), "the pitch holds a row");
+    constexpr bool V = !TR && ZR % 2 == 0;  // paired row stores
     static_for<0, QJ>([&](auto jj) {
       constexpr int j = jj;
       float2 a[P];
@@ -525,19 +531,25 @@ struct Line {
       dft<P, INV, NZP, P, PK>(a);
       const int q = t + T * j;
       const float4* twq = reinterpret_cast<const float4*>(tw + q * TWP);  // twiddle pairs
-      float2* zq = TR ? z + q : z + q * RP;
-      constexpr int ZK = TR ? RP : 1;  // stride of k1
-      zq[0] = a[0];
+      float2* zq = TR ? z + q : z + q * ZR;
+      constexpr int ZK = TR ? ZR : 1;  // stride of k1
       static_for<0, (P + 1) / 2>([&](auto pp) {
         constexpr int k0 = 2 * pp, k1 = 2 * pp + 1;
         const float4 w = twq[pp];
+        float2 o0 = a[k0], o1;
         if constexpr (k0 > 0) {
           const float2 w0 = make_float2(w.x, w.y);
-          zq[k0 * ZK] = INV ? cmulc(a[k0], w0) : cmul(a[k0], w0);
+          o0 = INV ? cmulc(a[k0], w0) : cmul(a[k0], w0);
         }
         if constexpr (k1 < P) {
           const float2 w1 = make_float2(w.z, w.w);
-          zq[k1 * ZK] = INV ? cmulc(a[k1], w1) : cmul(a[k1], w1);
+          o1 = INV ? cmulc(a[k1], w1) : cmul(a[k1], w1);
+        }
+        if constexpr (V && k1 < P) {
+          *reinterpret_cast<float4*>(zq + k0) = make_float4(o0.x, o0.y, o1.x, o1.y);
+        } else {
+          zq[k0 * ZK] = o0;
+          if constexpr (k1 < P) zq[k1 * ZK] = o1;
         }
       });
     });
@@ -545,13 +557,24 @@ struct Line {
   // Step 2: the P/T sub-DFTs of length Q owned by thread t (k1 = t + T*j),
   // read as columns of z; outputs k1 + P*k2 land in r[j + (P/T)*k2].
   // NOQ: leading outputs of each sub-DFT that are needed (cropping).
-  template <bool INV, int NOQ = Q, bool PK = false, bool TR = false>
+  template <bool INV, int NOQ = Q, bool PK = false, bool TR = false, int ZR = RP>
   DOS_HD static void step2(float2 (&r)[E], int t, const float2* z) {
+    constexpr bool V = TR && ZR % 2 == 0;  // paired row loads
     static_for<0, PJ>([&](auto jj) {
       constexpr int j = jj;
       const int k1 = t + T * j;
       float2 b[Q];
-      static_for<0, Q>([&](auto qq) { b[qq] = TR ? z[k1 * RP + qq] : z[qq * RP + k1]; });
+      if constexpr (V) {
+        const float4* zr = reinterpret_cast<const float4*>(z + k1 * ZR);
+        static_for<0, Q / 2>([&](auto qq) {
+          const float4 v = zr[qq];
+          b[2 * qq] = make_float2(v.x, v.y);
+          b[2 * qq + 1] = make_float2(v.z, v.w);
+        });
+        if constexpr (Q % 2 == 1) b[Q - 1] = z[k1 * ZR + Q - 1];
+      } else {
+        static_for<0, Q>([&](auto qq) { b[qq] = TR ? z[k1 * ZR + qq] : z[qq * ZR + k1]; });
+      }
       dft<Q, INV, Q, NOQ, PK>(b);
       static_for<0, NOQ>([&](auto k2) { r[j + PJ * k2] = b[k2]; });
     });

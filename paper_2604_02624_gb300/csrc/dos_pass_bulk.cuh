@@ -142,6 +142,7 @@ struct PassBulk {
   static constexpr bool STAGE_H = M <= 400;
   static_assert(!STAGE_H || HP <= 256, "a staged H tile row is one box row (at most 256 entries)");
   static constexpr int HTILE = STAGE_H ? HW * HP : 0;  // float2 of the H tile in shared memory
+  static_assert(HTILE % 2 == 0, "the exchange buffers after the tile start 16-byte aligned");
   // group stride in the stage (float2): whole 128-byte lines for any row count
   __host__ __device__ static int col_group_stride(int rows) { return (rows + 1) / 2 * 2 * GW; }
   // The two groups of an item share only the H tile: a group's 8 lines are
@@ -152,10 +153,16 @@ struct PassBulk {
   // warp size (M = 200) the groups share warps and the block barrier serves.
   static constexpr int GT = GW * T;                    // threads of a group
   static constexpr bool GROUP_BARS = GT % 32 == 0;
-  // exchange-matrix stride between the lines (float2): at least ZS and 2 mod
-  // 16, which with a group warp's 8 lines x 4 consecutive element owners puts
-  // every exchange write and read (both layouts) on distinct bank pairs
-  static constexpr int ZLB = LF::ZS + ((2 - LF::ZS % 16) + 16) % 16;
+  // Exchange matrices of the column lines: even pitch ZX (row entries k1,
+  // k1 + 1 are one 16-byte access), stride ZLB between the lines at least
+  // Q ZX and 2 mod 16.  A group warp holds 8 lines x 4 consecutive element
+  // owners; its 8-byte accesses (the column side of either layout) then fall
+  // on distinct bank pairs in each half-warp (8 lines x 2 owners) and its
+  // 16-byte ones (the row side) on distinct bank quads in each quarter-warp
+  // (8 lines, one owner).
+  static constexpr int ZX = LF::TWP, ZSX = LF::Q * ZX;
+  static constexpr int ZLB = ZSX + ((2 - ZSX % 16) + 16) % 16;
+  static_assert(ZX % 2 == 0 && ZLB % 16 == 2, "16-byte aligned rows, conflict-free line stride");
   __device__ static __forceinline__ void group_sync(int g) {
     if constexpr (GROUP_BARS) {
       // g is uniform over a warp; immediate barrier ids keep the count of
@@ -248,10 +255,10 @@ struct PassBulk {
         const int row = t + T * i;
         r[i] = (i < EF && row >= a.in_r0 && row < a.in_r1) ? sg[row * GW] : czero();
       }
-      LF::template step1<false, NZF, PKC>(r, t, z, tw);
+      LF::template step1<false, NZF, PKC, false, ZX>(r, t, z, tw);
       group_sync(g);  // the group is past its stage reads: its next rows may land there
       if (leader && it + (int)gridDim.x < items) fetch_s(it + gridDim.x, g);
-      LF::template step2<false, LF::Q, PKC>(r, t, z);
+      LF::template step2<false, LF::Q, PKC, false, ZX>(r, t, z);
       // square lines: the inverse DFT below writes the exchange matrix in
       // the transposed layout, i.e. only what this thread just read
       if constexpr (!LF::SQUARE) group_sync(g);
@@ -275,11 +282,11 @@ struct PassBulk {
         }
         r[i] = ADJ ? cmulc(r[i], h) : cmul(r[i], h);
       }
-      LF::template step1<true, LF::P, PKC, LF::SQUARE>(r, t, z, tw);
+      LF::template step1<true, LF::P, PKC, LF::SQUARE, ZX>(r, t, z, tw);
       group_sync(g);
       // no trailing barrier: the exchange buffer is next written after the
       // barrier at the top of the next item
-      LF::template step2<true, NOI, PKC, LF::SQUARE>(r, t, z);
+      LF::template step2<true, NOI, PKC, LF::SQUARE, ZX>(r, t, z);
       float2* dst = a.S + (size_t)w * a.n * M + cc;
 #pragma unroll
       for (int i = 0; i < E; ++i) {

@@ -88,11 +88,12 @@ static void check_sizes() {
 }
 
 // the cooperative M = P Q point line DFT of T threads (Line<P, Q, T>)
-template <int P, int Q, int T, bool INV, int NZP, int NOQ, bool TR>
+template <int P, int Q, int T, bool INV, int NZP, int NOQ, bool TR, int ZR = -1>
 static void check_line(unsigned seed) {
   using LF = Line<P, Q, T>;
   constexpr int M = P * Q, E = M / T;
-  std::vector<float2> tw(LF::ZS), z(LF::ZS);
+  constexpr int ZP = ZR < 0 ? LF::RP : ZR;  // exchange pitch
+  std::vector<float2> tw(LF::ZS), z((size_t)(P > Q ? P : Q) * ZP, make_float2(NAN, NAN));
   for (int q = 0; q < Q; ++q)
     for (int k1 = 0; k1 < P; ++k1) {
       const cd w = w_turn((long)q * k1, M, false);
@@ -115,11 +116,11 @@ static void check_line(unsigned seed) {
     }
   for (int t = 0; t < T; ++t) {
     float2(&rt)[E] = *reinterpret_cast<float2(*)[E]>(r[t].data());
-    LF::template step1<INV, NZP, false, TR>(rt, t, z.data(), tw.data());
+    LF::template step1<INV, NZP, false, TR, ZP>(rt, t, z.data(), tw.data());
   }
   for (int t = 0; t < T; ++t) {
     float2(&rt)[E] = *reinterpret_cast<float2(*)[E]>(r[t].data());
-    LF::template step2<INV, NOQ, false, TR>(rt, t, z.data());
+    LF::template step2<INV, NOQ, false, TR, ZP>(rt, t, z.data());
   }
   // outputs k = k1 + P k2 with k2 < NOQ, i.e. k < P NOQ, are produced
   double num = 0.0, den = 0.0;
@@ -136,24 +137,30 @@ static void check_line(unsigned seed) {
       den += std::norm(ref);
     }
   char what[128];
-  std::snprintf(what, sizeof what, "line %dx%d T=%d inv=%d nzp=%d noq=%d tr=%d", P, Q, T, (int)INV, NZP, NOQ,
-                (int)TR);
+  std::snprintf(what, sizeof what, "line %dx%d T=%d inv=%d nzp=%d noq=%d tr=%d pitch=%d", P, Q, T, (int)INV, NZP,
+                NOQ, (int)TR, ZP);
   record(what, std::sqrt(num / den), finite);
 }
 
 // every use the passes make of a line shape: forward DFT of a full or a
 // half-zero field, inverse DFT to a full or a cropped field, both layouts of
-// the exchange on square lines
+// the exchange on square lines, with the odd pitch and with the even one
+// (paired 16-byte accesses)
 template <int P, int Q, int T>
 static void check_shape() {
   constexpr bool SQ = Line<P, Q, T>::SQUARE;
+  constexpr int ZE = Line<P, Q, T>::TWP;
   check_line<P, Q, T, false, P, Q, false>(P * 100 + 1);
   check_line<P, Q, T, false, P / 2, Q, false>(P * 100 + 2);
   check_line<P, Q, T, true, P, Q, false>(P * 100 + 3);
   check_line<P, Q, T, true, P, Q / 2, false>(P * 100 + 4);
+  check_line<P, Q, T, false, P / 2, Q, false, ZE>(P * 100 + 7);
+  check_line<P, Q, T, true, P, Q / 2, false, ZE>(P * 100 + 8);
   if constexpr (SQ) {
     check_line<P, Q, T, false, P / 2, Q, true>(P * 100 + 5);
     check_line<P, Q, T, true, P, Q / 2, true>(P * 100 + 6);
+    check_line<P, Q, T, false, P / 2, Q, true, ZE>(P * 100 + 9);
+    check_line<P, Q, T, true, P, Q / 2, true, ZE>(P * 100 + 10);
   }
 }
 
