@@ -134,17 +134,40 @@ struct PassBulk {
   static constexpr int HW = GW + 2;                   // |kx| values per H tile (c0 .. c0+9)
   static constexpr int HP = M / 2 + 2;                // quadrant pitch (rows and columns)
   static_assert(GW == 8, "column groups of 8");
-  // The H tile is staged where the block still fits twice on an SM with it
-  // and a table row fits one box (M <= 400: 100.8 KB at N = 200); at M = 512
-  // the exchange buffers alone take 70 KB, so the tile stays out and each
-  // thread reads its H values from the table (L2-resident per channel) at the
-  // multiply: 107 KB, two blocks per SM.
+  // The H tile is staged in a region of its own where the block still fits
+  // twice on an SM with it and a table row fits one box (M <= 400: 96.8 KB
+  // at N = 200).  At M = 512 the exchange buffers alone take 66 KB and a
+  // separate tile would leave one block per SM, so each group stages its own
+  // 8 rows of the table in its stage slot instead (SLOT_H): the copy is
+  // issued once the group's input rows are in registers (at the barrier
+  // inside the forward DFT) and waited for just before the H multiply, and
+  // the next item's input rows are fetched at the barrier inside the inverse
+  // DFT, when the group is past its H reads.  A table row of M/2 + 2 > 256
+  // entries is then two boxes of HB entries, at x = 0 and x = HP - HB.
   static constexpr bool STAGE_H = M <= 400;
+  static constexpr bool SLOT_H = !STAGE_H;
   static_assert(!STAGE_H || HP <= 256, "a staged H tile row is one box row (at most 256 entries)");
   static constexpr int HTILE = STAGE_H ? HW * HP : 0;  // float2 of the H tile in shared memory
   static_assert(HTILE % 2 == 0, "the exchange buffers after the tile start 16-byte aligned");
-  // group stride in the stage (float2): whole 128-byte lines for any row count
-  __host__ __device__ static int col_group_stride(int rows) { return (rows + 1) / 2 * 2 * GW; }
+  static constexpr int HB = (HP / 2 + 1) / 2 * 2;         // SLOT_H box width: even (16-byte box rows)
+  static constexpr int HSLOT = SLOT_H ? 2 * GW * HB : 0;  // float2 of a group's H tile: [2 boxes][8][HB]
+  static_assert(!SLOT_H || (HB <= 256 && (HP - HB) % 2 == 0 && 2 * HB >= HP),
+                "two 16-byte aligned boxes cover a table row");
+  // every register's |ky| range (over the T element owners) lies in one box
+  static constexpr bool slot_boxes_cover() {
+    for (int i = 0; i < E; ++i) {
+      const int lo = i < E / 2 ? T * i : M - T * i - T + 1, hi = i < E / 2 ? T * i + T - 1 : M - T * i;
+      if (!(hi < HB || lo >= HP - HB)) return false;
+    }
+    return true;
+  }
+  static_assert(!SLOT_H || slot_boxes_cover(), "each register's H values come from one box");
+  // group stride in the stage (float2): whole 128-byte lines for any row
+  // count, and room for the group's H tile under SLOT_H
+  __host__ __device__ static int col_group_stride(int rows) {
+    const int s = (rows + 1) / 2 * 2 * GW, h = (HSLOT + 15) / 16 * 16;
+    return s > h ? s : h;
+  }
   // The two groups of an item share only the H tile: a group's 8 lines are
   // held by warps of their own (thread = group g, line lc, element owner t:
   // g = tid / GT, lc = tid % 8, t = (tid % GT) / 8), so the exchanges inside
@@ -174,10 +197,10 @@ struct PassBulk {
     }
   }
   // dynamic shared memory (from a 128-byte aligned base):
-  //   stage[2][rows][8] | H tile[10][M/2+2] | exchange[COLL][ZLB] | tw[ZS] | barrier[3] | flag
+  //   stage[2][rows][8] | H tile[10][M/2+2] | exchange[COLL][ZLB] | tw[ZS] | barrier[4] | flag
   static size_t col_smem(int n) {
     return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)HTILE + (size_t)COLL * ZLB +
-                                   LF::ZS + 1) + 3 * sizeof(uint64_t) + sizeof(int);
+                                   LF::ZS + 1) + 4 * sizeof(uint64_t) + sizeof(int);
   }
 
   template <bool ADJ>
@@ -191,9 +214,10 @@ struct PassBulk {
     float2* htile = stage + 2 * (size_t)GS;
     float2* zb = htile + HTILE;
     float2* tw = tw_align(zb + (size_t)COLL * ZLB);
-    // [0], [1] spectra of group 0, 1; [2] transfer-table tile
+    // [0], [1] spectra of group 0, 1; [2] transfer-table tile (STAGE_H), or
+    // [2], [3] the H tiles of group 0, 1 (SLOT_H)
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
-    int* h_late = reinterpret_cast<int*>(bar + 3);  // an H wait of this block expired
+    int* h_late = reinterpret_cast<int*>(bar + 4);  // an H wait of this block expired
     const int g = threadIdx.x / GT, lc = threadIdx.x % GW, t = (threadIdx.x % GT) / GW;
     const bool leader = threadIdx.x % GT == 0;  // issues the group's copies
     float2* z = zb + (g * GW + lc) * ZLB;
@@ -201,10 +225,12 @@ struct PassBulk {
     const int items = a.nw * npairs;
     const uint32_t sbytes = GW * 8u * (uint32_t)(a.in_r1 - a.in_r0);
     constexpr uint32_t hbytes = (uint32_t)HW * HP * 8u;
+    constexpr uint32_t hsbytes = (uint32_t)HSLOT * 8u;
     if (threadIdx.x == 0) {
       bulk_bar_init(&bar[0]);
       bulk_bar_init(&bar[1]);
       bulk_bar_init(&bar[2]);
+      bulk_bar_init(&bar[3]);
       *h_late = 0;
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(smap)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(hmap)) : "memory");
@@ -234,6 +260,17 @@ struct PassBulk {
       const int w = it / npairs, c0 = GW * (it % npairs);
       tensor_copy(htile, hmap, 0, c0, a.hmap_z0 + w, &bar[2]);
     };
+    // the 8 table rows |kx| = c0 + gg .. c0 + gg + 7 that group gg of item it
+    // reads, into its stage slot (its leader; SLOT_H)
+    auto fetch_hs = [&](int it, int gg) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_expect(&bar[2 + gg], hsbytes);
+      if (a.stall == 1) return;
+      const int w = it / npairs, c0 = GW * (it % npairs);
+      float2* dst = stage + gg * GS;
+      tensor_copy(dst, hmap, 0, c0 + gg, a.hmap_z0 + w, &bar[2 + gg]);
+      tensor_copy(dst + GW * HB, hmap, HP - HB, c0 + gg, a.hmap_z0 + w, &bar[2 + gg]);
+    };
     bool ok = true;
     int k = 0;
     if ((int)blockIdx.x < items && leader) fetch_s(blockIdx.x, g);
@@ -256,8 +293,12 @@ struct PassBulk {
         r[i] = (i < EF && row >= a.in_r0 && row < a.in_r1) ? sg[row * GW] : czero();
       }
       LF::template step1<false, NZF, PKC, false, ZX>(r, t, z, tw);
-      group_sync(g);  // the group is past its stage reads: its next rows may land there
-      if (leader && it + (int)gridDim.x < items) fetch_s(it + gridDim.x, g);
+      group_sync(g);  // the group is past its stage reads: its next rows (or its H tile) may land there
+      if constexpr (SLOT_H) {
+        if (leader) fetch_hs(it, g);
+      } else {
+        if (leader && it + (int)gridDim.x < items) fetch_s(it + gridDim.x, g);
+      }
       LF::template step2<false, LF::Q, PKC, false, ZX>(r, t, z);
       // square lines: the inverse DFT below writes the exchange matrix in
       // the transposed layout, i.e. only what this thread just read
@@ -265,17 +306,25 @@ struct PassBulk {
       // H(|ky|, |kx|) from the tile: |ky| = k below M/2 and M - k above, both
       // affine in i at compile time
       if (STAGE_H && !bulk_wait(&bar[2], (uint32_t)(k & 1))) *h_late = 1;
-      // tile[hc][|ky|] (pitch HP), or the table's H(|ky|, c0 + hc) (pitch hs)
-      // when the tile is not staged
-      const float2* hlo = STAGE_H ? htile + hc * HP + t : a.Hq + (size_t)w * a.hs * a.hs + (size_t)t * a.hs + c0 + hc;
-      const float2* hhi = STAGE_H ? htile + hc * HP + (M - t)
-                                  : a.Hq + (size_t)w * a.hs * a.hs + (size_t)(M - t) * a.hs + c0 + hc;
+      if (SLOT_H && !bulk_wait(&bar[2 + g], (uint32_t)(k & 1))) *h_late = 1;
+      // STAGE_H: tile[hc][|ky|] (pitch HP).  SLOT_H: box b of the group's
+      // tile, [hc - g][|ky| - b (HP - HB)] (pitch HB); box 0 holds |ky| < HB,
+      // box 1 |ky| >= HP - HB, and which one a register's |ky| range lies in
+      // is known at compile time.
+      const float2* hlo = STAGE_H ? htile + hc * HP + t : stage + (size_t)g * GS + (hc - g) * HB + t;
+      const float2* hhi = STAGE_H ? htile + hc * HP + (M - t) : stage + (size_t)g * GS + (hc - g) * HB + (M - t);
       const float* Sw = a.mis.sq ? a.mis.sq + (size_t)w * a.hs * a.hs : nullptr;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
         float2 h;
-        if constexpr (STAGE_H) h = i < E / 2 ? hlo[T * i] : hhi[-T * i];
-        else h = i < E / 2 ? __ldg(hlo + (size_t)T * i * a.hs) : __ldg(hhi - (size_t)T * i * a.hs);
+        if constexpr (STAGE_H) {
+          h = i < E / 2 ? hlo[T * i] : hhi[-T * i];
+        } else {
+          // |ky| in [T i, T i + T - 1] (i < E/2) or [M - T i - T + 1, M - T i]
+          constexpr int B1 = GW * HB - (HP - HB);  // offset of box 1, less its first |ky|
+          if (i < E / 2) h = T * i + T - 1 < HB ? hlo[T * i] : hlo[B1 + T * i];
+          else h = M - T * i < HB ? hhi[-T * i] : hhi[B1 - T * i];
+        }
         if (Sw) {
           const int kk = t + T * i;
           h = cmul(h, misalign_factor(a.mis, kk, cc, M, Sw[(size_t)min(kk, M - kk) * a.hs + c0 + hc]));
@@ -284,6 +333,8 @@ struct PassBulk {
       }
       LF::template step1<true, LF::P, PKC, LF::SQUARE, ZX>(r, t, z, tw);
       group_sync(g);
+      // SLOT_H: the group is past its H reads: its next rows may land in the slot
+      if (SLOT_H && leader && it + (int)gridDim.x < items) fetch_s(it + gridDim.x, g);
       // no trailing barrier: the exchange buffer is next written after the
       // barrier at the top of the next item
       LF::template step2<true, NOI, PKC, LF::SQUARE, ZX>(r, t, z);
@@ -301,6 +352,10 @@ struct PassBulk {
       (void)bulk_wait(&bar[0], (uint32_t)(k & 1));
       (void)bulk_wait(&bar[1], (uint32_t)(k & 1));
       if (STAGE_H && *h_late) (void)bulk_wait(&bar[2], (uint32_t)((k - 1) & 1));
+      if (SLOT_H && *h_late) {
+        (void)bulk_wait(&bar[2], (uint32_t)((k - 1) & 1));
+        (void)bulk_wait(&bar[3], (uint32_t)((k - 1) & 1));
+      }
       atomicExch(a.err, 1);
     }
   }
@@ -723,9 +778,8 @@ struct PassBulkLaunch {
     auto kern = adj ? k_col_bulk<LF, RL, H, true> : k_col_bulk<LF, RL, H, false>;
     cudaError_t e = slots(kern, PB::CT, sm, &n_slots);
     if (e != cudaSuccess) return e;
-    // (without a staged tile the H map is not read: the spectra map stands in)
     kern<<<std::min(items, n_slots), PB::CT, sm, s>>>(a, *static_cast<const CUtensorMap*>(a.tmap),
-                                                     *static_cast<const CUtensorMap*>(a.hmap ? a.hmap : a.tmap));
+                                                     *static_cast<const CUtensorMap*>(a.hmap));
     return cudaGetLastError();
   }
   // The tensor copies need maps whose boxes hold the input rows (at most 256)
@@ -733,7 +787,7 @@ struct PassBulkLaunch {
   // groups); otherwise the plain kernel runs.
   static cudaError_t col(const PassArgs& a, bool adj, cudaStream_t s) {
     const size_t sm = PB::col_smem(a.n);
-    if (!a.tmap || (PB::STAGE_H && !a.hmap) || a.tmap_rows != a.in_r1 - a.in_r0 || a.tmap_rows > 256 ||
+    if (!a.tmap || !a.hmap || a.tmap_rows != a.in_r1 - a.in_r0 || a.tmap_rows > 256 ||
         LF::M % 16 != 0 ||
         sm > 227 * 1024)
       return PassLaunch<LF>::col(a, adj, false, s);
@@ -790,7 +844,8 @@ const PassOps* pass_ops_table() {
                             &PL::row_out, &PL::row_seed,  &PL::row_adj,  &PL::row_in,
                             &PL::row_back, &PL::row_first, &PBL::col, &PBL::row_fwd,
                             &PBL::row_adj, &PBL::row_first, PassBulk<LF, RL>::GW,
-                            PassBulk<LF, RL>::STAGE_H ? PassBulk<LF, RL>::HP : 0, PassBulk<LF, RL>::HW};
+                            PassBulk<LF, RL>::STAGE_H ? PassBulk<LF, RL>::HP : PassBulk<LF, RL>::HB,
+                            PassBulk<LF, RL>::STAGE_H ? PassBulk<LF, RL>::HW : PassBulk<LF, RL>::GW};
   return &o;
 }
 
