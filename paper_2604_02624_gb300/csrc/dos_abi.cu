@@ -459,7 +459,7 @@ int build(dos_ctx* x, const dos_config* c) {
   if ((rc = x->alloc(&x->Hq, (size_t)x->n_slots * x->nw * x->hs * x->hs, "transfer tables"))) return rc;
   if ((rc = make_spectra_map(x))) return rc;
   if ((rc = x->alloc(&x->arow, (size_t)x->m, "aperture spectrum"))) return rc;
-  if ((rc = x->alloc(&x->tw, (size_t)x->ops->Q * (x->ops->P + 1), "twiddles"))) return rc;
+  if ((rc = x->alloc(&x->tw, (size_t)x->ops->Q * dos::twiddle_pitch(x->ops->P), "twiddles"))) return rc;
   if ((rc = x->alloc(&x->chan, (size_t)x->nw, "channel constants"))) return rc;
   if ((rc = x->alloc(&x->partial, partial_count, "gradient partials"))) return rc;
   if ((rc = x->alloc(&x->h_fwd, (size_t)x->K * n2, "saved thickness"))) return rc;
@@ -484,8 +484,8 @@ int build(dos_ctx* x, const dos_config* c) {
                                 x->n_med, x->pitch, x->m, x->hs, x->evan, x->stream),
              "transfer tables");
   DOS_CUDA(dos::launch_arow(x->arow, x->m, x->oa, x->ap, x->stream), "aperture spectrum");
-  const int TWP = x->ops->P + (x->ops->P & 1);  // even pitch (Line::TWP): pairs are 16-byte loads
-  DOS_CUDA(dos::launch_twiddles(x->tw, x->ops->P, x->ops->Q, TWP, x->m, x->stream), "twiddles");
+  DOS_CUDA(dos::launch_twiddles(x->tw, x->ops->P, x->ops->Q, dos::twiddle_pitch(x->ops->P), x->m, x->stream),
+           "twiddles");
   if (!gemm) {
     // v1: the aperture's separable spectrum through gap 0, inverse row DFT, crop
     if ((rc = x->alloc(&x->v1, (size_t)x->nw * n2, "input field"))) return rc;

@@ -495,17 +495,22 @@ DOS_HD void dft(float2* x) {
 // aligned, read two twiddles at a time.
 // Every thread of the block must call fft() the same number of times (it
 // contains two block-wide barriers).
+// Pitch of the twiddle table rows: the smallest TWP >= p with TWP = 2 mod 4.
+// Even, so that twiddles k1, k1 + 1 (k1 even) are one 16-byte load; and a
+// row is an odd number of 16-byte units, so the loads of 8 consecutive rows
+// (one quarter-warp of consecutive threads) fall on distinct bank quads.
+constexpr int twiddle_pitch(int p) { return p + ((2 - p % 4) + 4) % 4; }
+
 template <int P_, int Q_, int T_>
 struct Line {
   static constexpr int P = P_, Q = Q_, T = T_, M = P * Q, E = M / T;
   static constexpr int QJ = Q / T, PJ = P / T;
   static constexpr int RP = (P % 2 == 0) ? P + 1 : P;  // odd pitch: conflict-free columns
   static constexpr int ZS = Q * RP;
-  // twiddle table pitch: even, so that twiddles k1 and k1 + 1 (k1 even) are
-  // one 16-byte load; TWS entries in all (at most ZS)
-  static constexpr int TWP = P + (P & 1), TWS = Q * TWP;
+  // twiddle table [Q][TWP] (twiddle_pitch): TWS entries, the space kernels
+  // reserve for it in shared memory
+  static constexpr int TWP = twiddle_pitch(P), TWS = Q * TWP;
   static_assert(P % T == 0 && Q % T == 0, "T must divide P and Q");
-  static_assert(TWS <= ZS, "the twiddle table fits the space kernels reserve for it");
   // TR: the exchange matrix stored transposed (entry (q, k1) at k1 * RP + q).
   // For a square line (P = Q = T) step 1 of thread t writes exactly the
   // entries that step 2 of thread t read in the other layout, so two line

@@ -101,7 +101,7 @@ struct Fused {
 
   static size_t smem_bytes(int n) {
     const int R = (n + C - 1) / C;
-    return sizeof(float2) * (tw_offset(R) + ZS);
+    return sizeof(float2) * (tw_offset(R) + LF::TWS);
   }
   // the twiddle table starts on a 16-byte boundary (Line reads it in pairs)
   __host__ __device__ static constexpr size_t tw_offset(int R) {
@@ -111,7 +111,7 @@ struct Fused {
   struct Sm {
     float2* sp;    // [R][ZS] this CTA's rows of the spectrum plane (also their DFT exchange)
     float2* colz;  // [LINES][ZL] exchange buffers of the column lines
-    float2* tw;    // [ZS]
+    float2* tw;    // [TWS]
     int R;
   };
 

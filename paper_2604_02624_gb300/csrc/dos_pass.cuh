@@ -73,8 +73,8 @@ struct Pass {
   // column pass: line = tid % COLL, an odd stride keeps the lines apart
   static constexpr int ZL = LF::ZS + 1;
   static constexpr int RZL = row_line_stride(M, LF::ZS);
-  static constexpr size_t smem_bytes(int lines) { return sizeof(float2) * (LF::ZS + (size_t)lines * ZL); }
-  static constexpr size_t row_smem_bytes(int lines) { return sizeof(float2) * (LF::ZS + (size_t)lines * RZL); }
+  static constexpr size_t smem_bytes(int lines) { return sizeof(float2) * (LF::TWS + (size_t)lines * ZL); }
+  static constexpr size_t row_smem_bytes(int lines) { return sizeof(float2) * (LF::TWS + (size_t)lines * RZL); }
 
   __device__ static __forceinline__ void load_tw(float2* tw, const float2* g) {
     for (int i = threadIdx.x; i < LF::TWS; i += blockDim.x) tw[i] = g[i];
@@ -88,7 +88,7 @@ struct Pass {
     float2* tw = smem;
     const int l = threadIdx.x % COLL;
     const int t = threadIdx.x / COLL;
-    float2* z = smem + LF::ZS + l * ZL;
+    float2* z = smem + LF::TWS + l * ZL;
     load_tw(tw, a.tw);
     const int w = blockIdx.y;
     const int c = blockIdx.x * COLL + l;
@@ -141,7 +141,7 @@ struct Pass {
     rc.l = threadIdx.x / T;
     rc.t = threadIdx.x % T;
     rc.tw = smem;
-    rc.z = smem + LF::ZS + rc.l * RZL;
+    rc.z = smem + LF::TWS + rc.l * RZL;
     load_tw(rc.tw, a.tw);
     return rc;
   }

@@ -183,7 +183,7 @@ struct PassBulk {
   // on distinct bank pairs in each half-warp (8 lines x 2 owners) and its
   // 16-byte ones (the row side) on distinct bank quads in each quarter-warp
   // (8 lines, one owner).
-  static constexpr int ZX = LF::TWP, ZSX = LF::Q * ZX;
+  static constexpr int ZX = LF::P + (LF::P & 1), ZSX = LF::Q * ZX;
   static constexpr int ZLB = ZSX + ((2 - ZSX % 16) + 16) % 16;
   static_assert(ZX % 2 == 0 && ZLB % 16 == 2, "16-byte aligned rows, conflict-free line stride");
   __device__ static __forceinline__ void group_sync(int g) {
@@ -197,10 +197,10 @@ struct PassBulk {
     }
   }
   // dynamic shared memory (from a 128-byte aligned base):
-  //   stage[2][rows][8] | H tile[10][M/2+2] | exchange[COLL][ZLB] | tw[ZS] | barrier[4] | flag
+  //   stage[2][rows][8] | H tile[10][M/2+2] | exchange[COLL][ZLB] | tw[TWS] | barrier[4] | flag
   static size_t col_smem(int n) {
     return 128 + sizeof(float2) * (2 * (size_t)col_group_stride(n) + (size_t)HTILE + (size_t)COLL * ZLB +
-                                   LF::ZS + 1) + 4 * sizeof(uint64_t) + sizeof(int);
+                                   LF::TWS + 1) + 4 * sizeof(uint64_t) + sizeof(int);
   }
 
   template <bool ADJ>
@@ -216,7 +216,7 @@ struct PassBulk {
     float2* tw = tw_align(zb + (size_t)COLL * ZLB);
     // [0], [1] spectra of group 0, 1; [2] transfer-table tile (STAGE_H), or
     // [2], [3] the H tiles of group 0, 1 (SLOT_H)
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::TWS);
     int* h_late = reinterpret_cast<int*>(bar + 4);  // an H wait of this block expired
     const int g = threadIdx.x / GT, lc = threadIdx.x % GW, t = (threadIdx.x % GT) / GW;
     const bool leader = threadIdx.x % GT == 0;  // issues the group's copies
@@ -361,9 +361,9 @@ struct PassBulk {
   }
 
   // ------------------------------------------------------------- row passes
-  // dynamic shared memory: stage[RL][SR] | exchange[RL][RZL] | tw[ZS] | barrier
+  // dynamic shared memory: stage[RL][SR] | exchange[RL][RZL] | tw[TWS] | barrier
   static size_t row_smem() {
-    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * RZL + LF::ZS + 1) + sizeof(uint64_t);
+    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * RZL + LF::TWS + 1) + sizeof(uint64_t);
   }
 
   // Rows [blockIdx.x * RL, +RL) of the channels of chunk blockIdx.y.
@@ -377,7 +377,7 @@ struct PassBulk {
     float2* stage = smem;
     float2* zb = stage + (size_t)RL * SR;
     float2* tw = tw_align(zb + (size_t)RL * RZL);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::TWS);
     const int l = threadIdx.x / T, t = threadIdx.x % T;
     float2* z = zb + l * RZL;
     const int r0 = blockIdx.x * RL;
@@ -501,9 +501,9 @@ struct PassBulk {
   // -------------------------------------------------------- first row pass
   // t(h) * v1 -> pad -> DFT (as Pass::row_first) with the next channel's rows
   // of the input-field table v1 (fin) staged by bulk copies.  Needs N even.
-  // dynamic shared memory: stage[RL][cks] | exchange[RL][RZL] | tw[ZS] | barrier
+  // dynamic shared memory: stage[RL][cks] | exchange[RL][RZL] | tw[TWS] | barrier
   static size_t first_smem(int n) {
-    return sizeof(float2) * ((size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS + 1) + sizeof(uint64_t);
+    return sizeof(float2) * ((size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::TWS + 1) + sizeof(uint64_t);
   }
 
   __device__ static void row_first_staged(const PassArgs& a) {
@@ -512,7 +512,7 @@ struct PassBulk {
     float2* stage = smem;
     float2* zb = stage + (size_t)RL * cks;
     float2* tw = tw_align(zb + (size_t)RL * RZL);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::TWS);
     const int l = threadIdx.x / T, t = threadIdx.x % T;
     float2* z = zb + l * RZL;
     const int r0 = blockIdx.x * RL;
@@ -586,9 +586,9 @@ struct PassBulk {
   // (read after the inverse DFT; the next channel's copy is issued as soon as
   // every thread is past them, at the barrier inside the forward DFT).  With
   // few rows per block three blocks fit on an SM.  Needs N even.
-  // dynamic shared memory: stage[RL][SR] | ck[RL][cks] | exchange[RL][RZL] | tw[ZS] | barrier[2]
+  // dynamic shared memory: stage[RL][SR] | ck[RL][cks] | exchange[RL][RZL] | tw[TWS] | barrier[2]
   static size_t adj_staged_smem(int n) {
-    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::ZS + 1) +
+    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::TWS + 1) +
            2 * sizeof(uint64_t);
   }
 
@@ -600,7 +600,7 @@ struct PassBulk {
     float2* ckb = stage + (size_t)RL * SR;
     float2* zb = ckb + (size_t)RL * cks;
     float2* tw = tw_align(zb + (size_t)RL * RZL);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::ZS);  // [0] spectra rows, [1] checkpoint rows
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::TWS);  // [0] spectra rows, [1] checkpoint rows
     const int l = threadIdx.x / T, t = threadIdx.x % T;
     float2* z = zb + l * RZL;
     const int r0 = blockIdx.x * RL;

@@ -93,7 +93,7 @@ static void check_line(unsigned seed) {
   using LF = Line<P, Q, T>;
   constexpr int M = P * Q, E = M / T;
   constexpr int ZP = ZR < 0 ? LF::RP : ZR;  // exchange pitch
-  std::vector<float2> tw(LF::ZS), z((size_t)(P > Q ? P : Q) * ZP, make_float2(NAN, NAN));
+  std::vector<float2> tw(LF::TWS), z((size_t)(P > Q ? P : Q) * ZP, make_float2(NAN, NAN));
   for (int q = 0; q < Q; ++q)
     for (int k1 = 0; k1 < P; ++k1) {
       const cd w = w_turn((long)q * k1, M, false);
@@ -149,7 +149,7 @@ static void check_line(unsigned seed) {
 template <int P, int Q, int T>
 static void check_shape() {
   constexpr bool SQ = Line<P, Q, T>::SQUARE;
-  constexpr int ZE = Line<P, Q, T>::TWP;
+  constexpr int ZE = P + (P & 1);  // the bulk column pass's even exchange pitch
   check_line<P, Q, T, false, P, Q, false>(P * 100 + 1);
   check_line<P, Q, T, false, P / 2, Q, false>(P * 100 + 2);
   check_line<P, Q, T, true, P, Q, false>(P * 100 + 3);
