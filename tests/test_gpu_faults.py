@@ -17,10 +17,19 @@ from paper_2604_02624_gb300 import _lib as L
 from paper_2604_02624_gb300 import workloads as W
 from paper_2604_02624_gb300.api import DiffractiveStack
 
-from gpu_cases import TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS, assert_close, oracle_model
+from gpu_cases import TOL_GRAD_ORACLE, TOL_INTENSITY, TOL_LOSS, assert_close, custom, oracle_model
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
+
+
+def _geometry(name):
+    """tiny: M = 128, the column pass with one shared H tile; m512: N = 256 in
+    M = 512, the column pass whose groups stage their H rows in their stage
+    slots."""
+    if name == "m512":
+        return custom(256, 512, 1, [520, 610], 30, 64, name="m512")
+    return W.workload(name)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -90,15 +99,51 @@ def test_expired_wait_in_the_staged_adjoint_row_pass(monkeypatch):
     st.close()
 
 
-@pytest.mark.parametrize("force", ["multipass:bulk", "multipass:bulk[row_adj]", "multipass:bulk[row_fwd]"])
-def test_split_wait_verdict_is_taken_by_the_whole_block(monkeypatch, force):
+@pytest.mark.parametrize("geometry", ["tiny", "m512"])
+def test_expired_wait_in_the_column_pass(monkeypatch, geometry):
+    """With only the column pass on its TMA kernel, the injected stall reaches
+    that pass (its first forward gap): every block's wait for its input rows
+    expires, the host reads DOS_ERR_TIMEOUT, and the context then computes
+    the oracle's intensities and gradient, at M = 128 and at M = 512 (where
+    the H rows share the stage slots with the input rows)."""
+    w = _geometry(geometry)
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    monkeypatch.setenv("DOS_INJECT_WAIT_TIMEOUT", "1")
+    monkeypatch.setenv("DOS_FORCE_CONFIG", "multipass:bulk[col]")
+    st = DiffractiveStack.from_workload(w, device=DEV, path="auto")
+    monkeypatch.delenv("DOS_INJECT_WAIT_TIMEOUT")
+    monkeypatch.delenv("DOS_FORCE_CONFIG")
+    assert "bulk[col]" in L.dos_describe(st.handle)
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    Td = torch.tensor(T, dtype=torch.float32, device=DEV)
+    t0 = time.time()
+    st.forward(hd)
+    with pytest.raises(L.DosError) as e:
+        st.loss(Td)
+    assert e.value.code == L.DOS_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    I = st.forward(hd).cpu().numpy().astype(np.float64)
+    _, _, dl = st.loss(Td)
+    g = st.backward(dl).cpu().numpy().astype(np.float64)
+    _, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    assert_close(I, fwd["I"], TOL_INTENSITY)
+    assert_close(g, g_ref, TOL_GRAD_ORACLE)
+    st.close()
+
+
+@pytest.mark.parametrize("geometry,force", [
+    ("tiny", "multipass:bulk"), ("tiny", "multipass:bulk[row_adj]"), ("tiny", "multipass:bulk[row_fwd]"),
+    ("tiny", "multipass:bulk[col]"), ("m512", "multipass:bulk[col]"),
+])
+def test_split_wait_verdict_is_taken_by_the_whole_block(monkeypatch, geometry, force):
     """Each thread times its own bounded wait.  DOS_INJECT_WAIT_TIMEOUT=2 lets
     the copies of the next bulk pass land but makes the odd threads of every
     block give up their first wait: the block must take one verdict (all of
     its threads leave the item, none writes partial results) and the host
     must read DOS_ERR_TIMEOUT, not silently skipped items.  The context then
     computes the oracle's intensities and gradient."""
-    w = W.workload("tiny")
+    w = _geometry(geometry)
     h = W.thickness(w, 0)
     T = W.targets(w, 1)
     monkeypatch.setenv("DOS_INJECT_WAIT_TIMEOUT", "2")

@@ -197,6 +197,27 @@ def test_misaligned_layers_match_oracle(path):
     st.close()
 
 
+def test_misaligned_layers_at_m512_on_the_bulk_path():
+    """N = 256 in M = 512 on the bulk kernels: the column pass reads H from the
+    tiles its groups stage in their stage slots and the displacement phase
+    factors from the table."""
+    from gpu_cases import TOL_FIELD, TOL_GRAD_ORACLE, custom
+    w = custom(256, 512, 2, [520, 610], 30, 64, name="m512-misaligned")
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    st = DiffractiveStack.from_workload(w, device=DEV, path="multipass_bulk")
+    st.set_misalignment(DISP)
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    st.forward(hd)
+    o = st.output_field()
+    _, _, dl = st.loss(torch.tensor(T, dtype=torch.float32, device=DEV))
+    g = st.backward(dl).cpu().numpy().astype(np.float64)
+    _, _, g_ref, fwd = O.loss_and_grad(h, T, displacements=DISP, **oracle_model(w))
+    assert_close(o.cpu().numpy().astype(np.complex128), fwd["o"], TOL_FIELD, "field")
+    assert_close(g, g_ref, TOL_GRAD_ORACLE, "gradient")
+    st.close()
+
+
 def test_graph_step_follows_misalignment_changes():
     w = W.workload("small")
     h = torch.tensor(W.thickness(w, 0), dtype=torch.float32, device=DEV)
