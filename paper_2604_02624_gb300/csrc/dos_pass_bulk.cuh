@@ -586,9 +586,16 @@ struct PassBulk {
   // (read after the inverse DFT; the next channel's copy is issued as soon as
   // every thread is past them, at the barrier inside the forward DFT).  With
   // few rows per block three blocks fit on an SM.  Needs N even.
-  // dynamic shared memory: stage[RL][SR] | ck[RL][cks] | exchange[RL][RZL] | tw[TWS] | barrier[2]
+  // SHARE (32 elements per thread, M = 512): the two inputs take turns in one
+  // stage, which leaves room for three blocks per SM: the channel's checkpoint
+  // rows are fetched at the barrier inside its inverse DFT (every thread is
+  // past its spectra reads) and the next channel's spectra rows at the
+  // barrier inside its forward DFT (every thread is past its checkpoint reads).
+  static constexpr bool SHARE = LF::E > 20;
+  // dynamic shared memory: stage[RL][SR] | ck[RL][cks] (not with SHARE) | exchange[RL][RZL] | tw[TWS] | barrier[2]
   static size_t adj_staged_smem(int n) {
-    return sizeof(float2) * ((size_t)RL * SR + (size_t)RL * ck_stride(n) + (size_t)RL * RZL + LF::TWS + 1) +
+    return sizeof(float2) * ((size_t)RL * SR + (SHARE ? 0 : (size_t)RL * ck_stride(n)) + (size_t)RL * RZL +
+                             LF::TWS + 1) +
            2 * sizeof(uint64_t);
   }
 
@@ -597,8 +604,9 @@ struct PassBulk {
     extern __shared__ __align__(16) float2 smem[];
     const int cks = ck_stride(a.n);
     float2* stage = smem;
-    float2* ckb = stage + (size_t)RL * SR;
-    float2* zb = ckb + (size_t)RL * cks;
+    float2* ckb = SHARE ? stage : stage + (size_t)RL * SR;
+    float2* zb = SHARE ? stage + (size_t)RL * SR : ckb + (size_t)RL * cks;
+    static_assert(!SHARE || SR % 2 == 0, "the checkpoint rows share the 16-byte aligned stage");
     float2* tw = tw_align(zb + (size_t)RL * RZL);
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + LF::TWS);  // [0] spectra rows, [1] checkpoint rows
     const int l = threadIdx.x / T, t = threadIdx.x % T;
@@ -650,8 +658,11 @@ struct PassBulk {
     int issued_s = 0, issued_c = 0, done_s = 0, done_c = 0;  // copies per barrier (thread 0's view)
     if (w0 < w1) {
       fetch_s(w0);
-      fetch_c(w0);
-      issued_s = issued_c = 1;
+      issued_s = 1;
+      if constexpr (!SHARE) {
+        fetch_c(w0);
+        issued_c = 1;
+      }
     }
     for (int w = w0; w < w1; ++w) {
       const ChanConst cc = a.chan[w];
@@ -662,8 +673,11 @@ struct PassBulk {
 #pragma unroll
       for (int i = 0; i < E; ++i) r[i] = stage[(size_t)lr * SR + t + T * i];
       LF::template step1<true, LF::P, PKR>(r, t, z, tw);
-      __syncthreads();  // every thread is past its stage reads: the next channel may land there
-      if (w + 1 < w1) {
+      __syncthreads();  // every thread is past its stage reads: the next channel (SHARE: this channel's checkpoint) may land there
+      if constexpr (SHARE) {
+        fetch_c(w);
+        ++issued_c;
+      } else if (w + 1 < w1) {
         fetch_s(w + 1);
         ++issued_s;
       }
@@ -689,8 +703,13 @@ struct PassBulk {
         LF::template step1<false, NZF, PKR, LF::SQUARE>(r, t, z, tw);
         __syncthreads();  // every thread is past its checkpoint reads
         if (w + 1 < w1) {
-          fetch_c(w + 1);
-          ++issued_c;
+          if constexpr (SHARE) {
+            fetch_s(w + 1);
+            ++issued_s;
+          } else {
+            fetch_c(w + 1);
+            ++issued_c;
+          }
         }
         LF::template step2<false, LF::Q, PKR, LF::SQUARE>(r, t, z);  // next z write follows the loop-top barrier
         if (ok) {
@@ -701,8 +720,13 @@ struct PassBulk {
       } else {
         __syncthreads();  // every thread is past its checkpoint reads
         if (w + 1 < w1) {
-          fetch_c(w + 1);
-          ++issued_c;
+          if constexpr (SHARE) {
+            fetch_s(w + 1);
+            ++issued_s;
+          } else {
+            fetch_c(w + 1);
+            ++issued_c;
+          }
         }
       }
     }
@@ -728,7 +752,7 @@ struct PassBulk {
 
 // the staged adjoint row pass: three blocks of few rows per SM
 template <class LF, int RL, bool HALF, bool FIRST>
-__global__ void __launch_bounds__(LF::T * RL, LF::E <= 20 ? 3 : 1) k_row_adj_staged(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * RL, 3) k_row_adj_staged(PassArgs a) {
   PassBulk<LF, RL, HALF>::template row_adj_staged<FIRST>(a);
 }
 // two blocks per SM for every line shape: one leaves too few warps to hide the

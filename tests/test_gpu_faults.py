@@ -65,13 +65,15 @@ def test_expired_bulk_wait_is_reported_and_context_recovers(monkeypatch):
     st.close()
 
 
-def test_expired_wait_in_the_staged_adjoint_row_pass(monkeypatch):
+@pytest.mark.parametrize("geometry", ["tiny", "m512"])
+def test_expired_wait_in_the_staged_adjoint_row_pass(monkeypatch, geometry):
     """With only the adjoint row pass on its bulk kernel (both inputs staged by
     bulk copies), the injected stall reaches that pass: its blocks give up
     after the bounded waits, let their other copy land, and the next call that
     reads the device flag reports DOS_ERR_TIMEOUT; the context then computes
-    the oracle's gradient."""
-    w = W.workload("tiny")
+    the oracle's gradient.  At M = 512 the two inputs take turns in one
+    stage."""
+    w = _geometry(geometry)
     h = W.thickness(w, 0)
     T = W.targets(w, 1)
     monkeypatch.setenv("DOS_INJECT_WAIT_TIMEOUT", "1")
@@ -134,7 +136,7 @@ def test_expired_wait_in_the_column_pass(monkeypatch, geometry):
 
 @pytest.mark.parametrize("geometry,force", [
     ("tiny", "multipass:bulk"), ("tiny", "multipass:bulk[row_adj]"), ("tiny", "multipass:bulk[row_fwd]"),
-    ("tiny", "multipass:bulk[col]"), ("m512", "multipass:bulk[col]"),
+    ("tiny", "multipass:bulk[col]"), ("m512", "multipass:bulk[col]"), ("m512", "multipass:bulk[row_adj]"),
 ])
 def test_split_wait_verdict_is_taken_by_the_whole_block(monkeypatch, geometry, force):
     """Each thread times its own bounded wait.  DOS_INJECT_WAIT_TIMEOUT=2 lets
