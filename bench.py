@@ -493,12 +493,23 @@ def run_ours(a):
         loss_host = torch.empty(1, dtype=torch.float64).pin_memory()
         h_dev = torch.empty_like(h)
         T_dev = torch.empty_like(T)
+        # the targets (the step's large input) are uploaded on a copy stream
+        # while the forward pass runs; the loss waits for them, and the next
+        # upload waits until this step's loss has read them
+        main = torch.cuda.current_stream()
+        copy_stream = torch.cuda.Stream()
+        t_ready, t_free = torch.cuda.Event(), torch.cuda.Event()
 
         def e2e_step():
             h_dev.copy_(h_host, non_blocking=True)
-            T_dev.copy_(T_host, non_blocking=True)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(t_free)
+                T_dev.copy_(T_host, non_blocking=True)
+                t_ready.record(copy_stream)
             stack.forward(h_dev, out=I)
+            main.wait_event(t_ready)
             _, _, dLdI = stack.loss(T_dev, read=False)
+            t_free.record(main)
             stack.backward(dLdI, out=g)
             if dist is not None:
                 dist.all_reduce(g)
