@@ -112,7 +112,11 @@ enum {
  * first bulk-prefetch pass that the context launches announce its bytes
  * without copying them, so that the bounded waits of its blocks expire (one
  * second) and the next dos_read_loss reports DOS_ERR_TIMEOUT; later calls
- * run normally.
+ * run normally.  DOS_INJECT_WAIT_TIMEOUT=2 lets the copies land but makes the
+ * odd threads of every block give up their first wait; =3, for a first bulk
+ * pass that is a column pass, lets the copies land but makes every thread
+ * give up its wait for the transfer-table tile of its block's last item.
+ * Both are reported the same way.
  */
 enum {
   DOS_PATH_AUTO = 0,

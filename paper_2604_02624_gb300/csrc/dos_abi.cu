@@ -152,7 +152,9 @@ struct dos_ctx {
   int* h_err = nullptr;    // pinned copy
   // DOS_INJECT_WAIT_TIMEOUT (tests): the next bulk pass stalls.  1: its copies
   // never arrive, so every block's first wait expires; 2: the copies land, but
-  // the odd threads of every block report their first wait as expired
+  // the odd threads of every block report their first wait as expired; 3 (a
+  // column pass): the copies land, but every thread reports its wait for the
+  // transfer-table tile of its block's last item as expired
   int inject_stall = 0;
   CUtensorMap tmap_S;        // S as [nw][n][m] 8-byte elements, box {col_group, n, 1}
   CUtensorMap tmap_F;        // the same with box {col_group, fov, 1}: the adjoint's first column pass
@@ -501,7 +503,11 @@ int build(dos_ctx* x, const dos_config* c) {
   if ((rc = choose_path(x, c->path))) return rc;
   DOS_CUDA(cudaStreamSynchronize(x->stream), "create");
   const char* inj = std::getenv("DOS_INJECT_WAIT_TIMEOUT");
-  x->inject_stall = (inj && *inj) ? (std::string(inj) == "2" ? 2 : std::string(inj) != "0" ? 1 : 0) : 0;
+  x->inject_stall = (inj && *inj) ? (std::string(inj) == "2"   ? 2
+                                     : std::string(inj) == "3" ? 3
+                                     : std::string(inj) != "0" ? 1
+                                                               : 0)
+                                   : 0;
   return DOS_OK;
 }
 

@@ -63,7 +63,9 @@ struct PassArgs {
   Misalign mis;           // misaligned layers (mis.sq null: none)
   int* err;               // set to 1 by a bulk-copy pass whose bounded wait expired
   int stall;              // fault injection (tests): 1 = the bulk pass expects bytes that are never
-                          // copied; 2 = its copies land but odd threads give up their first wait
+                          // copied; 2 = its copies land but odd threads give up their first wait;
+                          // 3 = (column pass) the H tile of each block's last item lands but every
+                          // thread gives up its wait for it
   const void* tmap;       // host CUtensorMap of S as [nw][n][m] 8-byte elements (bulk column pass), or null
   int tmap_rows;          // rows of its box: the bulk column pass uses it when they are in_r1 - in_r0
   const void* hmap;       // host CUtensorMap of the transfer tables as [slots * nw][hs][hs] 8-byte elements

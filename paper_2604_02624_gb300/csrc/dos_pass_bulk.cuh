@@ -305,8 +305,10 @@ struct PassBulk {
       if constexpr (!LF::SQUARE) group_sync(g);
       // H(|ky|, |kx|) from the tile: |ky| = k below M/2 and M - k above, both
       // affine in i at compile time
-      if (STAGE_H && !bulk_wait(&bar[2], (uint32_t)(k & 1))) *h_late = 1;
-      if (SLOT_H && !bulk_wait(&bar[2 + g], (uint32_t)(k & 1))) *h_late = 1;
+      // (injected, tests: the wait of the block's last item gives up)
+      const bool give_up_h = a.stall == 3 && it + (int)gridDim.x >= items;
+      if (STAGE_H && !bulk_wait(&bar[2], (uint32_t)(k & 1), give_up_h)) *h_late = 1;
+      if (SLOT_H && !bulk_wait(&bar[2 + g], (uint32_t)(k & 1), give_up_h)) *h_late = 1;
       // STAGE_H: tile[hc][|ky|] (pitch HP).  SLOT_H: box b of the group's
       // tile, [hc - g][|ky| - b (HP - HB)] (pitch HB); box 0 holds |ky| < HB,
       // box 1 |ky| >= HP - HB, and which one a register's |ky| range lies in
@@ -345,14 +347,20 @@ struct PassBulk {
         if (i < EF && row >= a.out_r0 && row < a.out_r1) dst[(size_t)row * M] = r[i];
       }
     }
-    if (!ok && threadIdx.x == 0) {
-      // The copies in flight land (bounded) before the block leaves: both
-      // groups' rows of item k, and after an expired H wait in item k - 1
-      // that tile (no tile of item k was issued).
-      (void)bulk_wait(&bar[0], (uint32_t)(k & 1));
-      (void)bulk_wait(&bar[1], (uint32_t)(k & 1));
-      if (STAGE_H && *h_late) (void)bulk_wait(&bar[2], (uint32_t)((k - 1) & 1));
-      if (SLOT_H && *h_late) {
+    // An H wait that expired in the block's last item has no later verdict
+    // to read it: every thread (the loop ends for all of them together)
+    // takes it here.
+    const bool late = __syncthreads_or(*h_late != 0) != 0;
+    if ((!ok || late) && threadIdx.x == 0) {
+      // The copies in flight land (bounded) before the block leaves: after a
+      // failed verdict at item k both groups' rows of item k, and after an
+      // expired H wait in item k - 1 that tile (no tile of item k was issued).
+      if (!ok) {
+        (void)bulk_wait(&bar[0], (uint32_t)(k & 1));
+        (void)bulk_wait(&bar[1], (uint32_t)(k & 1));
+      }
+      if (STAGE_H && late) (void)bulk_wait(&bar[2], (uint32_t)((k - 1) & 1));
+      if (SLOT_H && late) {
         (void)bulk_wait(&bar[2], (uint32_t)((k - 1) & 1));
         (void)bulk_wait(&bar[3], (uint32_t)((k - 1) & 1));
       }

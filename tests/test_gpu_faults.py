@@ -134,6 +134,39 @@ def test_expired_wait_in_the_column_pass(monkeypatch, geometry):
     st.close()
 
 
+@pytest.mark.parametrize("geometry", ["tiny", "m512"])
+def test_expired_transfer_table_wait_in_a_blocks_last_item_is_reported(monkeypatch, geometry):
+    """DOS_INJECT_WAIT_TIMEOUT=3: the column pass's copies land, but every
+    thread gives up its wait for the transfer-table tile of its block's last
+    item.  No later item's verdict reads that, so the block takes it after
+    its loop, lets the tile land and sets the error flag: the host reads
+    DOS_ERR_TIMEOUT instead of results computed from a tile that had not
+    landed.  The context then computes the oracle's results."""
+    w = _geometry(geometry)
+    h = W.thickness(w, 0)
+    T = W.targets(w, 1)
+    monkeypatch.setenv("DOS_INJECT_WAIT_TIMEOUT", "3")
+    monkeypatch.setenv("DOS_FORCE_CONFIG", "multipass:bulk[col]")
+    st = DiffractiveStack.from_workload(w, device=DEV, path="auto")
+    monkeypatch.delenv("DOS_INJECT_WAIT_TIMEOUT")
+    monkeypatch.delenv("DOS_FORCE_CONFIG")
+    hd = torch.tensor(h, dtype=torch.float32, device=DEV)
+    Td = torch.tensor(T, dtype=torch.float32, device=DEV)
+    t0 = time.time()
+    st.forward(hd)
+    with pytest.raises(L.DosError) as e:
+        st.loss(Td)
+    assert e.value.code == L.DOS_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    I = st.forward(hd).cpu().numpy().astype(np.float64)
+    _, _, dl = st.loss(Td)
+    g = st.backward(dl).cpu().numpy().astype(np.float64)
+    _, _, g_ref, fwd = O.loss_and_grad(h, T, **oracle_model(w))
+    assert_close(I, fwd["I"], TOL_INTENSITY)
+    assert_close(g, g_ref, TOL_GRAD_ORACLE)
+    st.close()
+
+
 @pytest.mark.parametrize("geometry,force", [
     ("tiny", "multipass:bulk"), ("tiny", "multipass:bulk[row_adj]"), ("tiny", "multipass:bulk[row_fwd]"),
     ("tiny", "multipass:bulk[col]"), ("m512", "multipass:bulk[col]"), ("m512", "multipass:bulk[row_adj]"),
