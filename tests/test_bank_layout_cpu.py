@@ -146,8 +146,11 @@ def test_bulk_column_exchange_stage_and_tile_are_conflict_free(m):
             if c["STAGE_H"]:
                 addrs = [hc * HP + r for hc, r in zip(hcs, rows)]
             else:
+                # box 0 or box 1 of the group's tile, chosen per register (its |ky|
+                # range over the element owners) as the kernel does
                 b1 = GW * HB - (HP - HB)
-                addrs = [g * 100000 + (hc - g) * HB + (r if r < HB else r + b1)
+                box0 = (T * i + T - 1 < HB) if i < E // 2 else (M - T * i < HB)
+                addrs = [g * 100000 + (hc - g) * HB + (r if box0 else r + b1)
                          for (g, lc, t), hc, r in zip(L, hcs, rows)]
             checks.append((addrs, 1))
         for addrs, width in checks:
