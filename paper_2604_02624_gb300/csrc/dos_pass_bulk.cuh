@@ -673,7 +673,6 @@ struct PassBulk {
       }
     }
     for (int w = w0; w < w1; ++w) {
-      const ChanConst cc = a.chan[w];
       okw = __syncthreads_and(bulk_wait(&bar[0], (uint32_t)(done_s & 1), split_verdict(a, done_s))) != 0;  // one verdict for the block
       if (!okw) break;
       ++done_s;
@@ -693,6 +692,9 @@ struct PassBulk {
       okw = __syncthreads_and(bulk_wait(&bar[1], (uint32_t)(done_c & 1))) != 0;
       if (!okw) break;
       ++done_c;
+      // the channel's constants, loaded here rather than held through the
+      // inverse DFT (the registers they would take there spill)
+      const ChanConst cc = a.chan[w];
       const float2* ck = ckb + (size_t)lr * cks;
 #pragma unroll
       for (int i = 0; i < E; ++i) {
