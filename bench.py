@@ -91,8 +91,8 @@ def step_bytes(n, m, K, F, nw, bin_=1):
 
 
 def method_bytes_per_launch(kind, nw, n, K):
-    """The method's algorithmic bytes credited to one launch of a kernel kind
-    (SURVEY §8(d)): 16 N^2 B per forward layer-propagation (read v, write
+    """The method's algorithmic bytes credited to one launch of a kernel kind:
+    16 N^2 B per forward layer-propagation (read v, write
     v_next) and 24 N^2 B per adjoint one (read a and the checkpoint, write
     a_prev), complex64; a multi-pass launch advances every channel by one
     propagation, a fused sweep through all of its gaps."""

@@ -44,8 +44,8 @@ def test_step_bytes_structure():
 
 
 def test_roofline_bytes_are_the_methods():
-    """roofline.frac's numerator can be recomputed from SURVEY §8(d) alone:
-    16 N^2 bytes per forward and 24 N^2 per adjoint layer-propagation, times
+    """roofline.frac's numerator can be recomputed from the method's bytes
+    alone: 16 N^2 bytes per forward and 24 N^2 per adjoint layer-propagation, times
     the channels a launch advances; the whole step is (K + 1) * 40 N^2 per
     channel, which is step_bytes' "ideal"."""
     mb = bench.method_bytes_per_launch
