@@ -75,6 +75,37 @@ DOS_HD float2 vsub(float2 a, float2 b) {
   return csub(a, b);
 }
 
+// a * (c, c) + acc and a * (c, c) for a scalar constant c: one packed FP32-pair
+// instruction (fma / mul .rn.f32x2) when PK is set, two scalar ones otherwise
+template <bool PK>
+DOS_HD float2 vfma_bc(float2 a, float c, float2 acc) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (PK) {
+    float2 d;
+    asm("{\n .reg .b64 pa, pc, pacc, pd;\n mov.b64 pa, {%2, %3};\n mov.b64 pc, {%4, %4};\n"
+        " mov.b64 pacc, {%5, %6};\n fma.rn.f32x2 pd, pa, pc, pacc;\n mov.b64 {%0, %1}, pd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(c), "f"(acc.x), "f"(acc.y));
+    return d;
+  }
+#endif
+  return make_float2(fmaf(c, a.x, acc.x), fmaf(c, a.y, acc.y));
+}
+template <bool PK>
+DOS_HD float2 vmul_bc(float2 a, float c) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (PK) {
+    float2 d;
+    asm("{\n .reg .b64 pa, pc, pd;\n mov.b64 pa, {%2, %3};\n mov.b64 pc, {%4, %4};\n"
+        " mul.rn.f32x2 pd, pa, pc;\n mov.b64 {%0, %1}, pd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(c));
+    return d;
+  }
+#endif
+  return make_float2(a.x * c, a.y * c);
+}
+
 // ------------------------------------------------- compile-time trigonometry
 namespace ct {
 constexpr double kPi = 3.14159265358979323846264338327950288;
@@ -342,10 +373,10 @@ DOS_HD void bfly5(float2* x) {
   const float2 t2 = vadd<PK>(x[2], x[3]);
   const float2 t3 = vsub<PK>(x[1], x[4]);
   const float2 t4 = vsub<PK>(x[2], x[3]);
-  const float2 a1 = make_float2(fmaf(c2, t2.x, fmaf(c1, t1.x, x0.x)), fmaf(c2, t2.y, fmaf(c1, t1.y, x0.y)));
-  const float2 a2 = make_float2(fmaf(c1, t2.x, fmaf(c2, t1.x, x0.x)), fmaf(c1, t2.y, fmaf(c2, t1.y, x0.y)));
-  const float2 b1 = make_float2(fmaf(s2, t4.x, s1 * t3.x), fmaf(s2, t4.y, s1 * t3.y));
-  const float2 b2 = make_float2(fmaf(-s1, t4.x, s2 * t3.x), fmaf(-s1, t4.y, s2 * t3.y));
+  const float2 a1 = vfma_bc<PK>(t2, c2, vfma_bc<PK>(t1, c1, x0));
+  const float2 a2 = vfma_bc<PK>(t2, c1, vfma_bc<PK>(t1, c2, x0));
+  const float2 b1 = vfma_bc<PK>(t4, s2, vmul_bc<PK>(t3, s1));
+  const float2 b2 = vfma_bc<PK>(t4, -s1, vmul_bc<PK>(t3, s2));
   // forward: X1 = a1 - j b1, X4 = a1 + j b1, X2 = a2 - j b2, X3 = a2 + j b2
   const float2 jb1 = INV ? make_float2(-b1.y, b1.x) : make_float2(b1.y, -b1.x);
   const float2 jb2 = INV ? make_float2(-b2.y, b2.x) : make_float2(b2.y, -b2.x);

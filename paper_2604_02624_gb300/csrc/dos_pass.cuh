@@ -388,12 +388,14 @@ template <class LF, bool HALF>
 __global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>()) k_row_first(PassArgs a) {
   Pass<LF, HALF>::row_first(a);
 }
+// the output and seed passes: three blocks per SM where the lines are short
+// (the register count would otherwise drift past 64 and leave two)
 template <class LF, bool HALF>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_out(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>()) k_row_out(PassArgs a) {
   Pass<LF, HALF>::row_out(a);
 }
 template <class LF, bool HALF>
-__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL) k_row_seed(PassArgs a) {
+__global__ void __launch_bounds__(LF::T * Pass<LF>::ROWL, pass_min_blocks<LF>()) k_row_seed(PassArgs a) {
   Pass<LF, HALF>::row_seed(a);
 }
 template <class LF, bool HALF, bool FIRST>
