@@ -37,30 +37,30 @@ sys.path.insert(0, ROOT)
 TRAFFIC_PER_CHANNEL = {
     # One capture of every bulk pass of a step (dram__bytes_read + write per
     # launch / 256 channels), each kind averaged over its launches.
-    # 200 -> 400, K = 5: forward column 1.3866 / 1.3865 / 1.3867 / 1.3862 MB and
-    # 1.0640 MB (last gap, field-of-view output rows); adjoint column 0.9074 MB
-    # (first gap, field-of-view input rows) and 1.3866 / 1.3870 / 1.3869 / 1.3868 MB;
-    # forward row 0.7279 MB (first pass, from the input-field table) and 1.3574 /
-    # 1.3580 / 1.3576 / 1.3582 MB; adjoint row 1.4221 / 1.4199 / 1.4221 / 1.4198 MB
-    # and 0.9855 MB (layer 1: no spectra written back)
-    ("column_bulk", 200, 400, "column_forward"): ((1.3866e6 + 1.3865e6 + 1.3867e6 + 1.3862e6 + 1.0640e6) / 5,
+    # 200 -> 400, K = 5: forward column 1.3875 / 1.3875 / 1.3887 / 1.3872 MB and
+    # 1.0646 MB (last gap, field-of-view output rows); adjoint column 0.9075 MB
+    # (first gap, field-of-view input rows) and 1.3876 / 1.3883 / 1.3874 / 1.3904 MB;
+    # forward row 0.7277 MB (first pass, from the input-field table) and 1.3579 /
+    # 1.3580 / 1.3577 / 1.3583 MB; adjoint row 1.4205 / 1.4195 / 1.4215 / 1.4203 MB
+    # and 0.9861 MB (layer 1: no spectra written back)
+    ("column_bulk", 200, 400, "column_forward"): ((1.3875e6 + 1.3875e6 + 1.3887e6 + 1.3872e6 + 1.0646e6) / 5,
                                                   "profiles/column_pass_bulk_batched.md"),
-    ("column_bulk", 200, 400, "column_adjoint"): ((0.9074e6 + 1.3866e6 + 1.3870e6 + 1.3869e6 + 1.3868e6) / 5,
+    ("column_bulk", 200, 400, "column_adjoint"): ((0.9075e6 + 1.3876e6 + 1.3883e6 + 1.3874e6 + 1.3904e6) / 5,
                                                   "profiles/column_pass_bulk_batched.md"),
-    ("row_bulk", 200, 400, "row_forward"): ((0.7279e6 + 1.3574e6 + 1.3580e6 + 1.3576e6 + 1.3582e6) / 5,
+    ("row_bulk", 200, 400, "row_forward"): ((0.7277e6 + 1.3579e6 + 1.3580e6 + 1.3577e6 + 1.3583e6) / 5,
                                             "profiles/row_passes_batched.md"),
-    ("row_bulk", 200, 400, "row_adjoint"): ((1.4221e6 + 1.4199e6 + 1.4221e6 + 1.4198e6 + 0.9855e6) / 5,
+    ("row_bulk", 200, 400, "row_adjoint"): ((1.4205e6 + 1.4195e6 + 1.4215e6 + 1.4203e6 + 0.9861e6) / 5,
                                             "profiles/row_passes_batched.md"),
     # 256 -> 512, K = 8 (the precision geometry with 256 channels): forward column
-    # 2.4097 / 2.4095 / 2.4088 / 2.4097 / 2.4096 / 2.4088 / 2.4092 MB and 1.7782 MB;
-    # adjoint column 1.6245 MB and 2.4095 / 2.4092 / 2.4096 / 2.4094 / 2.4099 /
-    # 2.4094 / 2.4091 MB; forward row 1.3347 MB and 2.3728 / 2.3726 / 2.3729 /
-    # 2.3740 / 2.3726 / 2.3729 / 2.3729 MB; adjoint row 2.4558 / 2.4546 / 2.4537 /
-    # 2.4571 / 2.4549 / 2.4557 / 2.4532 MB and 1.6202 MB
-    ("column_bulk", 256, 512, "column_forward"): (2.33044e6, "profiles/column_pass_m512_precision.md"),
-    ("column_bulk", 256, 512, "column_adjoint"): (2.31133e6, "profiles/column_pass_m512_precision.md"),
-    ("row_bulk", 256, 512, "row_forward"): (2.24318e6, "profiles/row_passes_m512_precision.md"),
-    ("row_bulk", 256, 512, "row_adjoint"): (2.35065e6, "profiles/row_passes_m512_precision.md"),
+    # 2.4101 / 2.4105 / 2.4089 / 2.4096 / 2.4093 / 2.4098 / 2.4090 MB and 1.7779 MB;
+    # adjoint column 1.6248 MB and 2.4096 / 2.4094 / 2.4101 / 2.4092 / 2.4092 /
+    # 2.4092 / 2.4098 MB; forward row 1.3346 MB and 2.3736 / 2.3727 / 2.3729 /
+    # 2.3733 / 2.3738 / 2.3720 / 2.3721 MB; adjoint row 2.4562 / 2.4547 / 2.4545 /
+    # 2.4558 / 2.4562 / 2.4542 / 2.4540 MB and 1.6203 MB
+    ("column_bulk", 256, 512, "column_forward"): (2.33064e6, "profiles/column_pass_m512_precision.md"),
+    ("column_bulk", 256, 512, "column_adjoint"): (2.31141e6, "profiles/column_pass_m512_precision.md"),
+    ("row_bulk", 256, 512, "row_forward"): (2.24313e6, "profiles/row_passes_m512_precision.md"),
+    ("row_bulk", 256, 512, "row_adjoint"): (2.35074e6, "profiles/row_passes_m512_precision.md"),
 }
 
 
